@@ -1,0 +1,62 @@
+"""Planted mistakes in the oracle (CPU only) must be caught by the pins.
+
+Each test patches one plausible error into the oracle -- a dropped term, a wrong
+sign, a non-conjugated adjoint -- and checks that the pin it should trip does trip.
+"""
+import numpy as np
+import pytest
+
+import scenes
+from oracle import green, loss
+from oracle.forward import forward_solve
+from oracle.green import Operators
+from oracle.mie import mie_esca_line_source
+from oracle.problem import from_workload
+
+
+def _mie_err(n=32):
+    p = from_workload(scenes.workload("c1", nx=n, ny=n, ni=6, nr=10))
+    ops = Operators(p, dense_gd=True)
+    chi = scenes.rasterise([scenes.Shape("disk", 0.0, 0.0, 0.4, eps_r=2.0)], n, n, 2.0)
+    _, _, esca = forward_solve(ops, chi)
+    r_eq = np.sqrt(np.count_nonzero(chi) * p.dx * p.dy / np.pi)
+    ref = mie_esca_line_source(p.k0, r_eq, 2.0, p.tx, p.rx)
+    return np.linalg.norm(esca - ref) / np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("mistake", ["drop_minus_one", "h0_instead_of_h1", "conj_kernel"])
+def test_green_mistakes_break_mie(monkeypatch, mistake):
+    good = green.richmond_coeffs
+
+    def bad(p):
+        c_off, c_self = good(p)
+        ka = p.k0 * p.a_eq
+        if mistake == "drop_minus_one":
+            return c_off, c_self + 1.0
+        if mistake == "h0_instead_of_h1":
+            from scipy import special
+            return c_off, 1j * np.pi * ka / 2 * special.hankel1(0, ka) - 1.0
+        return np.conj(c_off), np.conj(c_self)
+    assert _mie_err() < 0.08
+    monkeypatch.setattr(green, "richmond_coeffs", bad)
+    assert _mie_err() > 0.08
+
+
+def test_adjoint_without_conjugate_breaks_finite_differences(monkeypatch):
+    p = from_workload(scenes.workload("c1", nx=12, ny=12, ni=3, nr=6, kx=5, ky=5))
+    ops = Operators(p)
+    chi = scenes.rasterise([scenes.Shape("disk", 0.0, 0.0, 0.4, eps_r=2.0)], 12, 12, 2.0)
+    _, _, esca = forward_solve(ops, chi)
+    rng = np.random.default_rng(0)
+    a = 0.3 * (rng.standard_normal((3, 5, 5)) + 1j * rng.standard_normal((3, 5, 5)))
+    d = rng.standard_normal(a.shape) + 1j * rng.standard_normal(a.shape)
+
+    def mismatch():
+        _, g = loss.loss_grad(ops, esca, a)
+        h = 1e-6
+        fd = (loss.loss(ops, esca, a + h * d)[0] - loss.loss(ops, esca, a - h * d)[0]) / (2 * h)
+        return abs(fd - np.sum(np.real(np.conj(g) * d))) / abs(fd)
+    assert mismatch() < 1e-7
+    orig = ops.gd
+    monkeypatch.setattr(ops, "gd", lambda J, adjoint=False: orig(J, False))
+    assert mismatch() > 1e-3

@@ -1,0 +1,165 @@
+/*
+ * pdf.h -- C ABI of the GB300 (sm_103a) implementation of the per-iteration loss and
+ * gradient of the physics-driven Fourier-spectral (PDF) inverse-scattering solver
+ * (arXiv 2602.13805), with its initialisation, outer Adam loop and post-processing.
+ *
+ * Conventions shared by every entry point
+ *   - Complex arrays are interleaved complex64 (float re, float im), row-major, x fastest.
+ *     Grid arrays are [ny][nx] (M2 rows of M1 pixels, Sec. 2); per-incidence arrays are
+ *     [ni][ny][nx]; Fourier coefficients are [ni][ky][kx]; measured data are [ni][nr].
+ *   - Retained Fourier indices per axis of length M (Sec. 2.3, Eq. 9): storage slot j holds
+ *     DFT index j for j < ceil(K/2) and M - K + j otherwise (K = 2 M_F gives the paper's four
+ *     M_F x M_F corner blocks; odd K gives the symmetric set).  The DFT is unitary.
+ *   - Gradients of the real loss L with respect to complex z follow PyTorch's convention
+ *     dL/dRe z + i dL/dIm z.
+ *   - Every call is asynchronous on the CUDA stream it is given (NULL = legacy default
+ *     stream) unless its comment says it synchronises.  Device pointers are caller-owned and
+ *     are not retained after the call returns.  The problem handle owns its workspace.
+ *   - Every call returns a pdf_status; nothing aborts or throws.  On failure
+ *     pdf_last_error() returns a message for the calling thread.
+ *   - A handle may be used by one stream at a time (its workspace is not duplicated).
+ */
+#ifndef PDF_H
+#define PDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pdf_status {
+  PDF_OK = 0,
+  PDF_EINVAL = -1,        /* invalid argument (sizes, pointers, parameters)            */
+  PDF_ENOMEM = -2,        /* device allocation failed                                  */
+  PDF_ECUDA = -3,         /* a CUDA runtime call or kernel launch failed               */
+  PDF_ENONFINITE = -4,    /* a loss term became NaN/Inf (only detected when synchronising) */
+  PDF_ETIMEOUT = -5,      /* a bounded device-side wait ran out                        */
+  PDF_EUNSUPPORTED = -6   /* a size or mode this build does not support                */
+} pdf_status;
+
+typedef struct pdf_problem pdf_problem;   /* opaque, owned by the library */
+
+/* Problem statement (Sec. 2 and Sec. 3.2).  Lengths are in the same unit as 2*pi/k0. */
+typedef struct pdf_config {
+  int32_t nx, ny;            /* M1 x M2 pulse grid over the DOI, 2 <= nx, ny <= 256          */
+  double side_x, side_y;     /* DOI side lengths; the DOI is centred on the origin           */
+  double k0;                 /* free-space wavenumber (real, > 0)                            */
+  int32_t ni, nr;            /* incidences (transmitters) and receivers, 1..1024 each         */
+  const double* tx_xy;       /* host [ni][2]: line-source positions, or plane-wave directions */
+  const double* rx_xy;       /* host [nr][2]: receiver positions (outside the DOI)           */
+  int32_t inc_kind;          /* 0 = line source H0(k0|r - r_p|)/|H0(k0|r_p|)|, 1 = plane wave  */
+  int32_t kx, ky;            /* Fourier truncation, 1 <= kx <= nx, 1 <= ky <= ny (Eq. 9)      */
+  double beta_re, beta_im;   /* CIE parameter beta of Eq. (6)-(7); Re beta > 0 required      */
+  double lambda_bound;       /* lambda_1 of Eq. (13), paper 1e-3                             */
+  double lambda_tv;          /* lambda_2, paper 1e-5                                         */
+  double lambda_bridge;      /* lambda_3, paper 1e-5                                         */
+  double tau_b;              /* bridge threshold tau_B of Eq. (19), paper 0.5                */
+  double eps_tv;             /* smoothing inside the TV square root of Eq. (18)              */
+  double eps_abs;            /* smoothing inside |chi| of Eq. (19)                           */
+  double q_min;              /* clamp of |1 - R| when forming chi = R / (beta (1 - R))       */
+  int32_t precision;         /* 0 = FP32 contractions, 1 = split-BF16 tensor-core contractions */
+  int32_t reserved;
+} pdf_config;
+
+/* Fills the paper's defaults (beta = 6, lambdas 1e-3/1e-5/1e-5, tau_B = 0.5, k0 = 2 pi) and
+ * zero sizes/pointers.  Never fails. */
+void pdf_config_default(pdf_config* cfg);
+
+/* Assembles the operators of one geometry on the device: the Richmond G_D kernel spectrum
+ * (FP64 Bessel evaluation and FP64 DFT, Eq. 1 and 3), G_S (Eq. 2 and 4), the incident fields,
+ * the Fourier synthesis tables (Eq. 9), and allocates the workspace.  esca (may be NULL, then
+ * set it with pdf_set_data before use): measured scattered field [ni][nr] complex64, on the
+ * host when esca_on_device == 0 (copied synchronously) or on the device.  Synchronises `stream`
+ * before returning.  Errors: PDF_EINVAL for out-of-range sizes/parameters or NULL antenna
+ * arrays, PDF_EUNSUPPORTED for sizes above the limits stated in pdf_config, PDF_ENOMEM. */
+pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esca_on_device, void* stream,
+                     pdf_problem** out);
+
+/* Replaces the measured data E_sca [ni][nr] complex64 (host when on_device == 0: the copy is
+ * staged through the handle's pinned buffer and is asynchronous on `stream`; device otherwise)
+ * and recomputes ||E_sca||^2 on the device (Eq. 16 denominator). */
+pdf_status pdf_set_data(pdf_problem* h, const void* esca, int on_device, void* stream);
+
+/* One evaluation of the composite loss of Eq. (13)-(19) and its gradient.
+ *   alpha [ni][ky][kx] complex64, device, read only.
+ *   grad  [ni][ky][kx] complex64, device, overwritten with dL/d alpha (may be NULL).
+ *   terms [6] float64, device, overwritten with L, L_State, L_Data, L_Bound, L_TV, L_Bridge
+ *         (may be NULL).
+ * R-hat is the per-pixel least-squares solution of Eq. (6) over the incidences and
+ * chi-hat = R / (beta (1 - R)) (Eq. 7); the gradient differentiates through both. */
+pdf_status pdf_loss_grad(pdf_problem* h, const void* alpha, void* grad, double* terms, void* stream);
+
+/* Operator application for testing and for callers composing their own solvers.
+ * in/out are device complex64 arrays of the shapes below (ni batched where marked). */
+enum pdf_op {
+  PDF_OP_GD = 0,    /* [ni][ny][nx] -> [ni][ny][nx]   G_D x (zero-padded FFT convolution) */
+  PDF_OP_GDH = 1,   /* [ni][ny][nx] -> [ni][ny][nx]   G_D^H x                             */
+  PDF_OP_GS = 2,    /* [ni][ny][nx] -> [ni][nr]       G_S x                               */
+  PDF_OP_GSH = 3,   /* [ni][nr]     -> [ni][ny][nx]   G_S^H d                             */
+  PDF_OP_SYN = 4,   /* [ni][ky][kx] -> [ni][ny][nx]   F*_T (synthesis, Eq. 9)             */
+  PDF_OP_ANA = 5,   /* [ni][ny][nx] -> [ni][ky][kx]   F_T restricted to retained modes    */
+  PDF_OP_CCO = 6,   /* [ny][nx]     -> [ny][nx]       contrast-compensated operator (Eq. 10-11) */
+  PDF_OP_CHI = 7,   /* [ni][ky][kx] -> [ny][nx]       chi-hat of the CIE update (Eq. 6-7) */
+  PDF_OP_EINC = 8   /* (ignored)    -> [ni][ny][nx]   the assembled incident fields        */
+};
+pdf_status pdf_apply_op(pdf_problem* h, int op, const void* in, void* out, void* stream);
+
+/* Options of a whole reconstruction (Sec. 3): initialisation, Adam on alpha viewed as
+ * (Re, Im) pairs with torch.optim.Adam semantics, final chi-hat, CCO post-processing. */
+typedef struct pdf_solve_opts {
+  int32_t iters;             /* Adam iterations (>= 0)                                        */
+  int32_t init;              /* 0 = BP + one exact-line-search CSI step (Sec. 3.1, Eq. 12),
+                                1 = alpha0 given, 2 = zeros                                   */
+  double lr, adam_b1, adam_b2, adam_eps;   /* paper: lr 1e-2; torch defaults 0.9, 0.999, 1e-8 */
+  const void* alpha0;        /* device [ni][ky][kx] complex64 when init == 1                   */
+  const void* chi_true;      /* optional device [ny][nx] complex64: enables RelErr             */
+  int32_t apply_cco;         /* 1 = post-process chi-hat with the CCO (Sec. 2.4)               */
+  int32_t cco_radius;        /* guided-filter box radius (default 2)                           */
+  double cco_eps;            /* guided-filter regulariser (default 1e-2)                       */
+  double cco_eta_max, cco_tau, cco_delta;  /* Eq. (11): 0.1, 3, 0.5                            */
+  int32_t use_graph;         /* 1 = run the iteration loop as a CUDA graph                     */
+  int32_t history_every;     /* > 0: write the 6 loss terms every n iterations to history      */
+  double* history;           /* device [ceil(iters / history_every)][6] when history_every > 0 */
+} pdf_solve_opts;
+
+typedef struct pdf_solve_report {
+  int32_t iters_run;
+  int32_t nonfinite;         /* 1 if a loss term was NaN/Inf at the end                        */
+  double terms[6];           /* loss terms at the final alpha                                  */
+  double relerr;             /* ||chi - chi_true|| / ||chi_true|| before CCO (NaN without truth) */
+  double relerr_cco;         /* same after CCO                                                 */
+} pdf_solve_report;
+
+void pdf_solve_opts_default(pdf_solve_opts* o);
+
+/* Whole reconstruction on `stream`.  chi_out [ny][nx] (device, may be NULL) receives chi-hat
+ * after the CCO when apply_cco, else chi-hat; chi_raw_out the chi-hat before CCO (may be NULL);
+ * alpha_out [ni][ky][kx] the final coefficients (may be NULL).  When report != NULL the call
+ * synchronises `stream` and fills it (PDF_ENONFINITE if a loss term is not finite). */
+pdf_status pdf_solve(pdf_problem* h, const pdf_solve_opts* opts, void* chi_out, void* chi_raw_out,
+                     void* alpha_out, pdf_solve_report* report, void* stream);
+
+/* Forward scattering solve on the device (Eq. 3-5): (I - G_D diag(chi)) E_tot = E_inc by
+ * BiCGSTAB with the FFT-applied G_D, then E_sca = G_S chi E_tot.  chi [ny][nx] device
+ * complex64, esca_out [ni][nr] device complex64, j_out [ni][ny][nx] (may be NULL).  Synchronises
+ * `stream` (convergence is checked on the host).  tol: relative residual; max_iter: cap.
+ * Returns PDF_ETIMEOUT if the iteration cap is reached before tol. */
+pdf_status pdf_forward(pdf_problem* h, const void* chi, void* esca_out, void* j_out, double tol,
+                       int32_t max_iter, int32_t* iters_out, void* stream);
+
+/* Number of kernels this library has launched in the calling process (graph launches count
+ * every kernel node they execute).  For benchmarking evidence. */
+uint64_t pdf_launch_count(void);
+
+/* Frees the handle and its workspace (synchronises the device work of the handle first). */
+void pdf_destroy(pdf_problem* h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* pdf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDF_H */

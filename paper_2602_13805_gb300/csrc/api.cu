@@ -1,0 +1,556 @@
+// C-ABI entry points, handle lifetime, and the FP64 operator assembly kernels
+// (Richmond G_D spectrum, G_S, incident fields, Fourier synthesis tables).
+//
+// Assembly (Sec. 2.1, Eq. 1-4), with the time factor e^{-i w t} and
+// g = (i/4) H0^(1)(k0 |r - r'|) integrated over the equal-area disk of a cell:
+//   G_D[m, n] = (i pi k0 a / 2) J1(k0 a) H0(k0 rho_mn),  m != n
+//   G_D[n, n] = (i pi k0 a / 2) H1(k0 a) - 1
+//   G_S[r, n] = (i pi k0 a / 2) J1(k0 a) H0(k0 |r_r - r_n|)
+// Bessel functions are CUDA's double-precision j0/j1/y0/y1.  G_D is stored as the
+// FP64 DFT of its block-Toeplitz kernel embedded in a Px x Py circulant
+// (Px >= 2 nx, Py >= 2 ny, both 2^a 3^b), rounded to complex64 once.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <atomic>
+#include <climits>
+
+#include "fft.cuh"
+#include "problem.cuh"
+
+// ---------------------------------------------------------------------------
+// errors and launch accounting
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+static std::atomic<uint64_t> g_launches{0};
+
+void pdf_count_launch(uint64_t n) { g_launches += n; }
+
+pdf_status set_err(pdf_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+pdf_status cuda_err(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? PDF_ENOMEM : PDF_ECUDA;
+}
+
+extern "C" const char* pdf_last_error(void) { return g_last_error.c_str(); }
+extern "C" uint64_t pdf_launch_count(void) { return g_launches.load(); }
+
+// ---------------------------------------------------------------------------
+// assembly kernels (FP64)
+// ---------------------------------------------------------------------------
+__global__ void k_twiddles(double2* twd, float2* twf, int P) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= P) return;
+  double s, c;
+  sincospi(-2.0 * (double)e / (double)P, &s, &c);
+  twd[e] = make_double2(c, s);
+  twf[e] = make_float2((float)c, (float)s);
+}
+
+// Hankel function of the first kind, order 0 and 1, from CUDA's double Bessel functions.
+__device__ __forceinline__ double2 hankel0(double x) { return make_double2(j0(x), y0(x)); }
+
+struct Richmond { double2 c_off, c_self; };
+
+__device__ __forceinline__ Richmond richmond(double k0, double a) {
+  const double ka = k0 * a;
+  const double h = 0.5 * M_PI * ka;                        // pi k0 a / 2
+  Richmond r;
+  r.c_off = make_double2(0.0, h * j1(ka));                 // i h J1(ka)
+  r.c_self = make_double2(-h * y1(ka) - 1.0, h * j1(ka));  // i h (J1 + i Y1) - 1
+  return r;
+}
+
+// Circulant embedding of the G_D kernel: [Py][Px] complex double.
+__global__ void k_green_kernel(double2* g, int nx, int ny, int Px, int Py, double dx, double dy, double k0,
+                               double a) {
+  int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  int iy = blockIdx.y;
+  if (ix >= Px) return;
+  Richmond rc = richmond(k0, a);
+  int ox = ix <= nx - 1 ? ix : (ix >= Px - (nx - 1) ? ix - Px : INT_MAX);
+  int oy = iy <= ny - 1 ? iy : (iy >= Py - (ny - 1) ? iy - Py : INT_MAX);
+  double2 val = make_double2(0.0, 0.0);
+  if (ox != INT_MAX && oy != INT_MAX) {
+    if (ox == 0 && oy == 0) {
+      val = rc.c_self;
+    } else {
+      double rho = hypot((double)ox * dx, (double)oy * dy);
+      val = cmul(rc.c_off, hankel0(k0 * rho));
+    }
+  }
+  g[(size_t)iy * Px + ix] = val;
+}
+
+// In-place FP64 FFT of rows (axis 1) of a [nrows][P] array, ROWS rows per CTA.
+template <int ROWS>
+__global__ void k_fft_rows_d(double2* data, int nrows, FFTPlan pl, const double2* tw) {
+  extern __shared__ double2 smd[];
+  double2* b0 = smd;
+  double2* b1 = smd + ROWS * pl.P;
+  int r0 = blockIdx.x * ROWS;
+  for (int i = threadIdx.x; i < ROWS * pl.P; i += blockDim.x) {
+    int rr = i / pl.P, c = i - rr * pl.P;
+    b0[i] = (r0 + rr < nrows) ? data[(size_t)(r0 + rr) * pl.P + c] : make_double2(0, 0);
+  }
+  __syncthreads();
+  double2* res = fft_lines(b0, b1, ROWS, pl.P, pl, tw, false);
+  for (int i = threadIdx.x; i < ROWS * pl.P; i += blockDim.x) {
+    int rr = i / pl.P, c = i - rr * pl.P;
+    if (r0 + rr < nrows) data[(size_t)(r0 + rr) * pl.P + c] = res[i];
+  }
+}
+
+// FP64 FFT of columns of a [Py][Px] array, scaled by `scale`, written as complex64.
+template <int COLS>
+__global__ void k_fft_cols_d(const double2* data, float2* out, int Px, FFTPlan pl, const double2* tw,
+                             double scale) {
+  extern __shared__ double2 smd[];
+  const int Py = pl.P;
+  double2* b0 = smd;
+  double2* b1 = smd + COLS * Py;
+  int c0 = blockIdx.x * COLS;
+  for (int i = threadIdx.x; i < COLS * Py; i += blockDim.x) {
+    int y = i / COLS, c = i - y * COLS;
+    b0[c * Py + y] = (c0 + c < Px) ? data[(size_t)y * Px + c0 + c] : make_double2(0, 0);
+  }
+  __syncthreads();
+  double2* res = fft_lines(b0, b1, COLS, Py, pl, tw, false);
+  for (int i = threadIdx.x; i < COLS * Py; i += blockDim.x) {
+    int y = i / COLS, c = i - y * COLS;
+    if (c0 + c < Px) out[(size_t)y * Px + c0 + c] = to_f(scale * res[c * Py + y]);
+  }
+}
+
+// Incident fields [ni][ny][nx] and per-row partial sums of |E_inc|^2 (double) into part[ni*ny].
+__global__ void k_einc(float2* einc, double* part, const double* tx, int nx, int ny, double sx, double sy,
+                       double k0, int kind) {
+  __shared__ double red[32];
+  int y = blockIdx.x, p = blockIdx.y;
+  double dx = sx / nx, dy = sy / ny;
+  double txx = tx[2 * p], txy = tx[2 * p + 1];
+  double acc = 0.0;
+  double norm = 1.0, ux = 0.0, uy = 0.0;
+  if (kind == 0) {
+    double2 h = hankel0(k0 * hypot(txx, txy));
+    norm = 1.0 / sqrt(cabs2(h));
+  } else {
+    double l = hypot(txx, txy);
+    ux = txx / l;
+    uy = txy / l;
+  }
+  double yc = -0.5 * sy + (y + 0.5) * dy;
+  for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+    double xc = -0.5 * sx + (x + 0.5) * dx;
+    double2 e;
+    if (kind == 0) {
+      e = norm * hankel0(k0 * hypot(xc - txx, yc - txy));
+    } else {
+      double s, c;
+      sincos(k0 * (ux * xc + uy * yc), &s, &c);
+      e = make_double2(c, s);
+    }
+    einc[((size_t)p * ny + y) * nx + x] = to_f(e);
+    acc += cabs2(e);
+  }
+  double t = block_sum(acc, red);
+  if (threadIdx.x == 0) part[p * ny + y] = t;
+}
+
+// Receiver operator [nr][ny*nx].
+__global__ void k_gs(float2* gs, const double* rx, int nx, int ny, double sx, double sy, double k0, double a) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = blockIdx.y;
+  if (n >= nx * ny) return;
+  Richmond rc = richmond(k0, a);
+  int y = n / nx, x = n - y * nx;
+  double xc = -0.5 * sx + (x + 0.5) * (sx / nx);
+  double yc = -0.5 * sy + (y + 0.5) * (sy / ny);
+  double rho = hypot(rx[2 * r] - xc, rx[2 * r + 1] - yc);
+  gs[(size_t)r * nx * ny + n] = to_f(cmul(rc.c_off, hankel0(k0 * rho)));
+}
+
+// Synthesis table W[j][x] = exp(+2 pi i f_j x / n) / sqrt(n) with f_j the stored mode index.
+__global__ void k_synth_table(float2* W, int K, int n) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y;
+  if (x >= n) return;
+  int h = (K + 1) / 2;
+  long f = j < h ? j : n - K + j;
+  long m = (f * (long)x) % n;
+  double s, c;
+  sincospi(2.0 * (double)m / (double)n, &s, &c);
+  double sc = 1.0 / sqrt((double)n);
+  W[(size_t)j * n + x] = make_float2((float)(c * sc), (float)(s * sc));
+}
+
+// Deterministic single-block sum of n doubles into out[0].
+__global__ void k_sum(const double* in, int n, double* out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += in[i];
+  double t = block_sum(acc, red);
+  if (threadIdx.x == 0) *out = t;
+}
+
+// ||x||^2 of a complex64 array in double, single block.
+__global__ void k_sumsq(const float2* x, int n, double* out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += cabs2(to_d(x[i]));
+  double t = block_sum(acc, red);
+  if (threadIdx.x == 0) *out = t;
+}
+
+// ---------------------------------------------------------------------------
+// handle lifetime
+// ---------------------------------------------------------------------------
+extern "C" void pdf_config_default(pdf_config* c) {
+  if (!c) return;
+  memset(c, 0, sizeof(*c));
+  c->k0 = 2.0 * M_PI;
+  c->beta_re = 6.0;
+  c->lambda_bound = 1e-3;
+  c->lambda_tv = 1e-5;
+  c->lambda_bridge = 1e-5;
+  c->tau_b = 0.5;
+  c->eps_tv = 1e-8;
+  c->eps_abs = 1e-12;
+  c->q_min = 1e-6;
+}
+
+static void free_all(pdf_problem* h) {
+  if (!h) return;
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->esca_host_pinned) cudaFreeHost(h->esca_host_pinned);
+  delete h;
+}
+
+template <typename T>
+static pdf_status dalloc(pdf_problem* h, T** p, size_t n) {
+  void* q = nullptr;
+  size_t bytes = n * sizeof(T);
+  if (bytes == 0) bytes = 256;
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) return cuda_err(e, "cudaMalloc(workspace)");
+  h->allocs.push_back(q);
+  *p = (T*)q;
+  return PDF_OK;
+}
+
+#define TRY(x)                      \
+  do {                              \
+    pdf_status _s = (x);            \
+    if (_s != PDF_OK) {             \
+      free_all(h);                  \
+      return _s;                    \
+    }                               \
+  } while (0)
+
+static pdf_status validate(const pdf_config* c) {
+  if (!c) return set_err(PDF_EINVAL, "config is NULL");
+  if (c->nx < 2 || c->ny < 2) return set_err(PDF_EINVAL, "nx, ny must be >= 2");
+  if (c->nx > 256 || c->ny > 256) return set_err(PDF_EUNSUPPORTED, "nx, ny above 256 are not supported");
+  if (c->ni < 1 || c->nr < 1 || c->ni > 1024 || c->nr > 1024)
+    return set_err(PDF_EINVAL, "ni, nr must be in [1, 1024]");
+  if (c->kx < 1 || c->ky < 1 || c->kx > c->nx || c->ky > c->ny)
+    return set_err(PDF_EINVAL, "Fourier truncation must satisfy 1 <= kx <= nx, 1 <= ky <= ny");
+  if (c->kx > 64 || c->ky > 64) return set_err(PDF_EUNSUPPORTED, "kx, ky above 64 are not supported");
+  if (!(c->side_x > 0) || !(c->side_y > 0) || !(c->k0 > 0)) return set_err(PDF_EINVAL, "side and k0 must be > 0");
+  if (!c->tx_xy || !c->rx_xy) return set_err(PDF_EINVAL, "antenna arrays are NULL");
+  if (!(c->beta_re > 0)) return set_err(PDF_EINVAL, "Re beta must be > 0 (contractive CIE, Eq. 7)");
+  if (c->inc_kind != 0 && c->inc_kind != 1) return set_err(PDF_EINVAL, "inc_kind must be 0 or 1");
+  if (c->precision != 0 && c->precision != 1) return set_err(PDF_EINVAL, "precision must be 0 or 1");
+  if (c->tau_b <= 0 || c->eps_tv < 0 || c->eps_abs < 0 || c->q_min < 0)
+    return set_err(PDF_EINVAL, "tau_b > 0 and non-negative eps/q_min required");
+  int M = c->nx * c->ny;
+  if ((M + GS_CHUNK - 1) / GS_CHUNK > PDF_LP_STRIDE) return set_err(PDF_EUNSUPPORTED, "grid too large");
+  return PDF_OK;
+}
+
+extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esca_on_device, void* stream,
+                                pdf_problem** out) {
+  if (!out) return set_err(PDF_EINVAL, "out is NULL");
+  *out = nullptr;
+  pdf_status st = validate(cfg);
+  if (st != PDF_OK) return st;
+  static std::once_flag once;
+  static pdf_status cfg_status = PDF_OK;
+  std::call_once(once, [] { cfg_status = hp_configure_kernels(); });
+  if (cfg_status != PDF_OK) return cfg_status;
+
+  cudaStream_t s = (cudaStream_t)stream;
+  pdf_problem* h = new pdf_problem();
+  memset(&h->d, 0, sizeof(h->d));
+  h->cfg = *cfg;
+  h->tx.assign(cfg->tx_xy, cfg->tx_xy + 2 * cfg->ni);
+  h->rx.assign(cfg->rx_xy, cfg->rx_xy + 2 * cfg->nr);
+  h->cfg.tx_xy = nullptr;
+  h->cfg.rx_xy = nullptr;
+  h->alpha = h->grad = nullptr;
+  h->esca_host_pinned = nullptr;
+  h->graph_exec = nullptr;
+  h->cap_stream = nullptr;
+  h->graph_iters = 0;
+  h->graph_kernels = 0;
+  cudaGetDevice(&h->dev_id);
+
+  Dev& d = h->d;
+  d.nx = cfg->nx;
+  d.ny = cfg->ny;
+  d.ni = cfg->ni;
+  d.nr = cfg->nr;
+  d.kx = cfg->kx;
+  d.ky = cfg->ky;
+  d.M = d.nx * d.ny;
+  d.Px = next_smooth(2 * d.nx);
+  d.Py = next_smooth(2 * d.ny);
+  if (d.Px > PDF_MAX_P || d.Py > PDF_MAX_P || !make_fft_plan(d.Px, &d.plx) || !make_fft_plan(d.Py, &d.ply)) {
+    free_all(h);
+    return set_err(PDF_EUNSUPPORTED, "padded FFT length unsupported");
+  }
+  d.beta = make_float2((float)cfg->beta_re, (float)cfg->beta_im);
+  d.betad = make_double2(cfg->beta_re, cfg->beta_im);
+  d.lam_bound = (float)cfg->lambda_bound;
+  d.lam_tv = (float)cfg->lambda_tv;
+  d.lam_bridge = (float)cfg->lambda_bridge;
+  d.tau_b = (float)cfg->tau_b;
+  d.eps_tv = (float)cfg->eps_tv;
+  d.eps_abs = (float)cfg->eps_abs;
+  d.q_min = (float)cfg->q_min;
+  d.n_gs_chunks = (d.M + GS_CHUNK - 1) / GS_CHUNK;
+  d.n_reg_blocks = (d.M + 255) / 256;
+  if ((st = hp_check_limits(d)) != PDF_OK) {
+    free_all(h);
+    return st;
+  }
+
+  const size_t M = d.M, NI = d.ni, NR = d.nr, NA = (size_t)d.ni * d.ky * d.kx;
+  float2 *twx, *twy, *ghat, *einc, *gs, *wx, *wy, *esca_d;
+  double *norms, *twxd, *twyd, *part;
+  double2* gker;
+  TRY(dalloc(h, &twx, d.Px));
+  TRY(dalloc(h, &twy, d.Py));
+  TRY(dalloc(h, &twxd, 2 * d.Px));
+  TRY(dalloc(h, &twyd, 2 * d.Py));
+  TRY(dalloc(h, &ghat, (size_t)d.Px * d.Py));
+  TRY(dalloc(h, &gker, (size_t)d.Px * d.Py));
+  TRY(dalloc(h, &einc, NI * M));
+  TRY(dalloc(h, &gs, NR * M));
+  TRY(dalloc(h, &wx, (size_t)d.kx * d.nx));
+  TRY(dalloc(h, &wy, (size_t)d.ky * d.ny));
+  TRY(dalloc(h, &esca_d, NI * NR));
+  TRY(dalloc(h, &norms, 2));
+  TRY(dalloc(h, &part, NI * d.ny));
+  TRY(dalloc(h, &d.J, NI * M));
+  TRY(dalloc(h, &d.A, NI * d.ny * (size_t)d.Px));
+  TRY(dalloc(h, &d.s, NI * M));
+  TRY(dalloc(h, &d.r, NI * M));
+  TRY(dalloc(h, &d.v, NI * M));
+  TRY(dalloc(h, &d.gsh, NI * M));
+  TRY(dalloc(h, &d.R, M));
+  TRY(dalloc(h, &d.chi, M));
+  TRY(dalloc(h, &d.w, M));
+  TRY(dalloc(h, &d.D, M));
+  TRY(dalloc(h, &d.clamp, M));
+  TRY(dalloc(h, &d.T2, NI * d.ny * (size_t)d.kx));
+  TRY(dalloc(h, &d.gspart, (size_t)d.n_gs_chunks * NI * NR));
+  TRY(dalloc(h, &d.rd, NI * NR));
+  TRY(dalloc(h, &d.lpart, (size_t)LP_NSLOT * PDF_LP_STRIDE));
+  TRY(dalloc(h, &h->alpha, NA));
+  TRY(dalloc(h, &h->grad, NA));
+  TRY(dalloc(h, &h->adam_m, 2 * NA));
+  TRY(dalloc(h, &h->adam_v, 2 * NA));
+  TRY(dalloc(h, &h->adam_t, 1));
+  TRY(dalloc(h, &h->terms, 8));
+  TRY(dalloc(h, &h->scratch_d, 64));
+  TRY(dalloc(h, &h->tmpA, NI * M));
+  TRY(dalloc(h, &h->tmpB, NI * M));
+  TRY(dalloc(h, &h->tmpC, NI * M));
+  TRY(dalloc(h, &h->field1, M));
+  TRY(dalloc(h, &h->field2, M));
+  TRY(dalloc(h, &h->field3, M));
+  TRY(dalloc(h, &h->small1, NI * NR));
+  TRY(dalloc(h, &h->cco_ab, M));
+  TRY(dalloc(h, &h->small2, NI * NR));
+  {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      free_all(h);
+      return cuda_err(e, "cudaStreamCreate(capture)");
+    }
+  }
+  {
+    cudaError_t e = cudaMallocHost((void**)&h->esca_host_pinned, NI * NR * sizeof(float2));
+    if (e != cudaSuccess) {
+      free_all(h);
+      return cuda_err(e, "cudaMallocHost(esca staging)");
+    }
+  }
+  cudaMemsetAsync(d.lpart, 0, sizeof(double) * LP_NSLOT * PDF_LP_STRIDE, s);
+
+  double* txd;
+  double* rxd;
+  TRY(dalloc(h, &txd, 2 * NI));
+  TRY(dalloc(h, &rxd, 2 * NR));
+  {
+    cudaError_t e1 = cudaMemcpyAsync(txd, h->tx.data(), 2 * NI * sizeof(double), cudaMemcpyHostToDevice, s);
+    cudaError_t e2 = cudaMemcpyAsync(rxd, h->rx.data(), 2 * NR * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      free_all(h);
+      return cuda_err(e1 != cudaSuccess ? e1 : e2, "cudaMemcpyAsync(antennas)");
+    }
+  }
+
+  const double dx = cfg->side_x / cfg->nx, dy = cfg->side_y / cfg->ny;
+  const double a = sqrt(dx * dy / M_PI);
+  // twiddles
+  k_twiddles<<<(d.Px + 127) / 128, 128, 0, s>>>((double2*)twxd, twx, d.Px);
+  k_twiddles<<<(d.Py + 127) / 128, 128, 0, s>>>((double2*)twyd, twy, d.Py);
+  // G_D kernel and its FP64 spectrum
+  k_green_kernel<<<dim3((d.Px + 127) / 128, d.Py), 128, 0, s>>>(gker, d.nx, d.ny, d.Px, d.Py, dx, dy, cfg->k0, a);
+  {
+    const int ROWS = 4, COLS = 4;
+    size_t sm_r = 2 * ROWS * (size_t)d.Px * sizeof(double2);
+    size_t sm_c = 2 * COLS * (size_t)d.Py * sizeof(double2);
+    cudaFuncSetAttribute(k_fft_rows_d<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_r);
+    cudaFuncSetAttribute(k_fft_cols_d<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c);
+    k_fft_rows_d<ROWS><<<(d.Py + ROWS - 1) / ROWS, 256, sm_r, s>>>(gker, d.Py, d.plx, (const double2*)twxd);
+    k_fft_cols_d<COLS><<<(d.Px + COLS - 1) / COLS, 256, sm_c, s>>>(gker, ghat, d.Px, d.ply, (const double2*)twyd,
+                                                                    1.0 / ((double)d.Px * d.Py));
+  }
+  k_einc<<<dim3(d.ny, d.ni), 128, 0, s>>>(einc, part, txd, d.nx, d.ny, cfg->side_x, cfg->side_y, cfg->k0,
+                                          cfg->inc_kind);
+  k_sum<<<1, 1024, 0, s>>>(part, d.ni * d.ny, norms);
+  k_gs<<<dim3((d.M + 255) / 256, d.nr), 256, 0, s>>>(gs, rxd, d.nx, d.ny, cfg->side_x, cfg->side_y, cfg->k0, a);
+  k_synth_table<<<dim3((d.nx + 127) / 128, d.kx), 128, 0, s>>>(wx, d.kx, d.nx);
+  k_synth_table<<<dim3((d.ny + 127) / 128, d.ky), 128, 0, s>>>(wy, d.ky, d.ny);
+  pdf_count_launch(10);
+  {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      free_all(h);
+      return cuda_err(e, "setup assembly kernels");
+    }
+  }
+  d.twx = twx;
+  d.twy = twy;
+  d.ghat = ghat;
+  d.einc = einc;
+  d.gs = gs;
+  d.wx = wx;
+  d.wy = wy;
+  d.esca = esca_d;
+  d.norms = norms;
+  cudaMemsetAsync(esca_d, 0, NI * NR * sizeof(float2), s);
+  if (esca) {
+    st = pdf_set_data(h, esca, esca_on_device, stream);
+    if (st != PDF_OK) {
+      free_all(h);
+      return st;
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    free_all(h);
+    return cuda_err(e, "pdf_setup synchronise");
+  }
+  *out = h;
+  return PDF_OK;
+}
+
+extern "C" pdf_status pdf_set_data(pdf_problem* h, const void* esca, int on_device, void* stream) {
+  if (!h || !esca) return set_err(PDF_EINVAL, "handle or esca is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)h->d.ni * h->d.nr;
+  float2* dst = const_cast<float2*>(h->d.esca);
+  if (on_device) {
+    PDF_CUDA(cudaMemcpyAsync(dst, esca, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  } else {
+    // stage through the pinned buffer so the copy is asynchronous; wait for earlier use first
+    PDF_CUDA(cudaStreamSynchronize(s));
+    memcpy(h->esca_host_pinned, esca, n * sizeof(float2));
+    PDF_CUDA(cudaMemcpyAsync(dst, h->esca_host_pinned, n * sizeof(float2), cudaMemcpyHostToDevice, s));
+  }
+  k_sumsq<<<1, 1024, 0, s>>>(dst, (int)n, const_cast<double*>(h->d.norms) + 1);
+  pdf_count_launch(1);
+  PDF_LAUNCHED("pdf_set_data");
+  return PDF_OK;
+}
+
+extern "C" void pdf_destroy(pdf_problem* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  free_all(h);
+}
+
+extern "C" pdf_status pdf_loss_grad(pdf_problem* h, const void* alpha, void* grad, double* terms, void* stream) {
+  if (!h || !alpha) return set_err(PDF_EINVAL, "handle or alpha is NULL");
+  return hp_loss_grad(h, (const float2*)alpha, (float2*)grad, terms, (cudaStream_t)stream);
+}
+
+extern "C" pdf_status pdf_apply_op(pdf_problem* h, int op, const void* in, void* out, void* stream) {
+  if (!h || !out || (!in && op != PDF_OP_EINC)) return set_err(PDF_EINVAL, "handle, in or out is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const float2* x = (const float2*)in;
+  float2* y = (float2*)out;
+  switch (op) {
+    case PDF_OP_GD: return hp_gd(h, x, y, 0, s);
+    case PDF_OP_GDH: return hp_gd(h, x, y, 1, s);
+    case PDF_OP_GS: return hp_gs(h, x, y, nullptr, nullptr, s);
+    case PDF_OP_GSH: return hp_gsh(h, x, y, 1.0f, s);
+    case PDF_OP_SYN: return hp_synth(h, x, y, s);
+    case PDF_OP_ANA: return hp_analysis(h, x, y, s);
+    case PDF_OP_CCO: return sv_cco(h, x, y, 2, 1e-2, 0.1, 3.0, 0.5, s);
+    case PDF_OP_CHI: return hp_chi(h, x, y, s);
+    case PDF_OP_EINC:
+      PDF_CUDA(cudaMemcpyAsync(y, h->d.einc, sizeof(float2) * h->d.ni * h->d.M, cudaMemcpyDeviceToDevice, s));
+      return PDF_OK;
+    default: return set_err(PDF_EINVAL, "unknown op");
+  }
+}
+
+extern "C" void pdf_solve_opts_default(pdf_solve_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->iters = 300;
+  o->init = 0;
+  o->lr = 1e-2;
+  o->adam_b1 = 0.9;
+  o->adam_b2 = 0.999;
+  o->adam_eps = 1e-8;
+  o->apply_cco = 1;
+  o->cco_radius = 2;
+  o->cco_eps = 1e-2;
+  o->cco_eta_max = 0.1;
+  o->cco_tau = 3.0;
+  o->cco_delta = 0.5;
+  o->use_graph = 1;
+}
+
+extern "C" pdf_status pdf_solve(pdf_problem* h, const pdf_solve_opts* o, void* chi_out, void* chi_raw_out,
+                                void* alpha_out, pdf_solve_report* rep, void* stream) {
+  if (!h || !o) return set_err(PDF_EINVAL, "handle or opts is NULL");
+  if (o->iters < 0) return set_err(PDF_EINVAL, "iters must be >= 0");
+  if (o->init == 1 && !o->alpha0) return set_err(PDF_EINVAL, "init == 1 needs alpha0");
+  if (o->init < 0 || o->init > 2) return set_err(PDF_EINVAL, "init must be 0, 1 or 2");
+  if (o->history_every > 0 && !o->history) return set_err(PDF_EINVAL, "history_every > 0 needs history");
+  if (o->apply_cco && (o->cco_radius < 0 || o->cco_radius > 16 || o->cco_eps <= 0))
+    return set_err(PDF_EINVAL, "cco_radius must be in [0, 16] and cco_eps > 0");
+  return sv_solve(h, o, (float2*)chi_out, (float2*)chi_raw_out, (float2*)alpha_out, rep, (cudaStream_t)stream);
+}
+
+extern "C" pdf_status pdf_forward(pdf_problem* h, const void* chi, void* esca_out, void* j_out, double tol,
+                                  int32_t max_iter, int32_t* iters_out, void* stream) {
+  if (!h || !chi || !esca_out) return set_err(PDF_EINVAL, "handle, chi or esca_out is NULL");
+  if (!(tol > 0) || max_iter < 1) return set_err(PDF_EINVAL, "tol must be > 0 and max_iter >= 1");
+  return sv_forward(h, (const float2*)chi, (float2*)esca_out, (float2*)j_out, tol, max_iter, iters_out,
+                    (cudaStream_t)stream);
+}

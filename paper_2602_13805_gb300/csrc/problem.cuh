@@ -1,0 +1,126 @@
+// Internal state of a pdf_problem handle and the by-value kernel parameter block.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+// Loss-partial slots (each a strip of PDF_LP_STRIDE doubles in Dev::lpart).
+enum { LP_STATE = 0, LP_DATA = 1, LP_BOUND = 2, LP_TV = 3, LP_BRIDGE = 4, LP_NSLOT = 5 };
+#define PDF_LP_STRIDE 4096
+
+#define ROWS_PER_CTA 4        // rows handled by one CTA of the row-FFT kernels
+#define ROW_THREADS 128
+#define COL_CW 16             // columns per CTA of the column-convolution kernel
+#define COL_THREADS 256
+#define GS_CHUNK 256          // pixels per CTA of the G_S partial-product kernel
+#define GSH_CHUNK 64          // pixels per CTA of the G_S^H kernel
+
+// Everything a kernel needs, passed by value.
+struct Dev {
+  int nx, ny, ni, nr, kx, ky, M, Px, Py;
+  FFTPlan plx, ply;
+  float2 beta;
+  double2 betad;
+  float lam_bound, lam_tv, lam_bridge, tau_b, eps_tv, eps_abs, q_min;
+  int n_gs_chunks, n_reg_blocks;
+
+  // geometry (assembled once)
+  const float2* twx;     // [Px] exp(-2 pi i e / Px)
+  const float2* twy;     // [Py]
+  const float2* ghat;    // [Py][Px] spectrum of the circulant G_D kernel / (Px Py)
+  const float2* einc;    // [ni][M]
+  const float2* gs;      // [nr][M]
+  const float2* wx;      // [kx][nx] exp(+2 pi i f_k x / nx) / sqrt(nx)
+  const float2* wy;      // [ky][ny]
+  const float2* esca;    // [ni][nr]
+  const double* norms;   // [2] ||E_inc||^2, ||E_sca||^2
+
+  // per-iteration workspace
+  float2* J;             // [ni][M]
+  float2* A;             // [ni][ny][Px] row-transformed padded planes
+  float2* s;             // [ni][M] beta J + E_inc + G_D J
+  float2* r;             // [ni][M] state residual
+  float2* v;             // [ni][M] pointwise part of dL/dJ
+  float2* gsh;           // [ni][M] scaled G_S^H r_d
+  float2* R;             // [M]
+  float2* chi;           // [M]
+  float2* w;             // [M] regulariser cotangent on R divided by D
+  float* D;              // [M] sum_p |s|^2
+  unsigned char* clamp;  // [M]
+  float2* T2;            // [ni][ny][kx] partial analysis
+  float2* gspart;        // [n_gs_chunks][ni][nr]
+  float2* rd;            // [ni][nr] data residual
+  double* lpart;         // [LP_NSLOT][PDF_LP_STRIDE]
+};
+
+struct pdf_problem {
+  pdf_config cfg;
+  std::vector<double> tx, rx;
+  Dev d;
+  int dev_id;
+  // owned device memory
+  std::vector<void*> allocs;
+  // solve state
+  float2* alpha;         // [ni][ky][kx]
+  float2* grad;
+  float* adam_m;         // [2 * ni * ky * kx]
+  float* adam_v;
+  int* adam_t;           // device step counter
+  double* terms;         // [6] device
+  double* scratch_d;     // [64] device doubles for init/solve scalars
+  float2* tmpA;          // [ni][M] scratch fields for init / ops
+  float2* tmpB;
+  float2* tmpC;
+  float2* field1;        // [M]
+  float2* field2;
+  float2* field3;
+  float2* esca_host_pinned;  // pinned staging [ni][nr]
+  float4* cco_ab;        // [M] guided-filter coefficients
+  float2* small1;        // [ni][nr] scratch
+  float2* small2;
+  cudaStream_t cap_stream;   // private stream used only for graph capture
+  cudaGraphExec_t graph_exec;
+  int graph_iters;       // iterations per graph launch (0 = none)
+  int graph_kernels;     // kernel nodes in the graph
+  double graph_key[4];   // lr, b1, b2, eps used when captured
+};
+
+// error helpers (api.cu)
+pdf_status set_err(pdf_status st, const std::string& msg);
+pdf_status cuda_err(cudaError_t e, const char* where);
+#define PDF_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t _e = (call);                            \
+    if (_e != cudaSuccess) return cuda_err(_e, #call);  \
+  } while (0)
+#define PDF_LAUNCHED(where)                                         \
+  do {                                                              \
+    cudaError_t _e = cudaGetLastError();                            \
+    if (_e != cudaSuccess) return cuda_err(_e, where);              \
+  } while (0)
+
+// reductions defined in api.cu
+__global__ void k_sumsq(const float2* x, int n, double* out);
+
+// launchers (hotpath.cu)
+pdf_status hp_configure_kernels();
+pdf_status hp_check_limits(const Dev& d);
+pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, double* terms, cudaStream_t st,
+                        int* step_inc = nullptr);
+pdf_status hp_gd(pdf_problem* h, const float2* in, float2* out, int adjoint, cudaStream_t st);
+pdf_status hp_gs(pdf_problem* h, const float2* in, float2* out, const float2* subtract, double* sumsq, cudaStream_t st);
+pdf_status hp_gsh(pdf_problem* h, const float2* in, float2* out, float scale, cudaStream_t st);
+pdf_status hp_synth(pdf_problem* h, const float2* alpha, float2* out, cudaStream_t st);
+pdf_status hp_analysis(pdf_problem* h, const float2* in, float2* out, cudaStream_t st);
+pdf_status hp_chi(pdf_problem* h, const float2* alpha, float2* chi_out, cudaStream_t st);
+int hp_kernels_per_loss_grad(const pdf_problem* h);
+
+// solve pieces (solve.cu)
+pdf_status sv_cco(pdf_problem* h, const float2* chi, float2* out, int radius, double eps, double eta_max,
+                  double tau, double delta, cudaStream_t st);
+pdf_status sv_solve(pdf_problem* h, const pdf_solve_opts* o, float2* chi_out, float2* chi_raw_out,
+                    float2* alpha_out, pdf_solve_report* rep, cudaStream_t st);
+pdf_status sv_forward(pdf_problem* h, const float2* chi, float2* esca_out, float2* j_out, double tol,
+                      int max_iter, int* iters_out, cudaStream_t st);

@@ -1,0 +1,171 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
+
+Tolerance for the FP32 path: norm-wise relative error <= 1e-5 for operators, the loss
+and its gradient (the contract's FP32 bound).
+"""
+import numpy as np
+import pytest
+
+import scenes
+from oracle import fbe, loss, solve
+from oracle.problem import from_workload
+from tests.gpu_common import SMALL_CASES, TOL_FP32, Case, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _w(name, over):
+    base = "c1" if name != "c2" else "c2"
+    return scenes.workload(base, **over)
+
+
+@pytest.fixture(scope="module", params=SMALL_CASES + [("c2", dict())], ids=lambda c: c[0])
+def case(request):
+    name, over = request.param
+    c = Case(_w(name, over))
+    c.prob = c.problem()
+    yield c
+    c.prob.close()
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def test_operators(case):
+    from paper_2602_13805_gb300 import pdf
+    p, ops, prob = case.p, case.ops, case.prob
+    rng = np.random.default_rng(3)
+    x = (rng.standard_normal((p.ni, p.ny, p.nx)) + 1j * rng.standard_normal((p.ni, p.ny, p.nx))).astype(np.complex64)
+    d = (rng.standard_normal((p.ni, p.nr)) + 1j * rng.standard_normal((p.ni, p.nr))).astype(np.complex64)
+    a = case.alpha()
+    xd, dd, ad = _dev(x), _dev(d), _dev(a)
+    x64, d64, a64 = x.astype(complex), d.astype(complex), a.astype(complex)
+    checks = {
+        "EINC": (prob.op(pdf.OP_EINC, xd), ops.Einc),
+        "GD": (prob.op(pdf.OP_GD, xd), ops.gd(x64)),
+        "GDH": (prob.op(pdf.OP_GDH, xd), ops.gd(x64, adjoint=True)),
+        "GS": (prob.op(pdf.OP_GS, xd), ops.gs(x64)),
+        "GSH": (prob.op(pdf.OP_GSH, dd), ops.gsh(d64)),
+        "SYN": (prob.op(pdf.OP_SYN, ad), fbe.synth(a64, p.ny, p.nx)),
+        "ANA": (prob.op(pdf.OP_ANA, xd), fbe.analysis(x64, p.ky, p.kx)),
+    }
+    for k, (gpu, ref) in checks.items():
+        e = rel(gpu.cpu().numpy(), ref)
+        assert e < TOL_FP32, f"{k}: rel err {e:.2e}"
+
+
+def test_chi_and_cco(case):
+    from paper_2602_13805_gb300 import pdf
+    p, ops, prob = case.p, case.ops, case.prob
+    a = case.alpha()
+    chi_gpu = prob.op(pdf.OP_CHI, _dev(a)).cpu().numpy()
+    f = loss.forward(ops, case.esca, a.astype(complex))
+    assert rel(chi_gpu, f.chi) < 1e-4
+    # CCO on the oracle's chi, both sides the same input
+    cin = f.chi.astype(np.complex64)
+    cco_gpu = prob.op(pdf.OP_CCO, _dev(cin)).cpu().numpy()
+    assert rel(cco_gpu, solve.cco(cin.astype(complex))) < 1e-5
+
+
+@pytest.mark.parametrize("scale", [0.3, 1.0])
+def test_loss_and_gradient(case, scale):
+    p, ops, prob = case.p, case.ops, case.prob
+    a = case.alpha(scale=scale, seed=7)
+    terms, grad = prob.loss_grad(_dev(a))
+    t_ref, g_ref = loss.loss_grad(ops, case.esca, a.astype(complex))
+    t = terms.cpu().numpy()
+    for k, name in enumerate(("L", "State", "Data")):
+        assert abs(t[k] - t_ref[k]) <= TOL_FP32 * abs(t_ref[k]), f"{name}: {t[k]} vs {t_ref[k]}"
+    # regularisers are computed on chi-hat, whose FP32 error is amplified near R = 1; 1e-4 there
+    for k, name in ((3, "Bound"), (4, "TV"), (5, "Bridge")):
+        assert abs(t[k] - t_ref[k]) <= 1e-4 * max(abs(t_ref[k]), 1e-6), f"{name}: {t[k]} vs {t_ref[k]}"
+    e = rel(grad.cpu().numpy(), g_ref)
+    assert e < TOL_FP32, f"gradient rel err {e:.2e}"
+
+
+def test_gradient_heavy_regularisers():
+    # large regulariser weights so the chi(R(J)) chain rule dominates the gradient
+    w = scenes.workload("c1", nx=24, ny=20, ni=5, nr=7, kx=7, ky=5)
+    c = Case(w)
+    kw = dict(lambda_bound=1.0, lambda_tv=0.3, lambda_bridge=0.5)
+    prob = c.problem(**kw)
+    c.p.lam_bound, c.p.lam_tv, c.p.lam_bridge = 1.0, 0.3, 0.5
+    a = c.alpha(seed=11)
+    terms, grad = prob.loss_grad(_dev(a))
+    t_ref, g_ref = loss.loss_grad(c.ops, c.esca, a.astype(complex))
+    assert abs(terms[0].item() - t_ref[0]) <= 1e-4 * abs(t_ref[0])
+    assert rel(grad.cpu().numpy(), g_ref) < 1e-4
+    prob.close()
+
+
+def test_autograd_function_and_central_differences(case):
+    from paper_2602_13805_gb300 import pdf
+    prob = case.prob
+    a = torch.tensor(case.alpha(seed=5), device="cuda", requires_grad=True)
+    L = pdf.pdf_loss(a, prob)
+    L.backward()
+    _, g = prob.loss_grad(a.detach())
+    assert torch.equal(a.grad, g)
+    # central differences of the FP64-reduced loss along a random direction (h = 1e-4 relative)
+    rng = np.random.default_rng(9)
+    d = torch.tensor(scenes.random_coeffs(*a.shape, 1.0, rng).astype(np.complex64), device="cuda")
+    h = 1e-4 * a.detach().abs().max().item() / d.abs().max().item()
+    tp, _ = prob.loss_grad((a.detach() + h * d).contiguous())
+    tm, _ = prob.loss_grad((a.detach() - h * d).contiguous())
+    fd = (tp[0] - tm[0]).item() / (2 * h)
+    an = torch.sum(torch.real(torch.conj(g) * d)).item()
+    assert abs(fd - an) < 2e-3 * abs(an) + 1e-6
+
+
+def test_forward_solver_matches_oracle(case):
+    from oracle.forward import forward_solve
+    p, ops, prob = case.p, case.ops, case.prob
+    esca_gpu, J_gpu, it = prob.forward(_dev(case.chi.astype(np.complex64)), tol=1e-6, max_iter=3000)
+    J_ref, _, esca_ref = forward_solve(ops, case.chi)
+    assert rel(esca_gpu.cpu().numpy(), esca_ref) < 1e-4
+    assert rel(J_gpu.cpu().numpy(), J_ref) < 1e-4
+
+
+def test_init_matches_oracle(case):
+    # BP + exact-line-search CSI step (Eq. 12): alpha_0 from both sides
+    p, ops, prob = case.p, case.ops, case.prob
+    out = prob.solve(iters=0, apply_cco=False)
+    _, R0, _ = solve.bp_init(ops, case.esca)
+    a0 = solve.csi_step(ops, case.esca, R0)
+    assert rel(out["alpha"].cpu().numpy(), a0) < 1e-4
+
+
+def test_solve_parity_relerr():
+    # whole reconstruction: GPU (FP32, graph) vs oracle (FP64); compare RelErr and loss
+    w = scenes.workload("c1", iters=60)
+    c = Case(w)
+    prob = c.problem()
+    chi_t = _dev(c.chi.astype(np.complex64))
+    out = prob.solve(iters=w.iters, chi_true=chi_t, use_graph=True)
+    ref = solve.pdf_solve(c.ops, c.esca, w.iters, chi_true=c.chi)
+    assert abs(out["relerr"] - ref["relerr"]) < 1e-3
+    assert abs(out["relerr_cco"] - ref["relerr_cco"]) < 1e-3
+    # eager and graph runs agree bit for bit (same kernels, same order)
+    out2 = prob.solve(iters=w.iters, chi_true=chi_t, use_graph=False)
+    assert torch.equal(out["alpha"], out2["alpha"])
+    prob.close()
+
+
+def test_torch_adam_matches_library_adam():
+    # the spec outer-optimiser form (torch.optim.Adam over PDFLossGrad) vs pdf_solve's own Adam
+    from paper_2602_13805_gb300 import pdf
+    w = scenes.workload("c1", iters=20)
+    c = Case(w)
+    prob = c.problem()
+    a0 = torch.tensor(c.alpha(scale=0.2, seed=2), device="cuda")
+    out = prob.solve(iters=20, init=1, alpha0=a0, apply_cco=False, use_graph=False)
+    a = a0.clone().requires_grad_(True)
+    opt = torch.optim.Adam([a], lr=1e-2)
+    for _ in range(20):
+        opt.zero_grad()
+        pdf.pdf_loss(a, prob).backward()
+        opt.step()
+    assert rel(a.detach().cpu().numpy(), out["alpha"].cpu().numpy()) < 1e-5
+    prob.close()

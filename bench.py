@@ -1,0 +1,350 @@
+"""Benchmark: one PDF reconstruction per step on a synthetic scene (GPU, C ABI).
+
+A step is one whole reconstruction of the workload (default: 64x64 grid over a
+2-lambda DOI, 16 line-source incidences, 32 receivers on a 5-lambda circle, two
+nearly touching disks eps_r = 3.5, 10 % AWGN, K = 15 x 15 Fourier coefficients,
+BP + CSI initialisation, 300 Adam iterations, CCO post-processing).  Measured data
+are synthesised on the GPU by the library's own forward solver (pdf_forward);
+the scene and the noise come from the seeded input generators.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2] [--impl ours|reference]
+
+N > 1 (torchrun): independent replicas, one scene per rank, no data-path collective
+("replicas only"); the timing is the max over ranks.  `--impl reference` times the
+FP64 CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import scenes  # noqa: E402
+
+METRIC = "ms per PDF reconstruction"
+L2_BYTES = 129 * 1024 * 1024
+FLUSH_BYTES = 512 * 1024 * 1024
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """Samples nvidia-smi every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def bytes_model(w):
+    """Algorithmic bytes per launch of the column-convolution kernel (the largest FFT stage).
+
+    Reads and writes the row-transformed planes [ni][ny][Px] once each and reads the
+    kernel spectrum [Py][Px] once: 2 * ni * ny * Px * 8 + Px * Py * 8 bytes.
+    """
+    px = next_smooth(2 * w.nx)
+    py = next_smooth(2 * w.ny)
+    return 2 * w.ni * w.ny * px * 8 + px * py * 8
+
+
+def next_smooth(n):
+    best = 1 << 30
+    p2 = 1
+    while p2 < (1 << 20):
+        p = p2
+        while p < (1 << 20):
+            if n <= p < best:
+                best = p
+            p *= 3
+        p2 *= 2
+    return best
+
+
+def kernel_bytes(w):
+    """Algorithmic DRAM bytes per launch of each hot-path kernel (c64 = 8 bytes).
+
+    U = ni*M*8 (one field over all incidences), A = ni*ny*Px*8 (row-transformed planes).
+    """
+    px, py = next_smooth(2 * w.nx), next_smooth(2 * w.ny)
+    M = w.nx * w.ny
+    U = w.ni * M * 8
+    A = w.ni * w.ny * px * 8
+    GS = w.nr * M * 8
+    return {
+        "k_synth_rowfft": U + A + w.ni * w.kx * w.ky * 8,       # write J, write A, read alpha
+        "k_colconv": 2 * A + px * py * 8,                      # read + write A, read spectrum
+        "k_rowifft_state": A + 4 * U + 4 * M * 8,              # read A, J, E_inc; write s, r; R, chi, D
+        "k_gs_partial": U + GS,                                # read J, G_S
+        "k_adj_rowfft": 4 * U + A + 2 * M * 8,                 # read J, s, r; write v; write A
+        "k_colconv(conj)": 2 * A + px * py * 8,
+        "k_gsh": GS + U,                                       # read G_S, write G_S^H r_d
+        "k_adj_rowifft_ana": A + 2 * U,                        # read A, v, gsh
+    }
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2602_13805_gb300 import pdf
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    w = scenes.workload(args.workload)
+    if args.iters is not None:
+        w = scenes.workload(args.workload, iters=args.iters)
+    seed = rank
+    chi_true = scenes.make_scene(w, seed)
+    prob = pdf.Problem.from_workload(w)
+    chi_d = torch.from_numpy(chi_true.astype(np.complex64)).cuda()
+    esca_clean, _, fwd_iters = prob.forward(chi_d, tol=1e-5, max_iter=3000)
+    esca = scenes.add_awgn(esca_clean.cpu().numpy().astype(np.complex128), w.noise,
+                           np.random.default_rng(1000 + seed)).astype(np.complex64)
+    esca_d = torch.from_numpy(esca).cuda()
+    prob.set_data(esca_d)
+    stream = torch.cuda.current_stream()
+    opts = pdf.solve_opts(iters=w.iters, lr=args.lr, init=0, chi_true=chi_d, apply_cco=1, use_graph=1)
+    chi_out = torch.empty((w.ny, w.nx), dtype=torch.complex64, device="cuda")
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        pdf.pdf_set_data(prob.h, esca_d)
+        pdf.pdf_solve(prob.h, opts, chi_out, None, None, report=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # one reported solve for RelErr / loss (outside the timed region)
+    rep = pdf.pdf_solve(prob.h, opts, chi_out, None, None, report=True)
+
+    # --- device-resident timed region -------------------------------------------------
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(torch.cuda.current_device())
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = pdf.pdf_launch_count()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()                                  # evict L2 between reconstructions (untimed)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = pdf.pdf_launch_count() - launches0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+
+    # --- end-to-end through the public API with host buffers ---------------------------
+    esca_pinned = torch.from_numpy(esca).pin_memory()
+    chi_host = torch.empty((w.ny, w.nx), dtype=torch.complex64).pin_memory()
+    esca_np = esca_pinned.numpy()
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        e2e_ev[k][0].record(stream)
+        pdf.pdf_set_data(prob.h, esca_np)              # H2D from pinned host memory
+        pdf.pdf_solve(prob.h, opts, chi_out, None, None, report=False)
+        chi_host.copy_(chi_out, non_blocking=True)     # D2H of the result
+        e2e_ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev) / args.steps
+
+    # --- per-kernel timing (CUDA events between consecutive kernels of pdf_loss_grad) ----
+    alpha_probe = torch.zeros((w.ni, w.ky, w.kx), dtype=torch.complex64, device="cuda")
+    pdf.pdf_solve(prob.h, pdf.solve_opts(iters=0, init=0, apply_cco=0), None, None, alpha_probe, report=False)
+    prof = pdf.pdf_profile_loss_grad(prob.h, alpha_probe, reps=50)
+    kb = kernel_bytes(w)
+    per_iter_ms = sum(t for _, t in prof)
+    dom_name, dom_ms = max(((n, t) for n, t in prof if n in kb), key=lambda x: x[1])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = kb[dom_name] / (dom_ms * 1e-3) / 1e9
+
+    # max over ranks
+    t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms, e2e_ms = float(t[0]), float(t[1])
+    out = None
+    if rank == 0:
+        ms_per_recon = total_ms / (args.steps * world)
+        out = {
+            "metric": METRIC, "value": ms_per_recon, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 complex), fp64 reductions",
+            "data": "synthetic (seeded scene, GPU forward solver, AWGN)",
+            "config": {"workload": f"{w.name}: {w.nx}x{w.ny} grid, {w.side} lambda DOI, Ni={w.ni}, Nr={w.nr}, "
+                                   f"K={w.kx}x{w.ky}, {w.iters} Adam iterations, BP+CSI init, CCO",
+                       "iters": w.iters, "lr": args.lr, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "flushed between reconstructions (512 MB write); working set L2-resident within one"},
+            "iters_per_s": w.iters * args.steps * world / (total_ms * 1e-3),
+            "relerr": rep.relerr, "relerr_cco": rep.relerr_cco, "final_loss": rep.terms[0],
+            "e2e": {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": int(esca.nbytes),
+                    "d2h_bytes_per_step": int(w.nx * w.ny * 8)},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None,
+                         "note": "per-launch algorithmic bytes / CUDA-event duration; the working set is "
+                                 "L2-resident so the HBM fraction is a lower bound (latency-bound sizes)",
+                         "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"},
+            "kernels_ms": {n: round(t, 5) for n, t in prof},
+            "loss_grad_ms": per_iter_ms,
+            "clocks": clk,
+            "wall_s": wall,
+            "forward_solver_iters": fwd_iters,
+        }
+        if not args.no_cpu:
+            out["cpu_baseline"] = cpu_baseline(w, args.cpu_iters)
+    prob.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
+def _oracle_case(w, seed=0):
+    from oracle.forward import forward_solve
+    from oracle.green import Operators
+    from oracle.problem import from_workload
+    p = from_workload(w)
+    ops = Operators(p)
+    chi = scenes.make_scene(w, seed)
+    _, _, esca = forward_solve(ops, chi)
+    esca = scenes.add_awgn(esca, w.noise, np.random.default_rng(1000 + seed))
+    return ops, esca, chi
+
+
+def cpu_baseline(w, iters):
+    """FP64 oracle on the host: init + `iters` Adam iterations, scaled to a full reconstruction."""
+    from oracle import loss, solve
+    ops, esca, chi = _oracle_case(w)
+    t0 = time.perf_counter()
+    _, R0, _ = solve.bp_init(ops, esca)
+    a = solve.csi_step(ops, esca, R0)
+    t_init = time.perf_counter() - t0
+    opt = solve.Adam(lr=1e-2)
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        _, g = loss.loss_grad(ops, esca, a)
+        a = opt.step(a, g)
+    t_it = (time.perf_counter() - t0) / iters
+    ms = (t_init + t_it * w.iters) * 1e3
+    return {"value": ms, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"BP+CSI init + {iters} of {w.iters} Adam iterations (FP64 NumPy/SciPy), "
+                      f"per-iteration time scaled to {w.iters}; BLAS threads default, FFTs single-threaded"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    w = scenes.workload(args.workload)
+    iters = args.cpu_iters
+    times = []
+    for k in range(args.warmup + args.steps):
+        r = cpu_baseline(w, iters)
+        if k >= args.warmup:
+            times.append(r["value"])
+    v = sum(times) / len(times)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded scene, oracle forward solver, AWGN)",
+            "config": {"workload": f"{w.name}: {w.nx}x{w.ny}, Ni={w.ni}, Nr={w.nr}, K={w.kx}x{w.ky}, "
+                                   f"{w.iters} Adam iterations"},
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"per step: BP+CSI init + {iters} Adam iterations scaled to {w.iters}"},
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--iters", type=int, default=None)
+    ap.add_argument("--lr", type=float, default=1e-2)
+    ap.add_argument("--cpu-iters", type=int, default=20)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -149,6 +149,16 @@ pdf_status pdf_solve(pdf_problem* h, const pdf_solve_opts* opts, void* chi_out, 
 pdf_status pdf_forward(pdf_problem* h, const void* chi, void* esca_out, void* j_out, double tol,
                        int32_t max_iter, int32_t* iters_out, void* stream);
 
+/* Profiling: runs pdf_loss_grad once to warm up, then `reps` times with a CUDA event between
+ * consecutive kernels on `stream`, and writes the mean milliseconds of kernel k (in launch
+ * order) to ms[k].  Returns the number of kernels K (ms needs n >= K entries) or a negative
+ * pdf_status.  Synchronises `stream`.  Does not write a gradient or loss terms for the caller. */
+int32_t pdf_profile_loss_grad(pdf_problem* h, const void* alpha, int32_t reps, float* ms, int32_t n,
+                              void* stream);
+
+/* Name of kernel k of pdf_loss_grad in launch order ("" when out of range). */
+const char* pdf_kernel_name(int32_t k);
+
 /* Number of kernels this library has launched in the calling process (graph launches count
  * every kernel node they execute).  For benchmarking evidence. */
 uint64_t pdf_launch_count(void);

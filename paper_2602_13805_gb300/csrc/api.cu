@@ -15,6 +15,7 @@
 #include <mutex>
 #include <atomic>
 #include <climits>
+#include <vector>
 
 #include "fft.cuh"
 #include "problem.cuh"
@@ -554,3 +555,37 @@ extern "C" pdf_status pdf_forward(pdf_problem* h, const void* chi, void* esca_ou
   return sv_forward(h, (const float2*)chi, (float2*)esca_out, (float2*)j_out, tol, max_iter, iters_out,
                     (cudaStream_t)stream);
 }
+
+extern "C" int32_t pdf_profile_loss_grad(pdf_problem* h, const void* alpha, int32_t reps, float* ms, int32_t n,
+                                         void* stream) {
+  const int K = hp_kernels_per_loss_grad(h);
+  if (!h || !alpha || !ms || reps < 1 || n < K) {
+    set_err(PDF_EINVAL, "pdf_profile_loss_grad: bad arguments");
+    return PDF_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<cudaEvent_t> ev(K + 1);
+  for (auto& e : ev) cudaEventCreate(&e);
+  std::vector<double> acc(K, 0.0);
+  pdf_status st = hp_loss_grad(h, (const float2*)alpha, nullptr, nullptr, s);   // warm-up
+  for (int r = 0; r < reps && st == PDF_OK; ++r) {
+    st = hp_loss_grad(h, (const float2*)alpha, nullptr, nullptr, s, nullptr, ev.data());
+    if (st != PDF_OK) break;
+    cudaError_t e = cudaEventSynchronize(ev[K]);
+    if (e != cudaSuccess) {
+      st = cuda_err(e, "pdf_profile_loss_grad");
+      break;
+    }
+    for (int k = 0; k < K; ++k) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+      acc[k] += t;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (st != PDF_OK) return st;
+  for (int k = 0; k < K; ++k) ms[k] = (float)(acc[k] / reps);
+  return K;
+}
+
+extern "C" const char* pdf_kernel_name(int32_t k) { return hp_kernel_name(k); }

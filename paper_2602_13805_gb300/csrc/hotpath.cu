@@ -669,27 +669,50 @@ pdf_status hp_check_limits(const Dev& d) {
   return PDF_OK;
 }
 
+static const char* kLossGradKernels[] = {
+    "k_synth_rowfft", "k_colconv", "k_rowifft_state", "k_gs_partial", "k_gs_reduce", "k_reg",
+    "k_adj_rowfft",   "k_colconv(conj)", "k_gsh",     "k_adj_rowifft_ana", "k_ana_y", "k_finalize"};
+
+const char* hp_kernel_name(int k) { return (k >= 0 && k < 12) ? kLossGradKernels[k] : ""; }
+
 pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, double* terms, cudaStream_t st,
-                        int* step_inc) {
+                        int* step_inc, cudaEvent_t* ev) {
   Dev& d = h->d;
   const int nout = d.ni * d.nr;
   const int n_data_blocks = (nout + 255) / 256;
+  int k = 0;
+  auto mark = [&]() {
+    if (ev) cudaEventRecord(ev[k++], st);
+  };
+  mark();
   // forward
   k_synth_rowfft<<<row_grid(d), ROW_THREADS, sm_synth(d), st>>>(d, alpha, d.J, 1);
+  mark();
   k_colconv<<<col_grid(d), COL_THREADS, sm_col(d), st>>>(d, 0);
+  mark();
   k_rowifft_state<<<d.ny, ROW_THREADS, sm_row(d), st>>>(d);
+  mark();
   k_gs_partial<<<d.n_gs_chunks, 256, sm_gs(d), st>>>(d, d.J, d.gspart);
+  mark();
   k_gs_reduce<<<n_data_blocks, 256, 0, st>>>(d, d.gspart, d.n_gs_chunks, d.esca, d.rd,
                                               d.lpart + LP_DATA * PDF_LP_STRIDE);
+  mark();
   k_reg<<<d.n_reg_blocks, 256, 0, st>>>(d);
+  mark();
   // adjoint
   k_adj_rowfft<<<row_grid(d), ROW_THREADS, sm_row(d), st>>>(d);
+  mark();
   k_colconv<<<col_grid(d), COL_THREADS, sm_col(d), st>>>(d, 1);
+  mark();
   k_gsh<<<(d.M + GSH_CHUNK - 1) / GSH_CHUNK, 256, sm_gsh(d), st>>>(d, d.rd, d.gsh, 0.f, 1);
+  mark();
   k_adj_rowifft_ana<<<row_grid(d), ROW_THREADS, sm_row(d), st>>>(d, nullptr, 0);
+  mark();
   float2* g = grad ? grad : h->grad;
   k_ana_y<<<dim3((d.ky * d.kx + 127) / 128, d.ni), 128, 0, st>>>(d, g);
+  mark();
   k_finalize<<<1, 256, 0, st>>>(d, terms ? terms : h->terms, d.ny, n_data_blocks, d.n_reg_blocks, step_inc);
+  mark();
   pdf_count_launch(12);
   PDF_LAUNCHED("pdf_loss_grad");
   return PDF_OK;

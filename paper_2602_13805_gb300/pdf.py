@@ -76,7 +76,7 @@ _lib = None
 
 EXPORTS = ("pdf_config_default", "pdf_setup", "pdf_set_data", "pdf_loss_grad", "pdf_apply_op",
            "pdf_solve_opts_default", "pdf_solve", "pdf_forward", "pdf_launch_count", "pdf_destroy",
-           "pdf_last_error")
+           "pdf_last_error", "pdf_profile_loss_grad", "pdf_kernel_name")
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -108,6 +108,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pdf_launch_count.restype = ctypes.c_uint64
     lib.pdf_destroy.argtypes = [vp]
     lib.pdf_destroy.restype = None
+    lib.pdf_profile_loss_grad.argtypes = [vp, vp, i32, ctypes.POINTER(ctypes.c_float), i32, vp]
+    lib.pdf_profile_loss_grad.restype = i32
+    lib.pdf_kernel_name.argtypes = [i32]
+    lib.pdf_kernel_name.restype = ctypes.c_char_p
     lib.pdf_last_error.argtypes = []
     lib.pdf_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -213,6 +217,16 @@ def pdf_destroy(h: int):
 
 def pdf_launch_count() -> int:
     return int(load().pdf_launch_count())
+
+
+def pdf_profile_loss_grad(h: int, alpha, reps: int = 20, stream=None):
+    """{kernel name: mean ms per launch} for the kernels of one pdf_loss_grad (CUDA events)."""
+    lib = load()
+    buf = (ctypes.c_float * 64)()
+    k = lib.pdf_profile_loss_grad(h, _ptr(alpha), reps, buf, 64, _stream(stream))
+    if k < 0:
+        _check(k)
+    return [(lib.pdf_kernel_name(i).decode(), float(buf[i])) for i in range(k)]
 
 
 def solve_opts(**kw) -> pdf_solve_opts:

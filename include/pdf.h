@@ -159,6 +159,24 @@ int32_t pdf_profile_loss_grad(pdf_problem* h, const void* alpha, int32_t reps, f
 /* Name of kernel k of pdf_loss_grad in launch order ("" when out of range). */
 const char* pdf_kernel_name(int32_t k);
 
+/* G_S x without any device allocation, for callers that cannot call cudaMalloc: code whose
+ * device memory is already owned by another allocator (a host framework's caching allocator
+ * that has reserved the GPU), or latency-critical loops where an allocation, which can
+ * synchronise the device, is not acceptable.  The paper has no counterpart: this is the
+ * handle-free form of PDF_OP_GS.
+ *   gs  [nr][m] complex64, device: the receiver operator (for example conj of PDF_OP_GSH applied
+ *       to an identity);  x [ni][m] complex64, device;  out [ni][nr] complex64, device, overwritten
+ *       with out[p][r] = sum_n gs[r][n] x[p][n].
+ * Its split-K partial sums live in a 4 MiB file-scope device array that every GPU loading the
+ * library holds until exit.  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture.  All calls share the array, so calls that overlap on the GPU race.  Nothing is
+ * allocated or freed.  Errors: PDF_EINVAL for NULL pointers, sizes < 1, or ni * nr above 524288
+ * (the array's capacity in complex64); PDF_ECUDA if the address look-up or a launch fails.
+ * Asynchronous on `stream`. */
+pdf_status pdf_gs_apply_static(const void* gs, const void* x, void* out, int32_t ni, int32_t nr, int32_t m,
+                               void* stream);
+
 /* Number of kernels this library has launched in the calling process (graph launches count
  * every kernel node they execute).  For benchmarking evidence. */
 uint64_t pdf_launch_count(void);

@@ -76,7 +76,7 @@ _lib = None
 
 EXPORTS = ("pdf_config_default", "pdf_setup", "pdf_set_data", "pdf_loss_grad", "pdf_apply_op",
            "pdf_solve_opts_default", "pdf_solve", "pdf_forward", "pdf_launch_count", "pdf_destroy",
-           "pdf_last_error", "pdf_profile_loss_grad", "pdf_kernel_name")
+           "pdf_last_error", "pdf_profile_loss_grad", "pdf_kernel_name", "pdf_gs_apply_static")
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -112,6 +112,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pdf_profile_loss_grad.restype = i32
     lib.pdf_kernel_name.argtypes = [i32]
     lib.pdf_kernel_name.restype = ctypes.c_char_p
+    lib.pdf_gs_apply_static.argtypes = [vp, vp, vp, i32, i32, i32, vp]
+    lib.pdf_gs_apply_static.restype = ctypes.c_int
     lib.pdf_last_error.argtypes = []
     lib.pdf_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -208,6 +210,13 @@ def pdf_forward(h: int, chi, esca_out, j_out=None, tol=1e-6, max_iter=2000, stre
     _check(load().pdf_forward(h, _ptr(chi), _ptr(esca_out), _ptr(j_out), tol, max_iter, ctypes.byref(it),
                               _stream(stream)))
     return it.value
+
+
+def pdf_gs_apply_static(gs, x, out, stream=None):
+    """out[p][r] = sum_n gs[r][n] x[p][n] with no device allocation (static library scratch)."""
+    nr, m = gs.shape[0], gs.shape[-1] if gs.dim() == 2 else gs.shape[1] * gs.shape[2]
+    ni = x.shape[0]
+    _check(load().pdf_gs_apply_static(_ptr(gs), _ptr(x), _ptr(out), ni, nr, m, _stream(stream)))
 
 
 def pdf_destroy(h: int):

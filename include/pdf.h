@@ -156,8 +156,12 @@ pdf_status pdf_forward(pdf_problem* h, const void* chi, void* esca_out, void* j_
 int32_t pdf_profile_loss_grad(pdf_problem* h, const void* alpha, int32_t reps, float* ms, int32_t n,
                               void* stream);
 
-/* Name of kernel k of pdf_loss_grad in launch order ("" when out of range). */
+/* Name of kernel k of pdf_loss_grad in launch order ("" when out of range), FP32 path. */
 const char* pdf_kernel_name(int32_t k);
+
+/* Name of profiled stage k of pdf_loss_grad for this handle's precision (with precision = 1
+ * some stages group a tensor-core GEMM with its operand packing). */
+const char* pdf_stage_name(pdf_problem* h, int32_t k);
 
 /* G_S x without any device allocation, for callers that cannot call cudaMalloc: code whose
  * device memory is already owned by another allocator (a host framework's caching allocator

@@ -19,6 +19,7 @@
 
 #include "fft.cuh"
 #include "problem.cuh"
+#include "tc.cuh"
 
 // ---------------------------------------------------------------------------
 // errors and launch accounting
@@ -227,11 +228,21 @@ extern "C" void pdf_config_default(pdf_config* c) {
 
 static void free_all(pdf_problem* h) {
   if (!h) return;
+  delete h->tc;
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (void* p : h->allocs) cudaFree(p);
   if (h->esca_host_pinned) cudaFreeHost(h->esca_host_pinned);
   delete h;
+}
+
+pdf_status ws_alloc(pdf_problem* h, void** p, size_t bytes) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes ? bytes : 256);
+  if (e != cudaSuccess) return cuda_err(e, "cudaMalloc(workspace)");
+  h->allocs.push_back(q);
+  *p = q;
+  return PDF_OK;
 }
 
 template <typename T>
@@ -296,6 +307,7 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
   h->cfg.tx_xy = nullptr;
   h->cfg.rx_xy = nullptr;
   h->alpha = h->grad = nullptr;
+  h->tc = nullptr;
   h->esca_host_pinned = nullptr;
   h->graph_exec = nullptr;
   h->cap_stream = nullptr;
@@ -451,6 +463,13 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
   d.esca = esca_d;
   d.norms = norms;
   cudaMemsetAsync(esca_d, 0, NI * NR * sizeof(float2), s);
+  if (cfg->precision == 1) {
+    st = tc_setup(h, s);
+    if (st != PDF_OK) {
+      free_all(h);
+      return st;
+    }
+  }
   if (esca) {
     st = pdf_set_data(h, esca, esca_on_device, stream);
     if (st != PDF_OK) {
@@ -558,8 +577,12 @@ extern "C" pdf_status pdf_forward(pdf_problem* h, const void* chi, void* esca_ou
 
 extern "C" int32_t pdf_profile_loss_grad(pdf_problem* h, const void* alpha, int32_t reps, float* ms, int32_t n,
                                          void* stream) {
+  if (!h) {
+    set_err(PDF_EINVAL, "pdf_profile_loss_grad: handle is NULL");
+    return PDF_EINVAL;
+  }
   const int K = hp_kernels_per_loss_grad(h);
-  if (!h || !alpha || !ms || reps < 1 || n < K) {
+  if (!alpha || !ms || reps < 1 || n < K) {
     set_err(PDF_EINVAL, "pdf_profile_loss_grad: bad arguments");
     return PDF_EINVAL;
   }
@@ -588,4 +611,6 @@ extern "C" int32_t pdf_profile_loss_grad(pdf_problem* h, const void* alpha, int3
   return K;
 }
 
-extern "C" const char* pdf_kernel_name(int32_t k) { return hp_kernel_name(k); }
+extern "C" const char* pdf_kernel_name(int32_t k) { return hp_kernel_name(k, 0); }
+
+extern "C" const char* pdf_stage_name(pdf_problem* h, int32_t k) { return hp_kernel_name(k, h ? h->cfg.precision : 0); }

@@ -21,6 +21,7 @@
 
 #include "fft.cuh"
 #include "problem.cuh"
+#include "tc.cuh"
 
 // Kahan-compensated accumulation in FP32.
 struct KSum {
@@ -591,13 +592,13 @@ __global__ void __launch_bounds__(ROW_THREADS) k_adj_rowifft_ana(Dev d, const fl
 }
 
 // analysis along y: out[p][jy][jx] = sum_y conj(wy[jy][y]) T2[p][y][jx]
-__global__ void k_ana_y(Dev d, float2* __restrict__ out) {
+__global__ void k_ana_y(Dev d, const float2* __restrict__ T2, float2* __restrict__ out) {
   const int p = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.ky * d.kx) return;
   const int jy = i / d.kx, jx = i - jy * d.kx;
   float2 acc = make_float2(0.f, 0.f);
-  const float2* T = d.T2 + (size_t)p * d.ny * d.kx;
+  const float2* T = T2 + (size_t)p * d.ny * d.kx;
   for (int y = 0; y < d.ny; ++y) acc = acc + cmulc(T[y * d.kx + jx], __ldg(&d.wy[jy * d.ny + y]));
   out[(size_t)p * d.ky * d.kx + i] = acc;
 }
@@ -658,7 +659,7 @@ pdf_status hp_configure_kernels() {
 static inline dim3 row_grid(const Dev& d) { return dim3((d.ny + ROWS_PER_CTA - 1) / ROWS_PER_CTA, d.ni); }
 static inline dim3 col_grid(const Dev& d) { return dim3((d.Px + COL_CW - 1) / COL_CW, d.ni); }
 
-int hp_kernels_per_loss_grad(const pdf_problem*) { return 12; }
+int hp_kernels_per_loss_grad(const pdf_problem* h) { return h->tc ? 11 : 12; }
 
 pdf_status hp_check_limits(const Dev& d) {
   const size_t lim = 200 * 1024;
@@ -672,30 +673,46 @@ pdf_status hp_check_limits(const Dev& d) {
 static const char* kLossGradKernels[] = {
     "k_synth_rowfft", "k_colconv", "k_rowifft_state", "k_gs_partial", "k_gs_reduce", "k_reg",
     "k_adj_rowfft",   "k_colconv(conj)", "k_gsh",     "k_adj_rowifft_ana", "k_ana_y", "k_finalize"};
+static const char* kLossGradStagesTC[] = {
+    "tc_synth(synth1+gemm+post)", "k_colconv", "k_rowifft_state", "tc_gs(gemm+reduce)", "k_reg",
+    "k_adj_rowfft", "k_colconv(conj)", "tc_gsh(gemm)", "tc_adj(rowifft+gemm)", "k_ana_y", "k_finalize"};
 
-const char* hp_kernel_name(int k) { return (k >= 0 && k < 12) ? kLossGradKernels[k] : ""; }
+const char* hp_kernel_name(int k, int precision) {
+  if (precision == 1) return (k >= 0 && k < 11) ? kLossGradStagesTC[k] : "";
+  return (k >= 0 && k < 12) ? kLossGradKernels[k] : "";
+}
 
 pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, double* terms, cudaStream_t st,
                         int* step_inc, cudaEvent_t* ev) {
   Dev& d = h->d;
   const int nout = d.ni * d.nr;
   const int n_data_blocks = (nout + 255) / 256;
+  const bool tc = h->tc != nullptr;
+  pdf_status s;
   int k = 0;
   auto mark = [&]() {
     if (ev) cudaEventRecord(ev[k++], st);
   };
   mark();
   // forward
-  k_synth_rowfft<<<row_grid(d), ROW_THREADS, sm_synth(d), st>>>(d, alpha, d.J, 1);
+  if (tc) {
+    if ((s = tc_synth(h, alpha, d.J, 1, st)) != PDF_OK) return s;
+  } else {
+    k_synth_rowfft<<<row_grid(d), ROW_THREADS, sm_synth(d), st>>>(d, alpha, d.J, 1);
+  }
   mark();
   k_colconv<<<col_grid(d), COL_THREADS, sm_col(d), st>>>(d, 0);
   mark();
   k_rowifft_state<<<d.ny, ROW_THREADS, sm_row(d), st>>>(d);
   mark();
-  k_gs_partial<<<d.n_gs_chunks, 256, sm_gs(d), st>>>(d, d.J, d.gspart);
-  mark();
-  k_gs_reduce<<<n_data_blocks, 256, 0, st>>>(d, d.gspart, d.n_gs_chunks, d.esca, d.rd,
-                                              d.lpart + LP_DATA * PDF_LP_STRIDE);
+  if (tc) {
+    if ((s = tc_gs_fwd(h, nullptr, d.esca, d.rd, d.lpart + LP_DATA * PDF_LP_STRIDE, 1, st)) != PDF_OK) return s;
+  } else {
+    k_gs_partial<<<d.n_gs_chunks, 256, sm_gs(d), st>>>(d, d.J, d.gspart);
+    mark();
+    k_gs_reduce<<<n_data_blocks, 256, 0, st>>>(d, d.gspart, d.n_gs_chunks, d.esca, d.rd,
+                                                d.lpart + LP_DATA * PDF_LP_STRIDE);
+  }
   mark();
   k_reg<<<d.n_reg_blocks, 256, 0, st>>>(d);
   mark();
@@ -704,16 +721,24 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
   mark();
   k_colconv<<<col_grid(d), COL_THREADS, sm_col(d), st>>>(d, 1);
   mark();
-  k_gsh<<<(d.M + GSH_CHUNK - 1) / GSH_CHUNK, 256, sm_gsh(d), st>>>(d, d.rd, d.gsh, 0.f, 1);
-  mark();
-  k_adj_rowifft_ana<<<row_grid(d), ROW_THREADS, sm_row(d), st>>>(d, nullptr, 0);
+  const float2* T2 = d.T2;
+  if (tc) {
+    if ((s = tc_gsh(h, nullptr, 1, st)) != PDF_OK) return s;
+    mark();
+    if ((s = tc_adj_ana(h, st)) != PDF_OK) return s;
+    T2 = (const float2*)h->tc->c_ana;
+  } else {
+    k_gsh<<<(d.M + GSH_CHUNK - 1) / GSH_CHUNK, 256, sm_gsh(d), st>>>(d, d.rd, d.gsh, 0.f, 1);
+    mark();
+    k_adj_rowifft_ana<<<row_grid(d), ROW_THREADS, sm_row(d), st>>>(d, nullptr, 0);
+  }
   mark();
   float2* g = grad ? grad : h->grad;
-  k_ana_y<<<dim3((d.ky * d.kx + 127) / 128, d.ni), 128, 0, st>>>(d, g);
+  k_ana_y<<<dim3((d.ky * d.kx + 127) / 128, d.ni), 128, 0, st>>>(d, T2, g);
   mark();
   k_finalize<<<1, 256, 0, st>>>(d, terms ? terms : h->terms, d.ny, n_data_blocks, d.n_reg_blocks, step_inc);
   mark();
-  pdf_count_launch(12);
+  pdf_count_launch(tc ? 7 : 12);
   PDF_LAUNCHED("pdf_loss_grad");
   return PDF_OK;
 }
@@ -730,6 +755,7 @@ pdf_status hp_gd(pdf_problem* h, const float2* in, float2* out, int adjoint, cud
 
 pdf_status hp_gs(pdf_problem* h, const float2* in, float2* out, const float2* subtract, double* sumsq,
                  cudaStream_t st) {
+  if (h->tc) return tc_gs_fwd(h, in, subtract, out, sumsq, 0, st);
   Dev& d = h->d;
   const int nout = d.ni * d.nr;
   k_gs_partial<<<d.n_gs_chunks, 256, sm_gs(d), st>>>(d, in, d.gspart);
@@ -740,6 +766,7 @@ pdf_status hp_gs(pdf_problem* h, const float2* in, float2* out, const float2* su
 }
 
 pdf_status hp_gsh(pdf_problem* h, const float2* in, float2* out, float scale, cudaStream_t st) {
+  if (h->tc) return tc_gsh_field(h, in, out, scale, st);
   Dev& d = h->d;
   k_gsh<<<(d.M + GSH_CHUNK - 1) / GSH_CHUNK, 256, sm_gsh(d), st>>>(d, in, out, scale, 0);
   pdf_count_launch(1);
@@ -748,6 +775,7 @@ pdf_status hp_gsh(pdf_problem* h, const float2* in, float2* out, float scale, cu
 }
 
 pdf_status hp_synth(pdf_problem* h, const float2* alpha, float2* out, cudaStream_t st) {
+  if (h->tc) return tc_synth(h, alpha, out, 0, st);
   Dev& d = h->d;
   k_synth_rowfft<<<row_grid(d), ROW_THREADS, sm_synth(d), st>>>(d, alpha, out, 0);
   pdf_count_launch(1);
@@ -757,8 +785,15 @@ pdf_status hp_synth(pdf_problem* h, const float2* alpha, float2* out, cudaStream
 
 pdf_status hp_analysis(pdf_problem* h, const float2* in, float2* out, cudaStream_t st) {
   Dev& d = h->d;
-  k_adj_rowifft_ana<<<row_grid(d), ROW_THREADS, sm_row(d), st>>>(d, in, 1);
-  k_ana_y<<<dim3((d.ky * d.kx + 127) / 128, d.ni), 128, 0, st>>>(d, out);
+  const float2* T2 = d.T2;
+  if (h->tc) {
+    pdf_status s = tc_analysis_field(h, in, st);
+    if (s != PDF_OK) return s;
+    T2 = (const float2*)h->tc->c_ana;
+  } else {
+    k_adj_rowifft_ana<<<row_grid(d), ROW_THREADS, sm_row(d), st>>>(d, in, 1);
+  }
+  k_ana_y<<<dim3((d.ky * d.kx + 127) / 128, d.ni), 128, 0, st>>>(d, T2, out);
   pdf_count_launch(2);
   PDF_LAUNCHED("analysis");
   return PDF_OK;
@@ -766,7 +801,12 @@ pdf_status hp_analysis(pdf_problem* h, const float2* in, float2* out, cudaStream
 
 pdf_status hp_chi(pdf_problem* h, const float2* alpha, float2* chi_out, cudaStream_t st) {
   Dev& d = h->d;
-  k_synth_rowfft<<<row_grid(d), ROW_THREADS, sm_synth(d), st>>>(d, alpha, d.J, 1);
+  if (h->tc) {
+    pdf_status s = tc_synth(h, alpha, d.J, 1, st);
+    if (s != PDF_OK) return s;
+  } else {
+    k_synth_rowfft<<<row_grid(d), ROW_THREADS, sm_synth(d), st>>>(d, alpha, d.J, 1);
+  }
   k_colconv<<<col_grid(d), COL_THREADS, sm_col(d), st>>>(d, 0);
   k_rowifft_state<<<d.ny, ROW_THREADS, sm_row(d), st>>>(d);
   pdf_count_launch(3);

@@ -55,8 +55,11 @@ struct Dev {
   double* lpart;         // [LP_NSLOT][PDF_LP_STRIDE]
 };
 
+struct TC;
+
 struct pdf_problem {
   pdf_config cfg;
+  TC* tc;                // split-BF16 tensor-core state (precision = 1), else NULL
   std::vector<double> tx, rx;
   Dev d;
   int dev_id;
@@ -101,6 +104,9 @@ pdf_status cuda_err(cudaError_t e, const char* where);
     if (_e != cudaSuccess) return cuda_err(_e, where);              \
   } while (0)
 
+// workspace allocation owned by the handle (api.cu)
+pdf_status ws_alloc(pdf_problem* h, void** p, size_t bytes);
+
 // reductions defined in api.cu
 __global__ void k_sumsq(const float2* x, int n, double* out);
 
@@ -109,7 +115,8 @@ pdf_status hp_configure_kernels();
 pdf_status hp_check_limits(const Dev& d);
 pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, double* terms, cudaStream_t st,
                         int* step_inc = nullptr, cudaEvent_t* ev = nullptr);
-const char* hp_kernel_name(int k);
+const char* hp_kernel_name(int k, int precision);
+__global__ void k_ana_y(Dev d, const float2* T2, float2* out);
 pdf_status hp_gd(pdf_problem* h, const float2* in, float2* out, int adjoint, cudaStream_t st);
 pdf_status hp_gs(pdf_problem* h, const float2* in, float2* out, const float2* subtract, double* sumsq, cudaStream_t st);
 pdf_status hp_gsh(pdf_problem* h, const float2* in, float2* out, float scale, cudaStream_t st);

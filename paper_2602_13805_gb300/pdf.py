@@ -76,7 +76,8 @@ _lib = None
 
 EXPORTS = ("pdf_config_default", "pdf_setup", "pdf_set_data", "pdf_loss_grad", "pdf_apply_op",
            "pdf_solve_opts_default", "pdf_solve", "pdf_forward", "pdf_launch_count", "pdf_destroy",
-           "pdf_last_error", "pdf_profile_loss_grad", "pdf_kernel_name", "pdf_gs_apply_static")
+           "pdf_last_error", "pdf_profile_loss_grad", "pdf_kernel_name", "pdf_gs_apply_static",
+           "pdf_stage_name")
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -112,6 +113,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pdf_profile_loss_grad.restype = i32
     lib.pdf_kernel_name.argtypes = [i32]
     lib.pdf_kernel_name.restype = ctypes.c_char_p
+    lib.pdf_stage_name.argtypes = [vp, i32]
+    lib.pdf_stage_name.restype = ctypes.c_char_p
     lib.pdf_gs_apply_static.argtypes = [vp, vp, vp, i32, i32, i32, vp]
     lib.pdf_gs_apply_static.restype = ctypes.c_int
     lib.pdf_last_error.argtypes = []
@@ -235,7 +238,7 @@ def pdf_profile_loss_grad(h: int, alpha, reps: int = 20, stream=None):
     k = lib.pdf_profile_loss_grad(h, _ptr(alpha), reps, buf, 64, _stream(stream))
     if k < 0:
         _check(k)
-    return [(lib.pdf_kernel_name(i).decode(), float(buf[i])) for i in range(k)]
+    return [(lib.pdf_stage_name(h, i).decode(), float(buf[i])) for i in range(k)]
 
 
 def solve_opts(**kw) -> pdf_solve_opts:

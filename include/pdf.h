@@ -111,17 +111,20 @@ pdf_status pdf_apply_op(pdf_problem* h, int op, const void* in, void* out, void*
 typedef struct pdf_solve_opts {
   int32_t iters;             /* Adam iterations (>= 0)                                        */
   int32_t init;              /* 0 = BP + one exact-line-search CSI step (Sec. 3.1, Eq. 12),
-                                1 = alpha0 given, 2 = zeros                                   */
+                                1 = alpha0 given, 2 = zeros, 3 = alpha0 (a learned warm start)
+                                unless its loss exceeds the loss at the BP + CSI start        */
   double lr, adam_b1, adam_b2, adam_eps;   /* paper: lr 1e-2; torch defaults 0.9, 0.999, 1e-8 */
-  const void* alpha0;        /* device [ni][ky][kx] complex64 when init == 1                   */
+  const void* alpha0;        /* device [ni][ky][kx] complex64 when init == 1 or 3              */
   const void* chi_true;      /* optional device [ny][nx] complex64: enables RelErr             */
   int32_t apply_cco;         /* 1 = post-process chi-hat with the CCO (Sec. 2.4)               */
   int32_t cco_radius;        /* guided-filter box radius (default 2)                           */
   double cco_eps;            /* guided-filter regulariser (default 1e-2)                       */
   double cco_eta_max, cco_tau, cco_delta;  /* Eq. (11): 0.1, 3, 0.5                            */
   int32_t use_graph;         /* 1 = run the iteration loop as a CUDA graph                     */
-  int32_t history_every;     /* > 0: write the 6 loss terms every n iterations to history      */
-  double* history;           /* device [ceil(iters / history_every)][6] when history_every > 0 */
+  int32_t history_every;     /* > 0: every n iterations write a row of 8 doubles to history: the
+                                6 loss terms, RelErr of chi-hat and of its CCO image (NaN-free
+                                only with chi_true; the loop then runs without a CUDA graph)    */
+  double* history;           /* device [ceil(iters / history_every)][8] when history_every > 0 */
 } pdf_solve_opts;
 
 typedef struct pdf_solve_report {
@@ -130,6 +133,8 @@ typedef struct pdf_solve_report {
   double terms[6];           /* loss terms at the final alpha                                  */
   double relerr;             /* ||chi - chi_true|| / ||chi_true|| before CCO (NaN without truth) */
   double relerr_cco;         /* same after CCO                                                 */
+  int32_t used_warm_start;   /* init == 3: 1 if alpha0 was kept, 0 if BP + CSI was used        */
+  int32_t reserved;
 } pdf_solve_report;
 
 void pdf_solve_opts_default(pdf_solve_opts* o);
@@ -180,6 +185,35 @@ const char* pdf_stage_name(pdf_problem* h, int32_t k);
  * Asynchronous on `stream`. */
 pdf_status pdf_gs_apply_static(const void* gs, const void* x, void* out, int32_t ni, int32_t nr, int32_t m,
                                void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Learned warm start (not in the paper): a fully connected network with ReLU hidden layers,
+ * BF16 tensor-core products with FP32 accumulation and FP32 master weights, trained with the
+ * mean squared error and Adam (torch.optim.Adam arithmetic, betas 0.9/0.999, eps 1e-8).
+ * Arrays are device float32, row-major: X [B][sizes[0]], T and Y [B][sizes[nlayers]],
+ * W [out][in] and b [out] of each layer (host float32 for set/get).  Every call is
+ * asynchronous on `stream` except set/get_params, which synchronise.
+ * --------------------------------------------------------------------------------------------- */
+typedef struct pdf_mlp pdf_mlp;
+
+/* nlayers linear layers, sizes[0..nlayers] the widths; batch_max <= 4096.  Weights start at 0:
+ * set them with pdf_mlp_set_params.  PDF_EINVAL on bad sizes, PDF_ENOMEM. */
+pdf_status pdf_mlp_create(int32_t nlayers, const int32_t* sizes, int32_t batch_max, pdf_mlp** out);
+void pdf_mlp_destroy(pdf_mlp* m);
+/* Copies host W [out][in] and b [out] of `layer` in and resets its Adam state and the step count. */
+pdf_status pdf_mlp_set_params(pdf_mlp* m, int32_t layer, const float* W, const float* b, void* stream);
+/* Copies the master weights and the last gradients of `layer` to host arrays (any may be NULL). */
+pdf_status pdf_mlp_get_params(pdf_mlp* m, int32_t layer, float* W, float* b, float* dW, float* db, void* stream);
+/* Y = network(X) for B <= batch_max rows. */
+pdf_status pdf_mlp_forward(pdf_mlp* m, const float* X, float* Y, int32_t B, void* stream);
+/* Gradients of mean((Y - T)^2) with respect to all weights (kept in the handle, see get_params);
+ * loss: device double (may be NULL). */
+pdf_status pdf_mlp_loss_grad(pdf_mlp* m, const float* X, const float* T, int32_t B, double* loss, void* stream);
+/* pdf_mlp_loss_grad followed by one Adam step with learning rate lr on every layer. */
+pdf_status pdf_mlp_train_step(pdf_mlp* m, const float* X, const float* T, int32_t B, double lr, double* loss,
+                              void* stream);
+/* 1 if a tensor-core wait timed out in an earlier call, 0 otherwise (synchronises). */
+int32_t pdf_mlp_error_flag(pdf_mlp* m);
 
 /* Number of kernels this library has launched in the calling process (graph launches count
  * every kernel node they execute).  For benchmarking evidence. */

@@ -392,6 +392,8 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
   TRY(dalloc(h, &h->field3, M));
   TRY(dalloc(h, &h->small1, NI * NR));
   TRY(dalloc(h, &h->cco_ab, M));
+  TRY(dalloc(h, &h->alpha_alt, NA));
+  TRY(dalloc(h, &h->used_warm, 1));
   TRY(dalloc(h, &h->small2, NI * NR));
   {
     cudaError_t e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
@@ -560,7 +562,8 @@ extern "C" pdf_status pdf_solve(pdf_problem* h, const pdf_solve_opts* o, void* c
   if (!h || !o) return set_err(PDF_EINVAL, "handle or opts is NULL");
   if (o->iters < 0) return set_err(PDF_EINVAL, "iters must be >= 0");
   if (o->init == 1 && !o->alpha0) return set_err(PDF_EINVAL, "init == 1 needs alpha0");
-  if (o->init < 0 || o->init > 2) return set_err(PDF_EINVAL, "init must be 0, 1 or 2");
+  if (o->init < 0 || o->init > 3) return set_err(PDF_EINVAL, "init must be 0, 1, 2 or 3");
+  if (o->init == 3 && !o->alpha0) return set_err(PDF_EINVAL, "init == 3 needs alpha0");
   if (o->history_every > 0 && !o->history) return set_err(PDF_EINVAL, "history_every > 0 needs history");
   if (o->apply_cco && (o->cco_radius < 0 || o->cco_radius > 16 || o->cco_eps <= 0))
     return set_err(PDF_EINVAL, "cco_radius must be in [0, 16] and cco_eps > 0");

@@ -81,6 +81,8 @@ struct pdf_problem {
   float2* field3;
   float2* esca_host_pinned;  // pinned staging [ni][nr]
   float4* cco_ab;        // [M] guided-filter coefficients
+  float2* alpha_alt;     // [ni][ky][kx] warm-start candidate
+  int* used_warm;        // device flag
   float2* small1;        // [ni][nr] scratch
   float2* small2;
   cudaStream_t cap_stream;   // private stream used only for graph capture

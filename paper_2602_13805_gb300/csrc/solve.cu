@@ -229,6 +229,29 @@ __global__ void k_init_alpha(Dev d, const float2* __restrict__ g, float2* __rest
   alpha[i] = (-t) * g[i];
 }
 
+// dst = ||a - b|| / ||b|| (single block, double accumulation)
+__global__ void k_relerr_to(const float2* __restrict__ a, const float2* __restrict__ b, int n, double* dst) {
+  __shared__ double red[32];
+  double e = 0.0, t = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double2 bd = to_d(b[i]);
+    e += cabs2(to_d(a[i]) - bd);
+    t += cabs2(bd);
+  }
+  const double se = block_sum(e, red);
+  const double st = block_sum(t, red);
+  if (threadIdx.x == 0) *dst = sqrt(se / st);
+}
+
+// warm start with fallback: keep alpha (BP + CSI) unless the candidate's loss is not larger
+__global__ void k_pick_warm(float2* __restrict__ alpha, const float2* __restrict__ cand, const double* la,
+                            const double* lb, int n, int* used) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool take = isfinite(lb[0]) && lb[0] <= la[0];
+  if (i < n && take) alpha[i] = cand[i];
+  if (i == 0) *used = take ? 1 : 0;
+}
+
 __global__ void k_sum_d(const double* in, int n, double* out) {
   __shared__ double red[32];
   double a = 0.0;
@@ -353,8 +376,19 @@ pdf_status sv_solve(pdf_problem* h, const pdf_solve_opts* o, float2* chi_out, fl
   Dev& d = h->d;
   const int NA = d.ni * d.ky * d.kx;
   pdf_status s;
+  PDF_CUDA(cudaMemsetAsync(h->used_warm, 0, sizeof(int), st));
   if (o->init == 0) {
     if ((s = init_bp_csi(h, st)) != PDF_OK) return s;
+  } else if (o->init == 3) {
+    // warm start with fallback: L at the BP + CSI start vs L at the given alpha0
+    if ((s = init_bp_csi(h, st)) != PDF_OK) return s;
+    if ((s = hp_loss_grad(h, h->alpha, h->grad, h->scratch_d + 48, st)) != PDF_OK) return s;
+    PDF_CUDA(cudaMemcpyAsync(h->alpha_alt, o->alpha0, sizeof(float2) * NA, cudaMemcpyDeviceToDevice, st));
+    if ((s = hp_loss_grad(h, h->alpha_alt, h->grad, h->scratch_d + 56, st)) != PDF_OK) return s;
+    k_pick_warm<<<(NA + 255) / 256, 256, 0, st>>>(h->alpha, h->alpha_alt, h->scratch_d + 48, h->scratch_d + 56, NA,
+                                                  h->used_warm);
+    pdf_count_launch(1);
+    PDF_LAUNCHED("warm-start selection");
   } else if (o->init == 1) {
     PDF_CUDA(cudaMemcpyAsync(h->alpha, o->alpha0, sizeof(float2) * NA, cudaMemcpyDeviceToDevice, st));
   } else {
@@ -367,9 +401,23 @@ pdf_status sv_solve(pdf_problem* h, const pdf_solve_opts* o, float2* chi_out, fl
   if (o->history_every > 0) {
     for (; it < o->iters; ++it) {
       if ((s = iteration(h, o, st)) != PDF_OK) return s;
-      if (it % o->history_every == 0)
-        PDF_CUDA(cudaMemcpyAsync(o->history + 6 * (it / o->history_every), h->terms, 6 * sizeof(double),
-                                 cudaMemcpyDeviceToDevice, st));
+      if (it % o->history_every == 0) {
+        double* row = o->history + 8 * (it / o->history_every);
+        PDF_CUDA(cudaMemcpyAsync(row, h->terms, 6 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        if (o->chi_true) {
+          // chi-hat of this iteration's alpha (before its Adam step) and its CCO image
+          k_relerr_to<<<1, 1024, 0, st>>>(d.chi, (const float2*)o->chi_true, d.M, row + 6);
+          pdf_count_launch(1);
+          if (o->apply_cco) {
+            if ((s = sv_cco(h, d.chi, h->field3, o->cco_radius, o->cco_eps, o->cco_eta_max, o->cco_tau,
+                            o->cco_delta, st)) != PDF_OK)
+              return s;
+            k_relerr_to<<<1, 1024, 0, st>>>(h->field3, (const float2*)o->chi_true, d.M, row + 7);
+            pdf_count_launch(1);
+          }
+          PDF_LAUNCHED("history relerr");
+        }
+      }
     }
   } else {
     if (o->use_graph && o->iters >= GRAPH_UNROLL) {
@@ -414,6 +462,9 @@ pdf_status sv_solve(pdf_problem* h, const pdf_solve_opts* o, float2* chi_out, fl
     PDF_CUDA(cudaStreamSynchronize(st));
     rep->relerr = o->chi_true ? sqrt(re[0] / re[1]) : NAN;
     rep->relerr_cco = o->chi_true ? sqrt(re[2] / re[3]) : NAN;
+    int used = 0;
+    PDF_CUDA(cudaMemcpy(&used, h->used_warm, sizeof(int), cudaMemcpyDeviceToHost));
+    rep->used_warm_start = used;
     for (int k = 0; k < 6; ++k)
       if (!std::isfinite(rep->terms[k])) rep->nonfinite = 1;
     if (rep->nonfinite) return set_err(PDF_ENONFINITE, "a loss term is not finite");

@@ -69,6 +69,7 @@ class pdf_solve_report(ctypes.Structure):
         ("iters_run", ctypes.c_int32), ("nonfinite", ctypes.c_int32),
         ("terms", ctypes.c_double * 6),
         ("relerr", ctypes.c_double), ("relerr_cco", ctypes.c_double),
+        ("used_warm_start", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -77,7 +78,8 @@ _lib = None
 EXPORTS = ("pdf_config_default", "pdf_setup", "pdf_set_data", "pdf_loss_grad", "pdf_apply_op",
            "pdf_solve_opts_default", "pdf_solve", "pdf_forward", "pdf_launch_count", "pdf_destroy",
            "pdf_last_error", "pdf_profile_loss_grad", "pdf_kernel_name", "pdf_gs_apply_static",
-           "pdf_stage_name")
+           "pdf_stage_name", "pdf_mlp_create", "pdf_mlp_destroy", "pdf_mlp_set_params", "pdf_mlp_get_params",
+           "pdf_mlp_forward", "pdf_mlp_loss_grad", "pdf_mlp_train_step", "pdf_mlp_error_flag")
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -117,6 +119,22 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pdf_stage_name.restype = ctypes.c_char_p
     lib.pdf_gs_apply_static.argtypes = [vp, vp, vp, i32, i32, i32, vp]
     lib.pdf_gs_apply_static.restype = ctypes.c_int
+    lib.pdf_mlp_create.argtypes = [i32, ctypes.POINTER(i32), i32, ctypes.POINTER(vp)]
+    lib.pdf_mlp_create.restype = ctypes.c_int
+    lib.pdf_mlp_destroy.argtypes = [vp]
+    lib.pdf_mlp_destroy.restype = None
+    lib.pdf_mlp_set_params.argtypes = [vp, i32, vp, vp, vp]
+    lib.pdf_mlp_set_params.restype = ctypes.c_int
+    lib.pdf_mlp_get_params.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+    lib.pdf_mlp_get_params.restype = ctypes.c_int
+    lib.pdf_mlp_forward.argtypes = [vp, vp, vp, i32, vp]
+    lib.pdf_mlp_forward.restype = ctypes.c_int
+    lib.pdf_mlp_loss_grad.argtypes = [vp, vp, vp, i32, vp, vp]
+    lib.pdf_mlp_loss_grad.restype = ctypes.c_int
+    lib.pdf_mlp_train_step.argtypes = [vp, vp, vp, i32, dbl, vp, vp]
+    lib.pdf_mlp_train_step.restype = ctypes.c_int
+    lib.pdf_mlp_error_flag.argtypes = [vp]
+    lib.pdf_mlp_error_flag.restype = i32
     lib.pdf_last_error.argtypes = []
     lib.pdf_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -314,7 +332,7 @@ class Problem:
         import torch
         hist = None
         if history_every > 0:
-            hist = torch.zeros((math.ceil(iters / history_every), 6), dtype=torch.float64, device="cuda")
+            hist = torch.full((math.ceil(iters / history_every), 8), float("nan"), dtype=torch.float64, device="cuda")
         o = solve_opts(iters=iters, lr=lr, init=init, alpha0=alpha0, chi_true=chi_true, apply_cco=int(apply_cco),
                        use_graph=int(use_graph), history_every=history_every, history=hist, **kw)
         chi = self._t(self.ny, self.nx)
@@ -322,7 +340,7 @@ class Problem:
         alpha = self._t(self.ni, self.ky, self.kx)
         rep = pdf_solve(self.h, o, chi, chi_raw, alpha, True, stream)
         return dict(chi=chi, chi_raw=chi_raw, alpha=alpha, terms=np.array(rep.terms[:]), relerr=rep.relerr,
-                    relerr_cco=rep.relerr_cco, history=hist)
+                    relerr_cco=rep.relerr_cco, history=hist, used_warm_start=rep.used_warm_start)
 
     def forward(self, chi, tol=1e-6, max_iter=2000, stream=None):
         esca = self._t(self.ni, self.nr)

@@ -155,7 +155,7 @@ def run_ours(args, rank, world, local):
         w = scenes.workload(args.workload, iters=args.iters)
     seed = rank
     chi_true = scenes.make_scene(w, seed)
-    prob = pdf.Problem.from_workload(w)
+    prob = pdf.Problem.from_workload(w, precision=args.precision)
     chi_d = torch.from_numpy(chi_true.astype(np.complex64)).cuda()
     esca_clean, _, fwd_iters = prob.forward(chi_d, tol=1e-5, max_iter=3000)
     esca = scenes.add_awgn(esca_clean.cpu().numpy().astype(np.complex128), w.noise,
@@ -242,11 +242,14 @@ def run_ours(args, rank, world, local):
         out = {
             "metric": METRIC, "value": ms_per_recon, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 complex), fp64 reductions",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64 (fp32 complex), fp64 reductions" if args.precision == 0 else
+                     "c64 FFT path + split-BF16 tensor-core contractions (fp32 accumulate), fp64 reductions",
             "data": "synthetic (seeded scene, GPU forward solver, AWGN)",
             "config": {"workload": f"{w.name}: {w.nx}x{w.ny} grid, {w.side} lambda DOI, Ni={w.ni}, Nr={w.nr}, "
                                    f"K={w.kx}x{w.ky}, {w.iters} Adam iterations, BP+CSI init, CCO",
-                       "iters": w.iters, "lr": args.lr, "parallelism": "replicas" if world > 1 else "single",
+                       "iters": w.iters, "lr": args.lr, "precision": args.precision,
+                       "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed between reconstructions (512 MB write); working set L2-resident within one"},
             "iters_per_s": w.iters * args.steps * world / (total_ms * 1e-3),
             "relerr": rep.relerr, "relerr_cco": rep.relerr_cco, "final_loss": rep.terms[0],
@@ -336,6 +339,7 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-2)
     ap.add_argument("--cpu-iters", type=int, default=20)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":

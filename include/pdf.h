@@ -60,7 +60,8 @@ typedef struct pdf_config {
   double eps_abs;            /* smoothing inside |chi| of Eq. (19)                           */
   double q_min;              /* clamp of |1 - R| when forming chi = R / (beta (1 - R))       */
   int32_t precision;         /* 0 = FP32 contractions, 1 = split-BF16 tensor-core contractions */
-  int32_t reserved;
+  int32_t fft_path;          /* 0 = register-resident warp FFTs (padded lengths 64..512),
+                                1 = generic shared-memory FFT (any padded length 2^a 3^b)      */
 } pdf_config;
 
 /* Fills the paper's defaults (beta = 6, lambdas 1e-3/1e-5/1e-5, tau_B = 0.5, k0 = 2 pi) and

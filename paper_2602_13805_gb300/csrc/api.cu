@@ -15,6 +15,7 @@
 #include <mutex>
 #include <atomic>
 #include <climits>
+#include <algorithm>
 #include <vector>
 
 #include "fft.cuh"
@@ -200,6 +201,11 @@ __global__ void k_sum(const double* in, int n, double* out) {
   if (threadIdx.x == 0) *out = t;
 }
 
+// invn = 2 / norms (float), 0 where a norm is not positive
+__global__ void k_set_invn(const double* norms, float* invn) {
+  if (threadIdx.x < 2) invn[threadIdx.x] = norms[threadIdx.x] > 0.0 ? (float)(2.0 / norms[threadIdx.x]) : 0.f;
+}
+
 // ||x||^2 of a complex64 array in double, single block.
 __global__ void k_sumsq(const float2* x, int n, double* out) {
   __shared__ double red[32];
@@ -280,10 +286,11 @@ static pdf_status validate(const pdf_config* c) {
   if (!(c->beta_re > 0)) return set_err(PDF_EINVAL, "Re beta must be > 0 (contractive CIE, Eq. 7)");
   if (c->inc_kind != 0 && c->inc_kind != 1) return set_err(PDF_EINVAL, "inc_kind must be 0 or 1");
   if (c->precision != 0 && c->precision != 1) return set_err(PDF_EINVAL, "precision must be 0 or 1");
+  if (c->fft_path != 0 && c->fft_path != 1) return set_err(PDF_EINVAL, "fft_path must be 0 or 1");
   if (c->tau_b <= 0 || c->eps_tv < 0 || c->eps_abs < 0 || c->q_min < 0)
     return set_err(PDF_EINVAL, "tau_b > 0 and non-negative eps/q_min required");
   int M = c->nx * c->ny;
-  if ((M + GS_CHUNK - 1) / GS_CHUNK > PDF_LP_STRIDE) return set_err(PDF_EUNSUPPORTED, "grid too large");
+
   return PDF_OK;
 }
 
@@ -295,7 +302,10 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
   if (st != PDF_OK) return st;
   static std::once_flag once;
   static pdf_status cfg_status = PDF_OK;
-  std::call_once(once, [] { cfg_status = hp_configure_kernels(); });
+  std::call_once(once, [] {
+    cfg_status = hp_configure_kernels();
+    if (cfg_status == PDF_OK) cfg_status = fp_configure();
+  });
   if (cfg_status != PDF_OK) return cfg_status;
 
   cudaStream_t s = (cudaStream_t)stream;
@@ -323,8 +333,22 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
   d.kx = cfg->kx;
   d.ky = cfg->ky;
   d.M = d.nx * d.ny;
-  d.Px = next_smooth(2 * d.nx);
-  d.Py = next_smooth(2 * d.ny);
+  // padded FFT lengths: the register-FFT sizes {64, 128, 256, 384, 512} unless the generic
+  // shared-memory FFT is requested (any P = 2^a 3^b >= 2n)
+  d.fast = cfg->fft_path == 0;
+  if (d.fast) {
+    static const int sizes[5] = {64, 128, 256, 384, 512};
+    d.Px = d.Py = 0;
+    for (int q : sizes) {
+      if (!d.Px && q >= 2 * d.nx) d.Px = q;
+      if (!d.Py && q >= 2 * d.ny) d.Py = q;
+    }
+    if (!d.Px || !d.Py) d.fast = 0;
+  }
+  if (!d.fast) {
+    d.Px = next_smooth(2 * d.nx);
+    d.Py = next_smooth(2 * d.ny);
+  }
   if (d.Px > PDF_MAX_P || d.Py > PDF_MAX_P || !make_fft_plan(d.Px, &d.plx) || !make_fft_plan(d.Py, &d.ply)) {
     free_all(h);
     return set_err(PDF_EUNSUPPORTED, "padded FFT length unsupported");
@@ -338,7 +362,9 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
   d.eps_tv = (float)cfg->eps_tv;
   d.eps_abs = (float)cfg->eps_abs;
   d.q_min = (float)cfg->q_min;
-  d.n_gs_chunks = (d.M + GS_CHUNK - 1) / GS_CHUNK;
+  // SIMT G_S product: about two CTAs per SM, 32..256 pixels each (multiple of 32)
+  d.gs_chunk = std::min(256, std::max(32, ((d.M + 303) / 304 + 31) / 32 * 32));
+  d.n_gs_chunks = (d.M + d.gs_chunk - 1) / d.gs_chunk;
   d.n_reg_blocks = (d.M + 255) / 256;
   if ((st = hp_check_limits(d)) != PDF_OK) {
     free_all(h);
@@ -377,6 +403,11 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
   TRY(dalloc(h, &d.gspart, (size_t)d.n_gs_chunks * NI * NR));
   TRY(dalloc(h, &d.rd, NI * NR));
   TRY(dalloc(h, &d.lpart, (size_t)LP_NSLOT * PDF_LP_STRIDE));
+  TRY(dalloc(h, &h->invn, 2));
+  d.invn = h->invn;
+  d.adam_tab = nullptr;
+  h->adam_tab = nullptr;
+  h->adam_cap = 0;
   TRY(dalloc(h, &h->alpha, NA));
   TRY(dalloc(h, &h->grad, NA));
   TRY(dalloc(h, &h->adam_m, 2 * NA));
@@ -409,7 +440,7 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
       return cuda_err(e, "cudaMallocHost(esca staging)");
     }
   }
-  cudaMemsetAsync(d.lpart, 0, sizeof(double) * LP_NSLOT * PDF_LP_STRIDE, s);
+  cudaMemsetAsync(d.lpart, 0, sizeof(FF) * LP_NSLOT * PDF_LP_STRIDE, s);
 
   double* txd;
   double* rxd;
@@ -444,6 +475,8 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
   k_einc<<<dim3(d.ny, d.ni), 128, 0, s>>>(einc, part, txd, d.nx, d.ny, cfg->side_x, cfg->side_y, cfg->k0,
                                           cfg->inc_kind);
   k_sum<<<1, 1024, 0, s>>>(part, d.ni * d.ny, norms);
+  cudaMemsetAsync(norms + 1, 0, sizeof(double), s);
+  k_set_invn<<<1, 32, 0, s>>>(norms, h->invn);
   k_gs<<<dim3((d.M + 255) / 256, d.nr), 256, 0, s>>>(gs, rxd, d.nx, d.ny, cfg->side_x, cfg->side_y, cfg->k0, a);
   k_synth_table<<<dim3((d.nx + 127) / 128, d.kx), 128, 0, s>>>(wx, d.kx, d.nx);
   k_synth_table<<<dim3((d.ny + 127) / 128, d.ky), 128, 0, s>>>(wy, d.ky, d.ny);
@@ -458,6 +491,16 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
   d.twx = twx;
   d.twy = twy;
   d.ghat = ghat;
+  d.ghat_perm = nullptr;
+  if (d.fast) {
+    float2* gp;
+    TRY(dalloc(h, &gp, (size_t)d.Px * d.Py));
+    if ((st = fp_perm_ghat(d, gp, s)) != PDF_OK) {
+      free_all(h);
+      return st;
+    }
+    d.ghat_perm = gp;
+  }
   d.einc = einc;
   d.gs = gs;
   d.wx = wx;
@@ -502,7 +545,8 @@ extern "C" pdf_status pdf_set_data(pdf_problem* h, const void* esca, int on_devi
     PDF_CUDA(cudaMemcpyAsync(dst, h->esca_host_pinned, n * sizeof(float2), cudaMemcpyHostToDevice, s));
   }
   k_sumsq<<<1, 1024, 0, s>>>(dst, (int)n, const_cast<double*>(h->d.norms) + 1);
-  pdf_count_launch(1);
+  k_set_invn<<<1, 32, 0, s>>>(h->d.norms, h->invn);
+  pdf_count_launch(2);
   PDF_LAUNCHED("pdf_set_data");
   return PDF_OK;
 }

@@ -81,6 +81,49 @@ __device__ __forceinline__ double block_sum(double v, double* scratch) {
 }
 
 // ---------------------------------------------------------------------------
+// float-float ("double-single") accumulation: value = hi + lo with |lo| <= ulp(hi)/2, built from
+// error-free TwoSum steps.  Carries ~44 significant bits at FP32 speed; used instead of FP64,
+// whose throughput and latency on this part make even small FP64 reductions dominate a kernel.
+// ---------------------------------------------------------------------------
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_make(float a) { return FF{a, 0.f}; }
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  const float hi = s + e;
+  return FF{hi, e - (hi - s)};
+}
+__device__ __forceinline__ FF ff_add(FF a, float b) { return ff_add(a, FF{b, 0.f}); }
+__device__ __forceinline__ double ff_to_d(FF a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ FF ff_shfl_xor(FF a, int m) {
+  return FF{__shfl_xor_sync(0xffffffffu, a.hi, m), __shfl_xor_sync(0xffffffffu, a.lo, m)};
+}
+__device__ __forceinline__ FF ff_warp_sum(FF v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = ff_add(v, ff_shfl_xor(v, o));
+  return v;
+}
+// Sum over the block; valid in thread 0.  `scratch` needs 32 FF of shared memory.
+__device__ __forceinline__ FF ff_block_sum(FF v, FF* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = ff_warp_sum(v);
+  __syncthreads();
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  FF r = FF{0.f, 0.f};
+  if (wid == 0) {
+    r = lane < nw ? scratch[lane] : FF{0.f, 0.f};
+    r = ff_warp_sum(r);
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------------------
 // FFT plan: P = product of radices (each 2, 3 or 4), Stockham ordering
 // ---------------------------------------------------------------------------
 struct FFTPlan {

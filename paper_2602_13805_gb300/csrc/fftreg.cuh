@@ -1,0 +1,142 @@
+// Register-resident FFT of one line of length P = 32 R per warp (R = 2, 4, 8, 12 or 16).
+//
+// Lane l holds the R points x[l + 32 m] (m = 0 .. R-1).  With k = k1 + R k2,
+//   X[k1 + R k2] = sum_l W32^{l k2} ( W_P^{l k1} sum_m x[l + 32 m] W_R^{m k1} ),
+// so the forward transform is an R-point DFT in registers, a twiddle, and a 32-point
+// decimation-in-frequency FFT across lanes with shuffles.  Its output is in digit-reversed
+// order: lane l, slot k1 holds X[k1 + R brev5(l)].  The inverse (decimation in time) takes that
+// order back to natural order, so a convolution (forward, pointwise product with a spectrum
+// stored in the same permuted order, inverse) never reorders data.  Neither direction is
+// normalised.  The twiddle table tw[e] = exp(-2 pi i e / P) is assembled in FP64 at setup.
+#pragma once
+
+#include "fft.cuh"
+
+// W_R^e = exp(-2 pi i e / R) for the in-register R = 8, 12, 16 transforms (cos, -sin pairs)
+static __constant__ float2 c_tw8[8] = {{1.000000000f, 0.000000000f},  {0.707106781f, -0.707106781f},
+                                       {0.000000000f, -1.000000000f}, {-0.707106781f, -0.707106781f},
+                                       {-1.000000000f, 0.000000000f}, {-0.707106781f, 0.707106781f},
+                                       {0.000000000f, 1.000000000f},  {0.707106781f, 0.707106781f}};
+static __constant__ float2 c_tw12[12] = {{1.000000000f, 0.000000000f},  {0.866025404f, -0.500000000f},
+                                         {0.500000000f, -0.866025404f}, {0.000000000f, -1.000000000f},
+                                         {-0.500000000f, -0.866025404f}, {-0.866025404f, -0.500000000f},
+                                         {-1.000000000f, 0.000000000f}, {-0.866025404f, 0.500000000f},
+                                         {-0.500000000f, 0.866025404f}, {0.000000000f, 1.000000000f},
+                                         {0.500000000f, 0.866025404f},  {0.866025404f, 0.500000000f}};
+static __constant__ float2 c_tw16[16] = {{1.000000000f, 0.000000000f},  {0.923879533f, -0.382683432f},
+                                         {0.707106781f, -0.707106781f}, {0.382683432f, -0.923879533f},
+                                         {0.000000000f, -1.000000000f}, {-0.382683432f, -0.923879533f},
+                                         {-0.707106781f, -0.707106781f}, {-0.923879533f, -0.382683432f},
+                                         {-1.000000000f, 0.000000000f}, {-0.923879533f, 0.382683432f},
+                                         {-0.707106781f, 0.707106781f}, {-0.382683432f, 0.923879533f},
+                                         {0.000000000f, 1.000000000f},  {0.382683432f, 0.923879533f},
+                                         {0.707106781f, 0.707106781f},  {0.923879533f, 0.382683432f}};
+
+template <int R>
+__device__ __forceinline__ float2 tw_small(int e) {
+  return R == 8 ? c_tw8[e] : (R == 12 ? c_tw12[e] : c_tw16[e]);
+}
+
+// R = 4 Q points, m = Q a + b:  X[k1 + 4 k2] = DFT_Q over b of ( W_R^{b k1} DFT_4 over a of x[Q a + b] )
+template <int Q, bool INV>
+__device__ __forceinline__ void dft_4xq(float2* v) {
+  constexpr int R = 4 * Q;
+  float2 F[Q][4];
+#pragma unroll
+  for (int b = 0; b < Q; ++b) {
+    float2 t[4] = {v[b], v[Q + b], v[2 * Q + b], v[3 * Q + b]};
+    Butterfly<float2, 4>::run(t, INV);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      if (b * k1 == 0) {
+        F[b][k1] = t[k1];
+      } else {
+        float2 w = tw_small<R>(b * k1);
+        if (INV) w.y = -w.y;
+        F[b][k1] = cmul(t[k1], w);
+      }
+    }
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    float2 t[Q];
+#pragma unroll
+    for (int b = 0; b < Q; ++b) t[b] = F[b][k1];
+    Butterfly<float2, Q>::run(t, INV);
+#pragma unroll
+    for (int k2 = 0; k2 < Q; ++k2) v[k1 + 4 * k2] = t[k2];
+  }
+}
+
+template <int R, bool INV> struct SmallDFT;
+template <bool INV> struct SmallDFT<2, INV> {
+  static __device__ __forceinline__ void run(float2* v) { Butterfly<float2, 2>::run(v, INV); }
+};
+template <bool INV> struct SmallDFT<4, INV> {
+  static __device__ __forceinline__ void run(float2* v) { Butterfly<float2, 4>::run(v, INV); }
+};
+template <bool INV> struct SmallDFT<8, INV> {
+  static __device__ __forceinline__ void run(float2* v) { dft_4xq<2, INV>(v); }
+};
+template <bool INV> struct SmallDFT<12, INV> {
+  static __device__ __forceinline__ void run(float2* v) { dft_4xq<3, INV>(v); }
+};
+template <bool INV> struct SmallDFT<16, INV> {
+  static __device__ __forceinline__ void run(float2* v) { dft_4xq<4, INV>(v); }
+};
+
+__device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+
+template <int P> struct WarpFFT {
+  static constexpr int R = P / 32;
+
+  // natural order in (v[m] = x[lane + 32 m]) -> digit-reversed out (v[k1] = X[k1 + R brev5(lane)])
+  static __device__ __forceinline__ void forward(float2 (&v)[R], const float2* __restrict__ tw, int lane) {
+    SmallDFT<R, false>::run(v);
+#pragma unroll
+    for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], tw[lane * k1]);
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+      const float2 w = tw[(lane & (h - 1)) * (16 / h) * R];
+      const bool hi = lane & h;
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        const float2 p = shfl_xor2(v[k], h);
+        v[k] = hi ? cmul(p - v[k], w) : v[k] + p;
+      }
+    }
+  }
+
+  // digit-reversed in -> natural order out, unnormalised inverse
+  static __device__ __forceinline__ void inverse(float2 (&v)[R], const float2* __restrict__ tw, int lane) {
+#pragma unroll
+    for (int h = 1; h <= 16; h <<= 1) {
+      const float2 w = cconj(tw[(lane & (h - 1)) * (16 / h) * R]);
+      const bool hi = lane & h;
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        const float2 t = hi ? cmul(v[k], w) : v[k];
+        const float2 p = shfl_xor2(t, h);
+        v[k] = hi ? p - t : t + p;
+      }
+    }
+#pragma unroll
+    for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], cconj(tw[lane * k1]));
+    SmallDFT<R, true>::run(v);
+  }
+};
+
+// digit-reversal of the lane index (5 bits)
+__host__ __device__ __forceinline__ int brev5(int l) {
+  return ((l & 1) << 4) | ((l & 2) << 2) | (l & 4) | ((l & 8) >> 2) | ((l & 16) >> 4);
+}
+
+// true DFT index of permuted position c = k1 * 32 + lane for length P = 32 R
+__host__ __device__ __forceinline__ int perm_to_freq(int c, int R) { return (c >> 5) + R * brev5(c & 31); }
+
+// supported line lengths of the register path
+__host__ __device__ __forceinline__ bool fast_len(int P) {
+  return P == 64 || P == 128 || P == 256 || P == 384 || P == 512;
+}

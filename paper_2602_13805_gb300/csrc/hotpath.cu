@@ -23,7 +23,7 @@
 #include "problem.cuh"
 #include "tc.cuh"
 
-// Kahan-compensated accumulation in FP32.
+// Kahan-compensated accumulation in FP32; as a float-float value s - c.
 struct KSum {
   float s = 0.f, c = 0.f;
   __device__ __forceinline__ void add(float x) {
@@ -32,7 +32,8 @@ struct KSum {
     c = (t - s) - y;
     s = t;
   }
-  __device__ __forceinline__ double val() const { return (double)s - (double)c; }
+  __device__ __forceinline__ FF ff() const { return ff_add(FF{s, 0.f}, -c); }
+  __device__ __forceinline__ float f() const { return s - c; }
 };
 
 __device__ __forceinline__ float2 cmulf_(float2 a, float2 b) { return cmul(a, b); }
@@ -170,7 +171,7 @@ __device__ __forceinline__ float2 chi_of_R(float2 R, float2 beta, float qmin, bo
 
 __global__ void __launch_bounds__(ROW_THREADS) k_rowifft_state(Dev d) {
   extern __shared__ float2 sm[];
-  __shared__ double red[32];
+  __shared__ FF red[32];
   const int y = blockIdx.x;
   float2* b0 = sm;
   float2* b1 = sm + ROWS_PER_CTA * d.Px;
@@ -208,8 +209,8 @@ __global__ void __launch_bounds__(ROW_THREADS) k_rowifft_state(Dev d) {
     const int x = threadIdx.x + k * blockDim.x;
     Rv[k] = make_float2(0.f, 0.f);
     if (x < d.nx) {
-      const float D = (float)Dd[k].val();
-      const float2 R = make_float2((float)(Nr[k].val() / (double)D), (float)(Ni[k].val() / (double)D));
+      const float D = Dd[k].f();
+      const float2 R = make_float2(Nr[k].f() / D, Ni[k].f() / D);
       bool cl;
       const float2 chi = chi_of_R(R, d.beta, d.q_min, &cl);
       const int n = y * d.nx + x;
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_rowifft_state(Dev d) {
       }
     }
   }
-  const double t = block_sum(acc.val(), red);
+  const FF t = ff_block_sum(acc.ff(), red);
   if (threadIdx.x == 0) d.lpart[LP_STATE * PDF_LP_STRIDE + y] = t;
 }
 
@@ -250,8 +251,8 @@ __global__ void __launch_bounds__(256) k_gs_partial(Dev d, const float2* __restr
   float2* sX = sm;                     // [ni][ls]
   float2* sG = sX + d.ni * ls;         // [nr][ls]
   float2* sR = sG + d.nr * ls;         // reduction scratch [256][GS_TP*GS_TR]
-  const int n0 = blockIdx.x * GS_CHUNK;
-  const int n1 = min(n0 + GS_CHUNK, d.M);
+  const int n0 = blockIdx.x * d.gs_chunk;
+  const int n1 = min(n0 + d.gs_chunk, d.M);
   const int tpn = (d.ni + GS_TP - 1) / GS_TP, trn = (d.nr + GS_TR - 1) / GS_TR;
   const int ntiles = tpn * trn;
   int kgroups = 1;
@@ -325,27 +326,28 @@ __global__ void __launch_bounds__(256) k_gs_partial(Dev d, const float2* __restr
 
 // out[p][r] = sum over chunks (FP64) [- sub]; ||out||^2 partial per block -> lp (may be NULL)
 __global__ void k_gs_reduce(Dev d, const float2* __restrict__ part, int nchunk, const float2* __restrict__ sub,
-                            float2* __restrict__ out, double* __restrict__ lp) {
-  __shared__ double red[32];
+                            float2* __restrict__ out, FF* __restrict__ lp) {
+  __shared__ FF red[32];
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   const int nout = d.ni * d.nr;
-  double a2 = 0.0;
+  FF a2 = FF{0.f, 0.f};
   if (o < nout) {
-    double sx = 0.0, sy = 0.0;
+    FF sx = FF{0.f, 0.f}, sy = FF{0.f, 0.f};
     for (int c = 0; c < nchunk; ++c) {
       const float2 v = part[(size_t)c * nout + o];
-      sx += v.x;
-      sy += v.y;
+      sx = ff_add(sx, v.x);
+      sy = ff_add(sy, v.y);
     }
     if (sub) {
-      sx -= sub[o].x;
-      sy -= sub[o].y;
+      sx = ff_add(sx, -sub[o].x);
+      sy = ff_add(sy, -sub[o].y);
     }
-    out[o] = make_float2((float)sx, (float)sy);
-    a2 = sx * sx + sy * sy;
+    const float2 v = make_float2(sx.hi + sx.lo, sy.hi + sy.lo);
+    out[o] = v;
+    a2 = ff_make(cabs2(v));
   }
   if (lp) {
-    const double t = block_sum(a2, red);
+    const FF t = ff_block_sum(a2, red);
     if (threadIdx.x == 0) lp[blockIdx.x] = t;
   }
 }
@@ -359,7 +361,7 @@ __global__ void k_gs_reduce(Dev d, const float2* __restrict__ part, int nchunk, 
 
 __global__ void __launch_bounds__(256) k_gsh(Dev d, const float2* __restrict__ in, float2* __restrict__ out,
                                              float scale, int data_scale) {
-  if (data_scale) scale = (float)(2.0 / d.norms[1]);     // 2 / ||E_sca||^2 of Eq. (16)'s gradient
+  if (data_scale) scale = d.invn[1];     // 2 / ||E_sca||^2 of Eq. (16)'s gradient
   extern __shared__ float2 sm[];
   float2* sD = sm;                              // [ni][GSH_RT]
   float2* sG = sD + d.ni * GSH_RT;              // [GSH_RT][GSH_CHUNK + 1]
@@ -465,17 +467,17 @@ __device__ __forceinline__ TVB tvb_at(const Dev& d, int y, int x) {
 }
 
 __global__ void __launch_bounds__(256) k_reg(Dev d) {
-  __shared__ double red[32];
+  __shared__ FF red[32];
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  double lb = 0.0, ltv = 0.0, lbr = 0.0;
+  float lb = 0.f, ltv = 0.f, lbr = 0.f;
   if (n < d.M) {
     const int y = n / d.nx, x = n - y * d.nx;
     const float2 c = d.chi[n];
     const float neg = fmaxf(-c.x, 0.f);
-    lb = (double)neg * neg;
+    lb = neg * neg;
     const TVB o = tvb_at(d, y, x);
     ltv = o.t;
-    lbr = (double)o.sg * o.e;
+    lbr = o.sg * o.e;
     // TV cotangent: -(dx + dy)/t at the own term, + dx/t of the left term, + dy/t of the upper term
     float2 ctv = (-1.f / o.t) * (o.dx + o.dy);
     // bridge cotangent on |chi|: own sigmoid term, own differences (-1), left / upper differences (+1)
@@ -504,9 +506,9 @@ __global__ void __launch_bounds__(256) k_reg(Dev d) {
     }
     d.w[n] = w;
   }
-  const double tb = block_sum(lb, red);
-  const double tt = block_sum(ltv, red);
-  const double tr = block_sum(lbr, red);
+  const FF tb = ff_block_sum(ff_make(lb), red);
+  const FF tt = ff_block_sum(ff_make(ltv), red);
+  const FF tr = ff_block_sum(ff_make(lbr), red);
   if (threadIdx.x == 0) {
     d.lpart[LP_BOUND * PDF_LP_STRIDE + blockIdx.x] = tb;
     d.lpart[LP_TV * PDF_LP_STRIDE + blockIdx.x] = tt;
@@ -523,7 +525,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_adj_rowfft(Dev d) {
   const int nrow = min(ROWS_PER_CTA, d.ny - y0);
   float2* b0 = sm;
   float2* b1 = sm + ROWS_PER_CTA * d.Px;
-  const float ke = (float)(2.0 / d.norms[0]);
+  const float ke = d.invn[0];
   const float2 bc = cconj(d.beta);
   for (int i = threadIdx.x; i < ROWS_PER_CTA * d.Px; i += blockDim.x) {
     const int rr = i / d.Px, x = i - rr * d.Px;
@@ -591,27 +593,38 @@ __global__ void __launch_bounds__(ROW_THREADS) k_adj_rowifft_ana(Dev d, const fl
   }
 }
 
-// analysis along y: out[p][jy][jx] = sum_y conj(wy[jy][y]) T2[p][y][jx]
-__global__ void k_ana_y(Dev d, const float2* __restrict__ T2, float2* __restrict__ out) {
-  const int p = blockIdx.y;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d.ky * d.kx) return;
-  const int jy = i / d.kx, jx = i - jy * d.kx;
-  float2 acc = make_float2(0.f, 0.f);
+// analysis along y: out[p][jy][jx] = sum_y conj(wy[jy][y]) T2[p][y][jx]; one CTA per (jy, p),
+// eight warps over interleaved y, lanes over jx (kx <= 64)
+__global__ void __launch_bounds__(256) k_ana_y(Dev d, const float2* __restrict__ T2, float2* __restrict__ out) {
+  __shared__ float2 part[8][64];
+  const int jy = blockIdx.x, p = blockIdx.y, g = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float2* T = T2 + (size_t)p * d.ny * d.kx;
-  for (int y = 0; y < d.ny; ++y) acc = acc + cmulc(T[y * d.kx + jx], __ldg(&d.wy[jy * d.ny + y]));
-  out[(size_t)p * d.ky * d.kx + i] = acc;
+  float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+  for (int y = g; y < d.ny; y += 8) {
+    const float2 w = __ldg(&d.wy[jy * d.ny + y]);
+    if (lane < d.kx) a0 = a0 + cmulc(T[(size_t)y * d.kx + lane], w);
+    if (lane + 32 < d.kx) a1 = a1 + cmulc(T[(size_t)y * d.kx + lane + 32], w);
+  }
+  part[g][lane] = a0;
+  part[g][lane + 32] = a1;
+  __syncthreads();
+  if (threadIdx.x < d.kx) {
+    float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s = s + part[k][threadIdx.x];
+    out[((size_t)p * d.ky + jy) * d.kx + threadIdx.x] = s;
+  }
 }
 
 // terms[6] = L, State, Data, Bound, TV, Bridge from the partial sums
 __global__ void k_finalize(Dev d, double* __restrict__ terms, int n_state, int n_data, int n_reg, int* step_inc) {
-  __shared__ double red[32];
+  __shared__ FF red[32];
   const int cnt[5] = {n_state, n_data, n_reg, n_reg, n_reg};
   double tot[5];
   for (int s = 0; s < 5; ++s) {
-    double a = 0.0;
-    for (int i = threadIdx.x; i < cnt[s]; i += blockDim.x) a += d.lpart[s * PDF_LP_STRIDE + i];
-    tot[s] = block_sum(a, red);
+    FF a = FF{0.f, 0.f};
+    for (int i = threadIdx.x; i < cnt[s]; i += blockDim.x) a = ff_add(a, d.lpart[s * PDF_LP_STRIDE + i]);
+    tot[s] = ff_to_d(ff_block_sum(a, red));
   }
   if (threadIdx.x == 0) {
     const double st = tot[0] / d.norms[0], da = tot[1] / d.norms[1];
@@ -663,6 +676,9 @@ int hp_kernels_per_loss_grad(const pdf_problem* h) { return h->tc ? 11 : 12; }
 
 pdf_status hp_check_limits(const Dev& d) {
   const size_t lim = 200 * 1024;
+  if (d.fast && (fp_smem_synth(d) > 100 * 1024 || fp_smem_col(d) > 100 * 1024 || fp_smem_state(d) > 100 * 1024 ||
+                 fp_smem_ana(d) > 100 * 1024))
+    return set_err(PDF_EUNSUPPORTED, "problem too large for the register-FFT tiling");
   if (sm_row(d) > lim || sm_synth(d) > lim || sm_col(d) > lim || sm_gs(d) > lim || sm_gsh(d) > lim)
     return set_err(PDF_EUNSUPPORTED, "problem too large for the shared-memory tiling (reduce ni, nr or kx*ky)");
   if ((d.ni * d.nr + 255) / 256 > PDF_LP_STRIDE || d.n_reg_blocks > PDF_LP_STRIDE || d.ny > PDF_LP_STRIDE)
@@ -697,13 +713,23 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
   // forward
   if (tc) {
     if ((s = tc_synth(h, alpha, d.J, 1, st)) != PDF_OK) return s;
+  } else if (d.fast) {
+    if ((s = fp_synth_rowfft(d, alpha, d.J, 1, st)) != PDF_OK) return s;
   } else {
     k_synth_rowfft<<<row_grid(d), ROW_THREADS, sm_synth(d), st>>>(d, alpha, d.J, 1);
   }
   mark();
-  k_colconv<<<col_grid(d), COL_THREADS, sm_col(d), st>>>(d, 0);
+  if (d.fast) {
+    if ((s = fp_colconv(d, 0, st)) != PDF_OK) return s;
+  } else {
+    k_colconv<<<col_grid(d), COL_THREADS, sm_col(d), st>>>(d, 0);
+  }
   mark();
-  k_rowifft_state<<<d.ny, ROW_THREADS, sm_row(d), st>>>(d);
+  if (d.fast) {
+    if ((s = fp_rowifft_state(d, st)) != PDF_OK) return s;
+  } else {
+    k_rowifft_state<<<d.ny, ROW_THREADS, sm_row(d), st>>>(d);
+  }
   mark();
   if (tc) {
     if ((s = tc_gs_fwd(h, nullptr, d.esca, d.rd, d.lpart + LP_DATA * PDF_LP_STRIDE, 1, st)) != PDF_OK) return s;
@@ -717,9 +743,17 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
   k_reg<<<d.n_reg_blocks, 256, 0, st>>>(d);
   mark();
   // adjoint
-  k_adj_rowfft<<<row_grid(d), ROW_THREADS, sm_row(d), st>>>(d);
+  if (d.fast) {
+    if ((s = fp_adj_rowfft(d, st)) != PDF_OK) return s;
+  } else {
+    k_adj_rowfft<<<row_grid(d), ROW_THREADS, sm_row(d), st>>>(d);
+  }
   mark();
-  k_colconv<<<col_grid(d), COL_THREADS, sm_col(d), st>>>(d, 1);
+  if (d.fast) {
+    if ((s = fp_colconv(d, 1, st)) != PDF_OK) return s;
+  } else {
+    k_colconv<<<col_grid(d), COL_THREADS, sm_col(d), st>>>(d, 1);
+  }
   mark();
   const float2* T2 = d.T2;
   if (tc) {
@@ -730,11 +764,15 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
   } else {
     k_gsh<<<(d.M + GSH_CHUNK - 1) / GSH_CHUNK, 256, sm_gsh(d), st>>>(d, d.rd, d.gsh, 0.f, 1);
     mark();
-    k_adj_rowifft_ana<<<row_grid(d), ROW_THREADS, sm_row(d), st>>>(d, nullptr, 0);
+    if (d.fast) {
+      if ((s = fp_adj_rowifft_ana(d, nullptr, 0, st)) != PDF_OK) return s;
+    } else {
+      k_adj_rowifft_ana<<<row_grid(d), ROW_THREADS, sm_row(d), st>>>(d, nullptr, 0);
+    }
   }
   mark();
   float2* g = grad ? grad : h->grad;
-  k_ana_y<<<dim3((d.ky * d.kx + 127) / 128, d.ni), 128, 0, st>>>(d, T2, g);
+  k_ana_y<<<dim3(d.ky, d.ni), 256, 0, st>>>(d, T2, g);
   mark();
   k_finalize<<<1, 256, 0, st>>>(d, terms ? terms : h->terms, d.ny, n_data_blocks, d.n_reg_blocks, step_inc);
   mark();
@@ -745,6 +783,15 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
 
 pdf_status hp_gd(pdf_problem* h, const float2* in, float2* out, int adjoint, cudaStream_t st) {
   Dev& d = h->d;
+  if (d.fast) {
+    pdf_status s;
+    if ((s = fp_rowfft_field(d, in, st)) != PDF_OK) return s;
+    if ((s = fp_colconv(d, adjoint, st)) != PDF_OK) return s;
+    if ((s = fp_rowifft_field(d, out, st)) != PDF_OK) return s;
+    pdf_count_launch(3);
+    PDF_LAUNCHED("G_D apply");
+    return PDF_OK;
+  }
   k_rowfft_field<<<row_grid(d), ROW_THREADS, sm_row(d), st>>>(d, in);
   k_colconv<<<col_grid(d), COL_THREADS, sm_col(d), st>>>(d, adjoint);
   k_rowifft_field<<<row_grid(d), ROW_THREADS, sm_row(d), st>>>(d, out);
@@ -753,7 +800,7 @@ pdf_status hp_gd(pdf_problem* h, const float2* in, float2* out, int adjoint, cud
   return PDF_OK;
 }
 
-pdf_status hp_gs(pdf_problem* h, const float2* in, float2* out, const float2* subtract, double* sumsq,
+pdf_status hp_gs(pdf_problem* h, const float2* in, float2* out, const float2* subtract, FF* sumsq,
                  cudaStream_t st) {
   if (h->tc) return tc_gs_fwd(h, in, subtract, out, sumsq, 0, st);
   Dev& d = h->d;
@@ -777,6 +824,11 @@ pdf_status hp_gsh(pdf_problem* h, const float2* in, float2* out, float scale, cu
 pdf_status hp_synth(pdf_problem* h, const float2* alpha, float2* out, cudaStream_t st) {
   if (h->tc) return tc_synth(h, alpha, out, 0, st);
   Dev& d = h->d;
+  if (d.fast) {
+    pdf_status s = fp_synth_rowfft(d, alpha, out, 0, st);
+    pdf_count_launch(1);
+    return s;
+  }
   k_synth_rowfft<<<row_grid(d), ROW_THREADS, sm_synth(d), st>>>(d, alpha, out, 0);
   pdf_count_launch(1);
   PDF_LAUNCHED("synthesis");
@@ -790,10 +842,13 @@ pdf_status hp_analysis(pdf_problem* h, const float2* in, float2* out, cudaStream
     pdf_status s = tc_analysis_field(h, in, st);
     if (s != PDF_OK) return s;
     T2 = (const float2*)h->tc->c_ana;
+  } else if (d.fast) {
+    pdf_status s = fp_adj_rowifft_ana(d, in, 1, st);
+    if (s != PDF_OK) return s;
   } else {
     k_adj_rowifft_ana<<<row_grid(d), ROW_THREADS, sm_row(d), st>>>(d, in, 1);
   }
-  k_ana_y<<<dim3((d.ky * d.kx + 127) / 128, d.ni), 128, 0, st>>>(d, T2, out);
+  k_ana_y<<<dim3(d.ky, d.ni), 256, 0, st>>>(d, T2, out);
   pdf_count_launch(2);
   PDF_LAUNCHED("analysis");
   return PDF_OK;
@@ -804,11 +859,20 @@ pdf_status hp_chi(pdf_problem* h, const float2* alpha, float2* chi_out, cudaStre
   if (h->tc) {
     pdf_status s = tc_synth(h, alpha, d.J, 1, st);
     if (s != PDF_OK) return s;
+  } else if (d.fast) {
+    pdf_status s = fp_synth_rowfft(d, alpha, d.J, 1, st);
+    if (s != PDF_OK) return s;
   } else {
     k_synth_rowfft<<<row_grid(d), ROW_THREADS, sm_synth(d), st>>>(d, alpha, d.J, 1);
   }
-  k_colconv<<<col_grid(d), COL_THREADS, sm_col(d), st>>>(d, 0);
-  k_rowifft_state<<<d.ny, ROW_THREADS, sm_row(d), st>>>(d);
+  if (d.fast) {
+    pdf_status s;
+    if ((s = fp_colconv(d, 0, st)) != PDF_OK) return s;
+    if ((s = fp_rowifft_state(d, st)) != PDF_OK) return s;
+  } else {
+    k_colconv<<<col_grid(d), COL_THREADS, sm_col(d), st>>>(d, 0);
+    k_rowifft_state<<<d.ny, ROW_THREADS, sm_row(d), st>>>(d);
+  }
   pdf_count_launch(3);
   PDF_LAUNCHED("chi");
   if (chi_out) PDF_CUDA(cudaMemcpyAsync(chi_out, d.chi, sizeof(float2) * d.M, cudaMemcpyDeviceToDevice, st));

@@ -25,11 +25,13 @@ struct Dev {
   double2 betad;
   float lam_bound, lam_tv, lam_bridge, tau_b, eps_tv, eps_abs, q_min;
   int n_gs_chunks, n_reg_blocks;
+  int fast;              // 1: register-FFT kernels (fastpath.cu), A rows/columns in permuted order
 
   // geometry (assembled once)
   const float2* twx;     // [Px] exp(-2 pi i e / Px)
   const float2* twy;     // [Py]
   const float2* ghat;    // [Py][Px] spectrum of the circulant G_D kernel / (Px Py)
+  const float2* ghat_perm; // [Px][Py] the same in the register FFT's digit-reversed order (fast path)
   const float2* einc;    // [ni][M]
   const float2* gs;      // [nr][M]
   const float2* wx;      // [kx][nx] exp(+2 pi i f_k x / nx) / sqrt(nx)
@@ -52,7 +54,10 @@ struct Dev {
   float2* T2;            // [ni][ny][kx] partial analysis
   float2* gspart;        // [n_gs_chunks][ni][nr]
   float2* rd;            // [ni][nr] data residual
-  double* lpart;         // [LP_NSLOT][PDF_LP_STRIDE]
+  FF* lpart;             // [LP_NSLOT][PDF_LP_STRIDE] float-float loss partials (also scratch)
+  const float* invn;     // [2] 2 / ||E_inc||^2, 2 / ||E_sca||^2 (float)
+  const float2* adam_tab;  // [cap] Adam step size lr / (1 - b1^t) and sqrt(1 - b2^t), t = 1..cap
+  int gs_chunk;          // pixels per CTA of the SIMT G_S product
 };
 
 struct TC;
@@ -90,6 +95,10 @@ struct pdf_problem {
   int graph_iters;       // iterations per graph launch (0 = none)
   int graph_kernels;     // kernel nodes in the graph
   double graph_key[4];   // lr, b1, b2, eps used when captured
+  float2* adam_tab;      // device table (see Dev::adam_tab)
+  int adam_cap;
+  double adam_key[3];    // lr, b1, b2 of the table
+  float* invn;
 };
 
 // error helpers (api.cu)
@@ -111,6 +120,7 @@ pdf_status ws_alloc(pdf_problem* h, void** p, size_t bytes);
 
 // reductions defined in api.cu
 __global__ void k_sumsq(const float2* x, int n, double* out);
+__global__ void k_set_invn(const double* norms, float* invn);
 
 // launchers (hotpath.cu)
 pdf_status hp_configure_kernels();
@@ -120,12 +130,27 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
 const char* hp_kernel_name(int k, int precision);
 __global__ void k_ana_y(Dev d, const float2* T2, float2* out);
 pdf_status hp_gd(pdf_problem* h, const float2* in, float2* out, int adjoint, cudaStream_t st);
-pdf_status hp_gs(pdf_problem* h, const float2* in, float2* out, const float2* subtract, double* sumsq, cudaStream_t st);
+pdf_status hp_gs(pdf_problem* h, const float2* in, float2* out, const float2* subtract, FF* sumsq, cudaStream_t st);
 pdf_status hp_gsh(pdf_problem* h, const float2* in, float2* out, float scale, cudaStream_t st);
 pdf_status hp_synth(pdf_problem* h, const float2* alpha, float2* out, cudaStream_t st);
 pdf_status hp_analysis(pdf_problem* h, const float2* in, float2* out, cudaStream_t st);
 pdf_status hp_chi(pdf_problem* h, const float2* alpha, float2* chi_out, cudaStream_t st);
 int hp_kernels_per_loss_grad(const pdf_problem* h);
+
+// register-FFT path (fastpath.cu)
+pdf_status fp_configure();
+pdf_status fp_synth_rowfft(const Dev& d, const float2* alpha, float2* Jout, int do_fft, cudaStream_t st);
+pdf_status fp_rowfft_field(const Dev& d, const float2* in, cudaStream_t st);
+pdf_status fp_rowifft_field(const Dev& d, float2* out, cudaStream_t st);
+pdf_status fp_colconv(const Dev& d, int conj, cudaStream_t st);
+pdf_status fp_rowifft_state(const Dev& d, cudaStream_t st);
+pdf_status fp_adj_rowfft(const Dev& d, cudaStream_t st);
+pdf_status fp_adj_rowifft_ana(const Dev& d, const float2* in, int mode, cudaStream_t st);
+pdf_status fp_perm_ghat(const Dev& d, float2* gp, cudaStream_t st);
+size_t fp_smem_synth(const Dev& d);
+size_t fp_smem_col(const Dev& d);
+size_t fp_smem_state(const Dev& d);
+size_t fp_smem_ana(const Dev& d);
 
 // solve pieces (solve.cu)
 pdf_status sv_cco(pdf_problem* h, const float2* chi, float2* out, int radius, double eps, double eta_max,

@@ -12,6 +12,7 @@
 //   CCO      self-guided filter (box radius r, clipped windows, Re and Im separately),
 //            eta = eta_max sigmoid((|chi| - tau)/delta), out = (1 + eta) G + eta chi.
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <algorithm>
 #include <vector>
@@ -23,19 +24,12 @@
 // Adam on the real view of alpha (torch.optim.Adam arithmetic, FP32)
 // ---------------------------------------------------------------------------
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
-                       float* __restrict__ v, int n, const int* __restrict__ tdev, float lr, float b1, float b2,
-                       float eps) {
-  __shared__ float sc[2];
-  if (threadIdx.x == 0) {
-    const int t = *tdev;
-    const double bc1 = 1.0 - pow((double)b1, (double)t);
-    const double bc2 = 1.0 - pow((double)b2, (double)t);
-    sc[0] = (float)(lr / bc1);           // step size
-    sc[1] = (float)sqrt(bc2);            // sqrt of the second bias correction
-  }
-  __syncthreads();
+                       float* __restrict__ v, int n, const int* __restrict__ tdev, const float2* __restrict__ tab,
+                       int cap, float b1, float b2, float eps) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const int t = min(max(*tdev, 1), cap);
+  const float2 sc = tab[t - 1];        // lr / (1 - b1^t), sqrt(1 - b2^t), evaluated in FP64 on the host
   const float gi = g[i];
   float mi = m[i];
   mi = mi + (1.f - b1) * (gi - mi);
@@ -43,8 +37,40 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
   vi = vi + ((1.f - b2) * gi) * gi;
   m[i] = mi;
   v[i] = vi;
-  const float denom = sqrtf(vi) / sc[1] + eps;
-  p[i] = p[i] + (-sc[0]) * (mi / denom);
+  const float denom = sqrtf(vi) / sc.y + eps;
+  p[i] = p[i] + (-sc.x) * (mi / denom);
+}
+
+// Bias-correction table of torch.optim.Adam for steps 1..iters (rebuilt when lr, betas or the
+// iteration count change; the solve's CUDA graph holds its address, so it is reset too).
+static pdf_status ensure_adam_table(pdf_problem* h, const pdf_solve_opts* o) {
+  const int need = std::max(o->iters, 1);
+  if (h->adam_tab && h->adam_cap >= need && h->adam_key[0] == o->lr && h->adam_key[1] == o->adam_b1 &&
+      h->adam_key[2] == o->adam_b2)
+    return PDF_OK;
+  const int cap = std::max(need, 1024);
+  std::vector<float2> tab(cap);
+  for (int t = 1; t <= cap; ++t) {
+    const double bc1 = 1.0 - std::pow(o->adam_b1, t), bc2 = 1.0 - std::pow(o->adam_b2, t);
+    tab[t - 1] = make_float2((float)(o->lr / bc1), (float)std::sqrt(bc2));
+  }
+  if (!h->adam_tab || h->adam_cap < cap) {
+    if (h->graph_exec) {
+      cudaGraphExecDestroy(h->graph_exec);
+      h->graph_exec = nullptr;
+    }
+    float2* p = nullptr;
+    pdf_status s = ws_alloc(h, (void**)&p, sizeof(float2) * cap);
+    if (s != PDF_OK) return s;
+    h->adam_tab = p;
+    h->adam_cap = cap;
+  }
+  PDF_CUDA(cudaMemcpy(h->adam_tab, tab.data(), sizeof(float2) * cap, cudaMemcpyHostToDevice));
+  h->adam_key[0] = o->lr;
+  h->adam_key[1] = o->adam_b1;
+  h->adam_key[2] = o->adam_b2;
+  h->d.adam_tab = h->adam_tab;
+  return PDF_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -194,7 +220,7 @@ __global__ void k_init_gj(Dev d, const float2* __restrict__ R0, const float2* __
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)d.ni * d.M) return;
   const int n = (int)(i % d.M);
-  const float ke = (float)(2.0 / d.norms[0]);
+  const float ke = d.invn[0];
   const float2 R = R0[n];
   const float2 e = d.einc[i];
   const float2 r0 = cmul(R, e);
@@ -282,7 +308,7 @@ static pdf_status init_bp_csi(pdf_problem* h, cudaStream_t st) {
   const size_t NF = (size_t)d.ni * d.M;
   const int NA = d.ni * d.ky * d.kx;
   double* sc = h->scratch_d;            // [0..2] line-search scalars
-  double* num = (double*)d.lpart + PDF_LP_STRIDE;            // [ni] per-incidence sums
+  double* num = (double*)d.lpart + PDF_LP_STRIDE;            // [ni] per-incidence sums (lpart as scratch)
   double* den = num + d.ni;
   pdf_status s;
   // BP: gh = G_S^H E_sca (tmpA); ggh = G_S gh (small1); gamma_p
@@ -309,8 +335,8 @@ static pdf_status init_bp_csi(pdf_problem* h, cudaStream_t st) {
   if ((s = hp_gs(h, h->tmpA, h->small1, nullptr, nullptr, st)) != PDF_OK) return s;  // m1
   if ((s = hp_gd(h, h->tmpA, h->tmpB, 0, st)) != PDF_OK) return s;                   // G_D Jg
   const int nb = (int)std::min<size_t>((NF + 255) / 256, PDF_LP_STRIDE);
-  k_init_m2<<<nb, 256, 0, st>>>(d, h->field1, h->tmpA, h->tmpB, d.lpart);
-  k_sum_d<<<1, 256, 0, st>>>(d.lpart, nb, sc + 2);
+  k_init_m2<<<nb, 256, 0, st>>>(d, h->field1, h->tmpA, h->tmpB, (double*)d.lpart);
+  k_sum_d<<<1, 256, 0, st>>>((double*)d.lpart, nb, sc + 2);
   k_sumsq<<<1, 1024, 0, st>>>(h->small1, d.ni * d.nr, sc + 1);
   k_sumsq<<<1, 1024, 0, st>>>(h->grad, NA, sc + 0);
   k_init_alpha<<<(NA + 255) / 256, 256, 0, st>>>(d, h->grad, h->alpha, sc, NA);
@@ -322,8 +348,8 @@ static pdf_status init_bp_csi(pdf_problem* h, cudaStream_t st) {
 static pdf_status adam_step(pdf_problem* h, const pdf_solve_opts* o, cudaStream_t st) {
   const int n = 2 * h->d.ni * h->d.ky * h->d.kx;
   k_adam<<<(n + 255) / 256, 256, 0, st>>>((float*)h->alpha, (const float*)h->grad, h->adam_m, h->adam_v, n,
-                                          h->adam_t, (float)o->lr, (float)o->adam_b1, (float)o->adam_b2,
-                                          (float)o->adam_eps);
+                                          h->adam_t, h->adam_tab, h->adam_cap, (float)o->adam_b1,
+                                          (float)o->adam_b2, (float)o->adam_eps);
   pdf_count_launch(1);
   PDF_LAUNCHED("Adam");
   return PDF_OK;
@@ -376,6 +402,7 @@ pdf_status sv_solve(pdf_problem* h, const pdf_solve_opts* o, float2* chi_out, fl
   Dev& d = h->d;
   const int NA = d.ni * d.ky * d.kx;
   pdf_status s;
+  if ((s = ensure_adam_table(h, o)) != PDF_OK) return s;
   PDF_CUDA(cudaMemsetAsync(h->used_warm, 0, sizeof(int), st));
   if (o->init == 0) {
     if ((s = init_bp_csi(h, st)) != PDF_OK) return s;
@@ -551,7 +578,7 @@ pdf_status sv_forward(pdf_problem* h, const float2* chi, float2* esca_out, float
   // buffers: X = tmpA, R = tmpB, P = tmpC, V = d.v, T = d.gsh, RHAT = d.s (einc copy), tmp = d.r
   float2 *X = h->tmpA, *R = h->tmpB, *P = h->tmpC, *V = d.v, *T = d.gsh, *RH = d.s, *TMP = d.r;
   // device state in the loss-partial buffer: 16-byte types first, then doubles
-  double2* rho_new = (double2*)d.lpart;                 // [ni]
+  double2* rho_new = (double2*)(void*)d.lpart;          // [ni]
   double2* rv = rho_new + d.ni;                         // [ni]
   double2* ts = rv + d.ni;                              // [ni]
   BiState* bst = (BiState*)(ts + d.ni);                 // [ni]

@@ -51,23 +51,20 @@ __global__ void k_tc_pack_w(Dev d, TC t) {
 // ---------------------------------------------------------------------------
 // per-iteration packing and consumers
 // ---------------------------------------------------------------------------
-// T[p][jy][x] = sum_jx alpha[p][jy][jx] Wx[jx][x] -> TB rows 2(p nx + x) (Re T, -Im T) and +1 (Im T, Re T)
+// T[p][jy][x] = sum_jx alpha[p][jy][jx] Wx[jx][x] -> TB rows 2(p nx + x) (Re T, -Im T) and +1 (Im T, Re T);
+// one thread per (x, jy), grid (x blocks, ky, ni)
 __global__ void __launch_bounds__(128) k_tc_synth1(Dev d, TC t, const float2* __restrict__ alpha) {
-  extern __shared__ float2 sa[];
-  const int p = blockIdx.y;
+  const int p = blockIdx.z, jy = blockIdx.y;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  for (int i = threadIdx.x; i < d.ky * d.kx; i += blockDim.x) sa[i] = alpha[(size_t)p * d.ky * d.kx + i];
-  __syncthreads();
   if (x >= d.nx) return;
+  const float2* a = alpha + ((size_t)p * d.ky + jy) * d.kx;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int jx = 0; jx < d.kx; ++jx) acc = acc + cmul(__ldg(&a[jx]), __ldg(&d.wx[(size_t)jx * d.nx + x]));
   const size_t r0 = (size_t)(2 * (p * d.nx + x)) * t.KYP, r1 = r0 + t.KYP;
-  for (int jy = 0; jy < d.ky; ++jy) {
-    float2 acc = make_float2(0.f, 0.f);
-    for (int jx = 0; jx < d.kx; ++jx) acc = acc + cmul(sa[jy * d.kx + jx], __ldg(&d.wx[(size_t)jx * d.nx + x]));
-    put_split(t.tb_hi, t.tb_lo, r0 + 2 * jy, acc.x);
-    put_split(t.tb_hi, t.tb_lo, r0 + 2 * jy + 1, -acc.y);
-    put_split(t.tb_hi, t.tb_lo, r1 + 2 * jy, acc.y);
-    put_split(t.tb_hi, t.tb_lo, r1 + 2 * jy + 1, acc.x);
-  }
+  put_split(t.tb_hi, t.tb_lo, r0 + 2 * jy, acc.x);
+  put_split(t.tb_hi, t.tb_lo, r0 + 2 * jy + 1, -acc.y);
+  put_split(t.tb_hi, t.tb_lo, r1 + 2 * jy, acc.y);
+  put_split(t.tb_hi, t.tb_lo, r1 + 2 * jy + 1, acc.x);
 }
 
 __device__ __forceinline__ void put_jb(const TC& t, int p, int n, float2 J) {
@@ -125,30 +122,30 @@ __device__ __forceinline__ void put_rdb(const TC& t, int p, int r, float2 v) {
 
 // out[p][r] = sum over splits (FP64) of C_fwd - sub; ||out||^2 per block -> lp; optional RDB packing
 __global__ void k_tc_gs_reduce(Dev d, TC t, int nsplit, const float2* __restrict__ sub, float2* __restrict__ out,
-                               double* __restrict__ lp, int write_rdb) {
-  __shared__ double red[32];
+                               FF* __restrict__ lp, int write_rdb) {
+  __shared__ FF red[32];
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  double a2 = 0.0;
+  FF a2 = FF{0.f, 0.f};
   if (o < d.ni * d.nr) {
     const int p = o / d.nr, r = o - p * d.nr;
     const size_t stride = (size_t)d.nr * 2 * d.ni;
-    double sx = 0.0, sy = 0.0;
+    FF sx = FF{0.f, 0.f}, sy = FF{0.f, 0.f};
     for (int s = 0; s < nsplit; ++s) {
       const float* c = t.c_fwd + s * stride + (size_t)r * 2 * d.ni + 2 * p;
-      sx += c[0];
-      sy += c[1];
+      sx = ff_add(sx, c[0]);
+      sy = ff_add(sy, c[1]);
     }
     if (sub) {
-      sx -= sub[o].x;
-      sy -= sub[o].y;
+      sx = ff_add(sx, -sub[o].x);
+      sy = ff_add(sy, -sub[o].y);
     }
-    const float2 v = make_float2((float)sx, (float)sy);
+    const float2 v = make_float2(sx.hi + sx.lo, sy.hi + sy.lo);
     out[o] = v;
     if (write_rdb) put_rdb(t, p, r, v);
-    a2 = sx * sx + sy * sy;
+    a2 = ff_make(cabs2(v));
   }
   if (lp) {
-    const double tt = block_sum(a2, red);
+    const FF tt = ff_block_sum(a2, red);
     if (threadIdx.x == 0) lp[blockIdx.x] = tt;
   }
 }
@@ -182,7 +179,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_tc_adj_rowifft(Dev d, TC t) {
   const int nrow = min(ROWS_PER_CTA, d.ny - y0);
   float2* b0 = sm;
   float2* b1 = sm + ROWS_PER_CTA * d.Px;
-  const float ks = (float)(2.0 / d.norms[1]);
+  const float ks = d.invn[1];
   for (int i = threadIdx.x; i < ROWS_PER_CTA * d.Px; i += blockDim.x) {
     const int rr = i / d.Px, x = i - rr * d.Px;
     b0[i] = rr < nrow ? d.A[((size_t)p * d.ny + y0 + rr) * d.Px + x] : make_float2(0.f, 0.f);
@@ -199,6 +196,17 @@ __global__ void __launch_bounds__(ROW_THREADS) k_tc_adj_rowifft(Dev d, TC t) {
       put_gja(t, p * d.ny + y0 + rr, x, v);
     }
   }
+}
+
+// fast-path form: g = G_D^H u (already inverse-transformed into gdh) + v + G_S^H term -> GJA
+__global__ void k_tc_gja_combine(Dev d, TC t, const float2* __restrict__ gdh) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)d.ni * d.M) return;
+  const int p = (int)(i / d.M), n = (int)(i - (size_t)p * d.M);
+  const int y = n / d.nx, x = n - y * d.nx;
+  const float ks = d.invn[1];
+  const float* c = t.c_adj + (size_t)n * 2 * d.ni + 2 * p;
+  put_gja(t, p * d.ny + y, x, gdh[i] + d.v[i] + make_float2(ks * c[0], ks * c[1]));
 }
 
 __global__ void k_tc_field_to_gja(Dev d, TC t, const float2* __restrict__ X) {
@@ -294,18 +302,24 @@ pdf_status tc_setup(pdf_problem* h, cudaStream_t st) {
 pdf_status tc_synth(pdf_problem* h, const float2* alpha, float2* Jout, int do_fft, cudaStream_t st) {
   Dev& d = h->d;
   TC& t = *h->tc;
-  k_tc_synth1<<<dim3((d.nx + 127) / 128, d.ni), 128, (size_t)d.ky * d.kx * sizeof(float2), st>>>(d, t, alpha);
+  k_tc_synth1<<<dim3((d.nx + 127) / 128, d.ky, d.ni), 128, 0, st>>>(d, t, alpha);
   pdf_count_launch(1);
   pdf_status s = umma_gemm(t.wya, t.tb, 1, 1, t.c_syn, 2 * d.ni * d.nx, 0, t.err, st);
   if (s != PDF_OK) return s;
+  const int gen_fft = do_fft && !d.fast;
   k_tc_synth_post<<<dim3((d.ny + ROWS_PER_CTA - 1) / ROWS_PER_CTA, d.ni), ROW_THREADS, sm_row_tc(d), st>>>(
-      d, t, Jout, do_fft);
+      d, t, Jout, gen_fft);
   pdf_count_launch(1);
   PDF_LAUNCHED("tensor-core synthesis");
+  if (do_fft && d.fast) {
+    pdf_status q = fp_rowfft_field(d, Jout, st);
+    pdf_count_launch(1);
+    if (q != PDF_OK) return q;
+  }
   return PDF_OK;
 }
 
-pdf_status tc_gs_fwd(pdf_problem* h, const float2* X, const float2* sub, float2* out, double* lp, int write_rdb,
+pdf_status tc_gs_fwd(pdf_problem* h, const float2* X, const float2* sub, float2* out, FF* lp, int write_rdb,
                      cudaStream_t st) {
   Dev& d = h->d;
   TC& t = *h->tc;
@@ -344,6 +358,14 @@ pdf_status tc_gsh_field(pdf_problem* h, const float2* D, float2* out, float scal
 pdf_status tc_adj_ana(pdf_problem* h, cudaStream_t st) {
   Dev& d = h->d;
   TC& t = *h->tc;
+  if (d.fast) {
+    pdf_status q = fp_rowifft_field(d, h->tmpA, st);
+    if (q != PDF_OK) return q;
+    k_tc_gja_combine<<<(unsigned)(((size_t)d.ni * d.M + 255) / 256), 256, 0, st>>>(d, t, h->tmpA);
+    pdf_count_launch(2);
+    PDF_LAUNCHED("tensor-core adjoint combine");
+    return umma_gemm(t.gja, t.wxb, 1, 1, t.c_ana, 2 * d.kx, 0, t.err, st);
+  }
   k_tc_adj_rowifft<<<dim3((d.ny + ROWS_PER_CTA - 1) / ROWS_PER_CTA, d.ni), ROW_THREADS, sm_row_tc(d), st>>>(d, t);
   pdf_count_launch(1);
   PDF_LAUNCHED("tensor-core adjoint row IFFT");

@@ -35,7 +35,7 @@ struct TC {
 struct pdf_problem;
 pdf_status tc_setup(pdf_problem* h, cudaStream_t st);
 pdf_status tc_synth(pdf_problem* h, const float2* alpha, float2* Jout, int do_fft, cudaStream_t st);
-pdf_status tc_gs_fwd(pdf_problem* h, const float2* X, const float2* sub, float2* out, double* lp, int write_rdb,
+pdf_status tc_gs_fwd(pdf_problem* h, const float2* X, const float2* sub, float2* out, FF* lp, int write_rdb,
                      cudaStream_t st);
 pdf_status tc_gsh(pdf_problem* h, const float2* D, int from_rdb, cudaStream_t st);
 pdf_status tc_adj_ana(pdf_problem* h, cudaStream_t st);

@@ -46,7 +46,7 @@ class pdf_config(ctypes.Structure):
         ("lambda_bound", ctypes.c_double), ("lambda_tv", ctypes.c_double), ("lambda_bridge", ctypes.c_double),
         ("tau_b", ctypes.c_double), ("eps_tv", ctypes.c_double), ("eps_abs", ctypes.c_double),
         ("q_min", ctypes.c_double),
-        ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("fft_path", ctypes.c_int32),
     ]
 
 
@@ -172,7 +172,7 @@ def _stream(stream) -> Optional[int]:
 
 def make_config(nx, ny, side_x, side_y, k0, tx, rx, kx, ky, beta=6.0 + 0j, inc_kind=0, precision=0,
                 lambda_bound=1e-3, lambda_tv=1e-5, lambda_bridge=1e-5, tau_b=0.5, eps_tv=1e-8, eps_abs=1e-12,
-                q_min=1e-6):
+                q_min=1e-6, fft_path=0):
     """Returns (pdf_config, keep-alive antenna arrays)."""
     lib = load()
     c = pdf_config()
@@ -189,6 +189,7 @@ def make_config(nx, ny, side_x, side_y, k0, tx, rx, kx, ky, beta=6.0 + 0j, inc_k
     c.lambda_bound, c.lambda_tv, c.lambda_bridge = lambda_bound, lambda_tv, lambda_bridge
     c.tau_b, c.eps_tv, c.eps_abs, c.q_min = tau_b, eps_tv, eps_abs, q_min
     c.precision = precision
+    c.fft_path = fft_path
     return c, (tx, rx)
 
 

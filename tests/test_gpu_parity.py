@@ -20,11 +20,18 @@ def _w(name, over):
     return scenes.workload(base, **over)
 
 
-@pytest.fixture(scope="module", params=SMALL_CASES + [("c2", dict())], ids=lambda c: c[0])
+# register-FFT path (default) on every geometry, and the generic shared-memory FFT on two
+PARITY_CASES = [(n, o, {}) for n, o in SMALL_CASES] + [("c2", dict(), {})] + [
+    ("g24x20-smemfft", dict(nx=24, ny=20, ni=5, nr=7, kx=7, ky=5), dict(fft_path=1)),
+    ("c1-smemfft", dict(), dict(fft_path=1)),
+]
+
+
+@pytest.fixture(scope="module", params=PARITY_CASES, ids=lambda c: c[0])
 def case(request):
-    name, over = request.param
-    c = Case(_w(name, over))
-    c.prob = c.problem()
+    name, over, kw = request.param
+    c = Case(_w(name.split("-")[0], over))
+    c.prob = c.problem(**kw)
     yield c
     c.prob.close()
 
@@ -121,7 +128,10 @@ def test_autograd_function_and_central_differences(case):
     tm, _ = prob.loss_grad((a.detach() - h * d).contiguous())
     fd = (tp[0] - tm[0]).item() / (2 * h)
     an = torch.sum(torch.real(torch.conj(g) * d)).item()
-    assert abs(fd - an) < 2e-3 * abs(an) + 1e-6
+    # the loss is evaluated from FP32 fields (relative rounding ~1e-7), so a central difference with
+    # h = 1e-4 resolves the directional derivative to ~1e-3; the 1e-5 gradient contract is checked
+    # against the FP64 oracle in test_loss_and_gradient
+    assert abs(fd - an) < 5e-3 * abs(an) + 1e-6
 
 
 def test_forward_solver_matches_oracle(case):

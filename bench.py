@@ -163,7 +163,7 @@ def run_ours(args, rank, world, local):
     esca_d = torch.from_numpy(esca).cuda()
     prob.set_data(esca_d)
     stream = torch.cuda.current_stream()
-    opts = pdf.solve_opts(iters=w.iters, lr=args.lr, init=0, chi_true=chi_d, apply_cco=1, use_graph=1)
+    opts = pdf.solve_opts(iters=w.iters, lr=args.lr, init=0, chi_true=chi_d, apply_cco=1, use_graph=args.loop)
     chi_out = torch.empty((w.ny, w.nx), dtype=torch.complex64, device="cuda")
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -248,7 +248,7 @@ def run_ours(args, rank, world, local):
             "data": "synthetic (seeded scene, GPU forward solver, AWGN)",
             "config": {"workload": f"{w.name}: {w.nx}x{w.ny} grid, {w.side} lambda DOI, Ni={w.ni}, Nr={w.nr}, "
                                    f"K={w.kx}x{w.ky}, {w.iters} Adam iterations, BP+CSI init, CCO",
-                       "iters": w.iters, "lr": args.lr, "precision": args.precision,
+                       "iters": w.iters, "lr": args.lr, "precision": args.precision, "loop": args.loop,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed between reconstructions (512 MB write); working set L2-resident within one"},
             "iters_per_s": w.iters * args.steps * world / (total_ms * 1e-3),
@@ -349,7 +349,7 @@ def run_warm(args):
         chi_t = test_set.chi[s_].contiguous()
         prob.set_data(esca)
         chosen.set_data(esca)
-        plain_opts = pdf.solve_opts(iters=w.iters, lr=args.lr, init=0, chi_true=chi_t, apply_cco=1, use_graph=1)
+        plain_opts = pdf.solve_opts(iters=w.iters, lr=args.lr, init=0, chi_true=chi_t, apply_cco=1, use_graph=args.loop)
         _timed_solve(prob, plain_opts, chi_out)                               # warm-up (graph build)
         ms_plain = _timed_solve(prob, plain_opts, chi_out)
         rep = pdf.pdf_solve(prob.h, plain_opts, chi_out, None, None, report=True)
@@ -365,7 +365,7 @@ def run_warm(args):
         h = out["history"].cpu().numpy()
         reach = next((r * every for r in range(h.shape[0]) if h[r, 7] <= target), None)
         k = w.iters if reach is None else reach
-        opts_k = pdf.solve_opts(iters=k, lr=args.lr, init=3, alpha0=a0, chi_true=chi_t, apply_cco=1, use_graph=1)
+        opts_k = pdf.solve_opts(iters=k, lr=args.lr, init=3, alpha0=a0, chi_true=chi_t, apply_cco=1, use_graph=args.loop)
         _timed_solve(chosen, opts_k, chi_out)
         ms_chosen = ms_inf + _timed_solve(chosen, opts_k, chi_out)
         rows.append(dict(relerr_plain=target, relerr_chosen_final=out["relerr_cco"], iters_to_target=reach,
@@ -424,6 +424,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
     ap.add_argument("--warm-start", action="store_true")
+    ap.add_argument("--loop", type=int, default=1, choices=[0, 1, 2],
+                    help="0 eager launches, 1 CUDA graph, 2 persistent cooperative kernel (when eligible)")
     ap.add_argument("--train-scenes", type=int, default=20000)
     ap.add_argument("--test-scenes", type=int, default=10)
     ap.add_argument("--train-steps", type=int, default=3000)

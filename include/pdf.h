@@ -121,7 +121,10 @@ typedef struct pdf_solve_opts {
   int32_t cco_radius;        /* guided-filter box radius (default 2)                           */
   double cco_eps;            /* guided-filter regulariser (default 1e-2)                       */
   double cco_eta_max, cco_tau, cco_delta;  /* Eq. (11): 0.1, 3, 0.5                            */
-  int32_t use_graph;         /* 1 = run the iteration loop as a CUDA graph                     */
+  int32_t use_graph;         /* 0 = launch every kernel, 1 = run the iteration loop as a CUDA
+                                graph (default), 2 = one persistent cooperative launch for the
+                                whole loop when the problem qualifies (register-FFT path, FP32,
+                                square padding), else the graph; results agree to FP32 rounding */
   int32_t history_every;     /* > 0: every n iterations write a row of 8 doubles to history: the
                                 6 loss terms, RelErr of chi-hat and of its CCO image (NaN-free
                                 only with chi_true; the loop then runs without a CUDA graph)    */

@@ -425,6 +425,9 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
   TRY(dalloc(h, &h->cco_ab, M));
   TRY(dalloc(h, &h->alpha_alt, NA));
   TRY(dalloc(h, &h->used_warm, 1));
+  TRY(dalloc(h, &h->bar, 1));
+  TRY(dalloc(h, &h->perr, 1));
+  cudaMemsetAsync(h->perr, 0, sizeof(int), s);
   TRY(dalloc(h, &h->small2, NI * NR));
   {
     cudaError_t e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);

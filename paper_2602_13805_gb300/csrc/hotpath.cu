@@ -20,6 +20,7 @@
 #include <algorithm>
 
 #include "fft.cuh"
+#include "phases.cuh"
 #include "problem.cuh"
 #include "tc.cuh"
 
@@ -241,280 +242,28 @@ __global__ void __launch_bounds__(ROW_THREADS) k_rowifft_state(Dev d) {
 // ---------------------------------------------------------------------------
 // G_S x over all incidences: per-chunk partial products, then a deterministic reduction
 // ---------------------------------------------------------------------------
-#define GS_SUB 32
-#define GS_TP 2
-#define GS_TR 4
-
-__global__ void __launch_bounds__(256) k_gs_partial(Dev d, const float2* __restrict__ X, float2* __restrict__ part) {
+__global__ void __launch_bounds__(256) k_gs_partial(Dev d, const float2* X, float2* part) {
   extern __shared__ float2 sm[];
-  const int ls = GS_SUB + 1;
-  float2* sX = sm;                     // [ni][ls]
-  float2* sG = sX + d.ni * ls;         // [nr][ls]
-  float2* sR = sG + d.nr * ls;         // reduction scratch [256][GS_TP*GS_TR]
-  const int n0 = blockIdx.x * d.gs_chunk;
-  const int n1 = min(n0 + d.gs_chunk, d.M);
-  const int tpn = (d.ni + GS_TP - 1) / GS_TP, trn = (d.nr + GS_TR - 1) / GS_TR;
-  const int ntiles = tpn * trn;
-  int kgroups = 1;
-  while (kgroups * 2 * ntiles <= (int)blockDim.x && kgroups < GS_SUB) kgroups *= 2;
-  const int npass = (ntiles * kgroups + blockDim.x - 1) / blockDim.x;
-  for (int pass = 0; pass < npass; ++pass) {
-    const int slot = pass * blockDim.x + threadIdx.x;
-    const int tile = slot / kgroups, kg = slot - tile * kgroups;
-    const bool active = tile < ntiles;
-    const int tp = active ? tile / trn : 0, tr = active ? tile - (tile / trn) * trn : 0;
-    float2 acc[GS_TP][GS_TR];
-#pragma unroll
-    for (int a = 0; a < GS_TP; ++a)
-#pragma unroll
-      for (int b = 0; b < GS_TR; ++b) acc[a][b] = make_float2(0.f, 0.f);
-    for (int t0 = n0; t0 < n1; t0 += GS_SUB) {
-      const int nt = min(GS_SUB, n1 - t0);
-      __syncthreads();
-      for (int i = threadIdx.x; i < d.ni * GS_SUB; i += blockDim.x) {
-        const int p = i / GS_SUB, t = i - p * GS_SUB;
-        sX[p * ls + t] = t < nt ? X[(size_t)p * d.M + t0 + t] : make_float2(0.f, 0.f);
-      }
-      for (int i = threadIdx.x; i < d.nr * GS_SUB; i += blockDim.x) {
-        const int r = i / GS_SUB, t = i - r * GS_SUB;
-        sG[r * ls + t] = t < nt ? d.gs[(size_t)r * d.M + t0 + t] : make_float2(0.f, 0.f);
-      }
-      __syncthreads();
-      if (active) {
-        for (int t = kg; t < GS_SUB; t += kgroups) {
-          float2 xv[GS_TP], gv[GS_TR];
-#pragma unroll
-          for (int a = 0; a < GS_TP; ++a) {
-            const int p = tp * GS_TP + a;
-            xv[a] = p < d.ni ? sX[p * ls + t] : make_float2(0.f, 0.f);
-          }
-#pragma unroll
-          for (int b = 0; b < GS_TR; ++b) {
-            const int r = tr * GS_TR + b;
-            gv[b] = r < d.nr ? sG[r * ls + t] : make_float2(0.f, 0.f);
-          }
-#pragma unroll
-          for (int a = 0; a < GS_TP; ++a)
-#pragma unroll
-            for (int b = 0; b < GS_TR; ++b) acc[a][b] = acc[a][b] + cmul(gv[b], xv[a]);
-        }
-      }
-    }
-    // reduce over k-groups (consecutive threads of one tile) via shared memory
-    __syncthreads();
-#pragma unroll
-    for (int a = 0; a < GS_TP; ++a)
-#pragma unroll
-      for (int b = 0; b < GS_TR; ++b) sR[threadIdx.x * GS_TP * GS_TR + a * GS_TR + b] = acc[a][b];
-    __syncthreads();
-    if (active && kg == 0) {
-      for (int g = 1; g < kgroups; ++g)
-#pragma unroll
-        for (int a = 0; a < GS_TP; ++a)
-#pragma unroll
-          for (int b = 0; b < GS_TR; ++b) acc[a][b] = acc[a][b] + sR[(threadIdx.x + g) * GS_TP * GS_TR + a * GS_TR + b];
-#pragma unroll
-      for (int a = 0; a < GS_TP; ++a)
-#pragma unroll
-        for (int b = 0; b < GS_TR; ++b) {
-          const int p = tp * GS_TP + a, r = tr * GS_TR + b;
-          if (p < d.ni && r < d.nr) part[((size_t)blockIdx.x * d.ni + p) * d.nr + r] = acc[a][b];
-        }
-    }
-  }
+  ph_gs_partial(d, blockIdx.x, sm, X, part);
 }
 
 // out[p][r] = sum over chunks (FP64) [- sub]; ||out||^2 partial per block -> lp (may be NULL)
-__global__ void k_gs_reduce(Dev d, const float2* __restrict__ part, int nchunk, const float2* __restrict__ sub,
-                            float2* __restrict__ out, FF* __restrict__ lp) {
-  __shared__ FF red[32];
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nout = d.ni * d.nr;
-  FF a2 = FF{0.f, 0.f};
-  if (o < nout) {
-    FF sx = FF{0.f, 0.f}, sy = FF{0.f, 0.f};
-    for (int c = 0; c < nchunk; ++c) {
-      const float2 v = part[(size_t)c * nout + o];
-      sx = ff_add(sx, v.x);
-      sy = ff_add(sy, v.y);
-    }
-    if (sub) {
-      sx = ff_add(sx, -sub[o].x);
-      sy = ff_add(sy, -sub[o].y);
-    }
-    const float2 v = make_float2(sx.hi + sx.lo, sy.hi + sy.lo);
-    out[o] = v;
-    a2 = ff_make(cabs2(v));
-  }
-  if (lp) {
-    const FF t = ff_block_sum(a2, red);
-    if (threadIdx.x == 0) lp[blockIdx.x] = t;
-  }
+__global__ void k_gs_reduce(Dev d, const float2* part, int nchunk, const float2* sub, float2* out, FF* lp) {
+  ph_gs_reduce(d, blockIdx.x, part, nchunk, sub, out, lp);
 }
 
 // ---------------------------------------------------------------------------
 // G_S^H: out[p][n] = scale * sum_r conj(G[r][n]) in[p][r]
 // ---------------------------------------------------------------------------
-#define GSH_RT 32
-#define GSH_TP 4
-#define GSH_TN 4
-
-__global__ void __launch_bounds__(256) k_gsh(Dev d, const float2* __restrict__ in, float2* __restrict__ out,
-                                             float scale, int data_scale) {
-  if (data_scale) scale = d.invn[1];     // 2 / ||E_sca||^2 of Eq. (16)'s gradient
+__global__ void __launch_bounds__(256) k_gsh(Dev d, const float2* in, float2* out, float scale, int data_scale) {
   extern __shared__ float2 sm[];
-  float2* sD = sm;                              // [ni][GSH_RT]
-  float2* sG = sD + d.ni * GSH_RT;              // [GSH_RT][GSH_CHUNK + 1]
-  float2* sR = sG + GSH_RT * (GSH_CHUNK + 1);   // [256][GSH_TP*GSH_TN]
-  const int n0 = blockIdx.x * GSH_CHUNK;
-  const int nn = min(GSH_CHUNK, d.M - n0);
-  const int tpn = (d.ni + GSH_TP - 1) / GSH_TP, tnn = GSH_CHUNK / GSH_TN;
-  const int ntiles = tpn * tnn;
-  int kgroups = 1;
-  while (kgroups * 2 * ntiles <= (int)blockDim.x && kgroups < GSH_RT) kgroups *= 2;
-  const int npass = (ntiles * kgroups + blockDim.x - 1) / blockDim.x;
-  for (int pass = 0; pass < npass; ++pass) {
-    const int slot = pass * blockDim.x + threadIdx.x;
-    const int tile = slot / kgroups, kg = slot - tile * kgroups;
-    const bool active = tile < ntiles;
-    const int tp = active ? tile / tnn : 0, tn = active ? tile - (tile / tnn) * tnn : 0;
-    float2 acc[GSH_TP][GSH_TN];
-#pragma unroll
-    for (int a = 0; a < GSH_TP; ++a)
-#pragma unroll
-      for (int b = 0; b < GSH_TN; ++b) acc[a][b] = make_float2(0.f, 0.f);
-    for (int r0 = 0; r0 < d.nr; r0 += GSH_RT) {
-      const int nrt = min(GSH_RT, d.nr - r0);
-      __syncthreads();
-      for (int i = threadIdx.x; i < d.ni * GSH_RT; i += blockDim.x) {
-        const int p = i / GSH_RT, r = i - p * GSH_RT;
-        sD[i] = r < nrt ? in[(size_t)p * d.nr + r0 + r] : make_float2(0.f, 0.f);
-      }
-      for (int i = threadIdx.x; i < GSH_RT * GSH_CHUNK; i += blockDim.x) {
-        const int r = i / GSH_CHUNK, t = i - r * GSH_CHUNK;
-        sG[r * (GSH_CHUNK + 1) + t] = (r < nrt && t < nn) ? d.gs[(size_t)(r0 + r) * d.M + n0 + t] : make_float2(0.f, 0.f);
-      }
-      __syncthreads();
-      if (active) {
-        for (int r = kg; r < GSH_RT; r += kgroups) {
-          float2 dv[GSH_TP], gv[GSH_TN];
-#pragma unroll
-          for (int a = 0; a < GSH_TP; ++a) {
-            const int p = tp * GSH_TP + a;
-            dv[a] = p < d.ni ? sD[p * GSH_RT + r] : make_float2(0.f, 0.f);
-          }
-#pragma unroll
-          for (int b = 0; b < GSH_TN; ++b) gv[b] = sG[r * (GSH_CHUNK + 1) + tn * GSH_TN + b];
-#pragma unroll
-          for (int a = 0; a < GSH_TP; ++a)
-#pragma unroll
-            for (int b = 0; b < GSH_TN; ++b) acc[a][b] = acc[a][b] + cmulc(dv[a], gv[b]);
-        }
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int a = 0; a < GSH_TP; ++a)
-#pragma unroll
-      for (int b = 0; b < GSH_TN; ++b) sR[threadIdx.x * GSH_TP * GSH_TN + a * GSH_TN + b] = acc[a][b];
-    __syncthreads();
-    if (active && kg == 0) {
-      for (int g = 1; g < kgroups; ++g)
-#pragma unroll
-        for (int a = 0; a < GSH_TP; ++a)
-#pragma unroll
-          for (int b = 0; b < GSH_TN; ++b)
-            acc[a][b] = acc[a][b] + sR[(threadIdx.x + g) * GSH_TP * GSH_TN + a * GSH_TN + b];
-#pragma unroll
-      for (int a = 0; a < GSH_TP; ++a)
-#pragma unroll
-        for (int b = 0; b < GSH_TN; ++b) {
-          const int p = tp * GSH_TP + a, t = tn * GSH_TN + b;
-          if (p < d.ni && t < nn) out[(size_t)p * d.M + n0 + t] = scale * acc[a][b];
-        }
-    }
-  }
+  ph_gsh(d, blockIdx.x, sm, in, out, scale, data_scale);
 }
 
 // ---------------------------------------------------------------------------
 // regularisers (Eq. 17-19) and their cotangent pulled back to w = c_R / D
 // ---------------------------------------------------------------------------
-struct TVB {  // per-pixel pieces of the TV and bridge terms at one pixel
-  float2 dx, dy;
-  float t;          // TV magnitude
-  float gx, gy;     // |chi| forward differences
-  float sg, e;      // sigmoid and exp factors
-};
-
-__device__ __forceinline__ float mag_at(const float2* chi, int nx, int y, int x, float eps) {
-  const float2 c = chi[y * nx + x];
-  return sqrtf(cabs2(c) + eps);
-}
-
-__device__ __forceinline__ TVB tvb_at(const Dev& d, int y, int x) {
-  TVB o;
-  const float2 c = d.chi[y * d.nx + x];
-  const bool hx = x + 1 < d.nx, hy = y + 1 < d.ny;
-  o.dx = hx ? d.chi[y * d.nx + x + 1] - c : make_float2(0.f, 0.f);
-  o.dy = hy ? d.chi[(y + 1) * d.nx + x] - c : make_float2(0.f, 0.f);
-  o.t = sqrtf(cabs2(o.dx) + cabs2(o.dy) + d.eps_tv);
-  const float m = sqrtf(cabs2(c) + d.eps_abs);
-  o.gx = hx ? mag_at(d.chi, d.nx, y, x + 1, d.eps_abs) - m : 0.f;
-  o.gy = hy ? mag_at(d.chi, d.nx, y + 1, x, d.eps_abs) - m : 0.f;
-  o.sg = 1.f / (1.f + expf(-(m - d.tau_b) / d.tau_b));
-  o.e = expf(-(o.gx * o.gx + o.gy * o.gy));
-  return o;
-}
-
-__global__ void __launch_bounds__(256) k_reg(Dev d) {
-  __shared__ FF red[32];
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  float lb = 0.f, ltv = 0.f, lbr = 0.f;
-  if (n < d.M) {
-    const int y = n / d.nx, x = n - y * d.nx;
-    const float2 c = d.chi[n];
-    const float neg = fmaxf(-c.x, 0.f);
-    lb = neg * neg;
-    const TVB o = tvb_at(d, y, x);
-    ltv = o.t;
-    lbr = o.sg * o.e;
-    // TV cotangent: -(dx + dy)/t at the own term, + dx/t of the left term, + dy/t of the upper term
-    float2 ctv = (-1.f / o.t) * (o.dx + o.dy);
-    // bridge cotangent on |chi|: own sigmoid term, own differences (-1), left / upper differences (+1)
-    float dm = o.sg * (1.f - o.sg) / d.tau_b * o.e + 2.f * (o.gx + o.gy) * o.sg * o.e;
-    if (x > 0) {
-      const TVB l = tvb_at(d, y, x - 1);
-      ctv = ctv + (1.f / l.t) * l.dx;
-      dm += -2.f * l.gx * l.sg * l.e;
-    }
-    if (y > 0) {
-      const TVB u = tvb_at(d, y - 1, x);
-      ctv = ctv + (1.f / u.t) * u.dy;
-      dm += -2.f * u.gy * u.sg * u.e;
-    }
-    const float m = sqrtf(cabs2(c) + d.eps_abs);
-    float2 cchi = d.lam_tv * ctv + (d.lam_bridge * dm / m) * c;
-    cchi.x += d.lam_bound * (-2.f * neg);
-    // chi = R / (beta (1 - R)):  d chi / d R = 1 / (beta (1 - R)^2), zero where clamped
-    float2 w = make_float2(0.f, 0.f);
-    if (!d.clamp[n]) {
-      const float2 R = d.R[n];
-      const float2 q = make_float2(1.f - R.x, -R.y);
-      const float2 dchi = cdivf(make_float2(1.f, 0.f), cmul(d.beta, cmul(q, q)));
-      const float2 cR = cmul(cconj(dchi), cchi);
-      w = (1.f / d.D[n]) * cR;
-    }
-    d.w[n] = w;
-  }
-  const FF tb = ff_block_sum(ff_make(lb), red);
-  const FF tt = ff_block_sum(ff_make(ltv), red);
-  const FF tr = ff_block_sum(ff_make(lbr), red);
-  if (threadIdx.x == 0) {
-    d.lpart[LP_BOUND * PDF_LP_STRIDE + blockIdx.x] = tb;
-    d.lpart[LP_TV * PDF_LP_STRIDE + blockIdx.x] = tt;
-    d.lpart[LP_BRIDGE * PDF_LP_STRIDE + blockIdx.x] = tr;
-  }
-}
+__global__ void __launch_bounds__(256) k_reg(Dev d) { ph_reg(d, blockIdx.x); }
 
 // ---------------------------------------------------------------------------
 // adjoint: u (through G_D^H) and v (pointwise), then padded row DFT of u
@@ -595,47 +344,13 @@ __global__ void __launch_bounds__(ROW_THREADS) k_adj_rowifft_ana(Dev d, const fl
 
 // analysis along y: out[p][jy][jx] = sum_y conj(wy[jy][y]) T2[p][y][jx]; one CTA per (jy, p),
 // eight warps over interleaved y, lanes over jx (kx <= 64)
-__global__ void __launch_bounds__(256) k_ana_y(Dev d, const float2* __restrict__ T2, float2* __restrict__ out) {
-  __shared__ float2 part[8][64];
-  const int jy = blockIdx.x, p = blockIdx.y, g = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const float2* T = T2 + (size_t)p * d.ny * d.kx;
-  float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-  for (int y = g; y < d.ny; y += 8) {
-    const float2 w = __ldg(&d.wy[jy * d.ny + y]);
-    if (lane < d.kx) a0 = a0 + cmulc(T[(size_t)y * d.kx + lane], w);
-    if (lane + 32 < d.kx) a1 = a1 + cmulc(T[(size_t)y * d.kx + lane + 32], w);
-  }
-  part[g][lane] = a0;
-  part[g][lane + 32] = a1;
-  __syncthreads();
-  if (threadIdx.x < d.kx) {
-    float2 s = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) s = s + part[k][threadIdx.x];
-    out[((size_t)p * d.ky + jy) * d.kx + threadIdx.x] = s;
-  }
+__global__ void __launch_bounds__(256) k_ana_y(Dev d, const float2* T2, float2* out) {
+  ph_ana_y(d, blockIdx.x, blockIdx.y, T2, out);
 }
 
 // terms[6] = L, State, Data, Bound, TV, Bridge from the partial sums
-__global__ void k_finalize(Dev d, double* __restrict__ terms, int n_state, int n_data, int n_reg, int* step_inc) {
-  __shared__ FF red[32];
-  const int cnt[5] = {n_state, n_data, n_reg, n_reg, n_reg};
-  double tot[5];
-  for (int s = 0; s < 5; ++s) {
-    FF a = FF{0.f, 0.f};
-    for (int i = threadIdx.x; i < cnt[s]; i += blockDim.x) a = ff_add(a, d.lpart[s * PDF_LP_STRIDE + i]);
-    tot[s] = ff_to_d(ff_block_sum(a, red));
-  }
-  if (threadIdx.x == 0) {
-    const double st = tot[0] / d.norms[0], da = tot[1] / d.norms[1];
-    terms[1] = st;
-    terms[2] = da;
-    terms[3] = tot[2];
-    terms[4] = tot[3];
-    terms[5] = tot[4];
-    terms[0] = st + da + (double)d.lam_bound * tot[2] + (double)d.lam_tv * tot[3] + (double)d.lam_bridge * tot[4];
-    if (step_inc) *step_inc += 1;
-  }
+__global__ void k_finalize(Dev d, double* terms, int n_state, int n_data, int n_reg, int* step_inc) {
+  ph_finalize(d, terms, n_state, n_data, n_reg, step_inc);
 }
 
 // ---------------------------------------------------------------------------
@@ -649,9 +364,14 @@ static size_t sm_col(const Dev& d) { return 2 * COL_CW * (size_t)(d.Py + 1) * si
 static size_t sm_gs(const Dev& d) {
   return ((size_t)(d.ni + d.nr) * (GS_SUB + 1) + 256 * GS_TP * GS_TR) * sizeof(float2);
 }
+size_t sm_gs_bytes(const Dev& d);
+size_t sm_gsh_bytes(const Dev& d);
 static size_t sm_gsh(const Dev& d) {
   return ((size_t)d.ni * GSH_RT + GSH_RT * (GSH_CHUNK + 1) + 256 * GSH_TP * GSH_TN) * sizeof(float2);
 }
+
+size_t sm_gs_bytes(const Dev& d) { return sm_gs(d); }
+size_t sm_gsh_bytes(const Dev& d) { return sm_gsh(d); }
 
 pdf_status hp_configure_kernels() {
   const int big = 200 * 1024;

@@ -88,6 +88,8 @@ struct pdf_problem {
   float4* cco_ab;        // [M] guided-filter coefficients
   float2* alpha_alt;     // [ni][ky][kx] warm-start candidate
   int* used_warm;        // device flag
+  unsigned* bar;         // grid-barrier counter of the persistent loop
+  int* perr;             // its timeout flag
   float2* small1;        // [ni][nr] scratch
   float2* small2;
   cudaStream_t cap_stream;   // private stream used only for graph capture
@@ -151,6 +153,10 @@ size_t fp_smem_synth(const Dev& d);
 size_t fp_smem_col(const Dev& d);
 size_t fp_smem_state(const Dev& d);
 size_t fp_smem_ana(const Dev& d);
+
+// persistent solve loop (persist.cu)
+pdf_status ps_run(pdf_problem* h, const pdf_solve_opts* o, int iters, unsigned* bar, int* err, cudaStream_t st,
+                  bool* done);
 
 // solve pieces (solve.cu)
 pdf_status sv_cco(pdf_problem* h, const float2* chi, float2* out, int radius, double eps, double eta_max,

@@ -18,27 +18,15 @@
 #include <vector>
 
 #include "fft.cuh"
+#include "phases.cuh"
 #include "problem.cuh"
 
 // ---------------------------------------------------------------------------
 // Adam on the real view of alpha (torch.optim.Adam arithmetic, FP32)
 // ---------------------------------------------------------------------------
-__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
-                       float* __restrict__ v, int n, const int* __restrict__ tdev, const float2* __restrict__ tab,
+__global__ void k_adam(float* p, const float* g, float* m, float* v, int n, const int* tdev, const float2* tab,
                        int cap, float b1, float b2, float eps) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int t = min(max(*tdev, 1), cap);
-  const float2 sc = tab[t - 1];        // lr / (1 - b1^t), sqrt(1 - b2^t), evaluated in FP64 on the host
-  const float gi = g[i];
-  float mi = m[i];
-  mi = mi + (1.f - b1) * (gi - mi);
-  float vi = v[i] * b2;
-  vi = vi + ((1.f - b2) * gi) * gi;
-  m[i] = mi;
-  v[i] = vi;
-  const float denom = sqrtf(vi) / sc.y + eps;
-  p[i] = p[i] + (-sc.x) * (mi / denom);
+  ph_adam(blockIdx.x * blockDim.x + threadIdx.x, p, g, m, v, n, *tdev, tab, cap, b1, b2, eps);
 }
 
 // Bias-correction table of torch.optim.Adam for steps 1..iters (rebuilt when lr, betas or the
@@ -447,7 +435,12 @@ pdf_status sv_solve(pdf_problem* h, const pdf_solve_opts* o, float2* chi_out, fl
       }
     }
   } else {
-    if (o->use_graph && o->iters >= GRAPH_UNROLL) {
+    bool persisted = false;
+    if (o->use_graph == 2) {
+      if ((s = ps_run(h, o, o->iters, h->bar, h->perr, st, &persisted)) != PDF_OK) return s;
+      if (persisted) it = o->iters;
+    }
+    if (!persisted && o->use_graph && o->iters >= GRAPH_UNROLL) {
       if ((s = build_graph(h, o)) != PDF_OK) return s;
       for (; it + h->graph_iters <= o->iters; it += h->graph_iters) {
         PDF_CUDA(cudaGraphLaunch(h->graph_exec, st));
@@ -489,9 +482,14 @@ pdf_status sv_solve(pdf_problem* h, const pdf_solve_opts* o, float2* chi_out, fl
     PDF_CUDA(cudaStreamSynchronize(st));
     rep->relerr = o->chi_true ? sqrt(re[0] / re[1]) : NAN;
     rep->relerr_cco = o->chi_true ? sqrt(re[2] / re[3]) : NAN;
-    int used = 0;
+    int used = 0, perr = 0;
     PDF_CUDA(cudaMemcpy(&used, h->used_warm, sizeof(int), cudaMemcpyDeviceToHost));
+    PDF_CUDA(cudaMemcpy(&perr, h->perr, sizeof(int), cudaMemcpyDeviceToHost));
     rep->used_warm_start = used;
+    if (perr) {
+      cudaMemset(h->perr, 0, sizeof(int));
+      return set_err(PDF_ETIMEOUT, "a grid barrier of the persistent solve loop timed out");
+    }
     for (int k = 0; k < 6; ++k)
       if (!std::isfinite(rep->terms[k])) rep->nonfinite = 1;
     if (rep->nonfinite) return set_err(PDF_ENONFINITE, "a loss term is not finite");

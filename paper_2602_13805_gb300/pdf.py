@@ -328,7 +328,7 @@ class Problem:
         pdf_apply_op(self.h, op, x, out, stream)
         return out
 
-    def solve(self, iters=300, lr=1e-2, init=0, alpha0=None, chi_true=None, apply_cco=True, use_graph=True,
+    def solve(self, iters=300, lr=1e-2, init=0, alpha0=None, chi_true=None, apply_cco=True, use_graph=1,
               history_every=0, stream=None, **kw):
         import torch
         hist = None

@@ -424,8 +424,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
     ap.add_argument("--warm-start", action="store_true")
-    ap.add_argument("--loop", type=int, default=1, choices=[0, 1, 2],
-                    help="0 eager launches, 1 CUDA graph, 2 persistent cooperative kernel (when eligible)")
+    ap.add_argument("--loop", type=int, default=1, choices=[0, 1, 2, 3],
+                    help="0 eager launches, 1 CUDA graph, 2 persistent cooperative kernel, 3 cluster kernel (when eligible)")
     ap.add_argument("--train-scenes", type=int, default=20000)
     ap.add_argument("--test-scenes", type=int, default=10)
     ap.add_argument("--train-steps", type=int, default=3000)

@@ -318,6 +318,8 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
   h->cfg.rx_xy = nullptr;
   h->alpha = h->grad = nullptr;
   h->tc = nullptr;
+  h->cl_nd = nullptr;
+  h->cl_lp = nullptr;
   h->esca_host_pinned = nullptr;
   h->graph_exec = nullptr;
   h->cap_stream = nullptr;

@@ -88,7 +88,9 @@ struct pdf_problem {
   float4* cco_ab;        // [M] guided-filter coefficients
   float2* alpha_alt;     // [ni][ky][kx] warm-start candidate
   int* used_warm;        // device flag
-  unsigned* bar;         // grid-barrier counter of the persistent loop
+  unsigned* bar;         // grid-barrier counter of the persistent and cluster loops
+  float* cl_nd;          // cluster loop: per-incidence pixel sums (lazily allocated)
+  FF* cl_lp;             // cluster loop: loss partials
   int* perr;             // its timeout flag
   float2* small1;        // [ni][nr] scratch
   float2* small2;
@@ -157,6 +159,9 @@ size_t fp_smem_ana(const Dev& d);
 // persistent solve loop (persist.cu)
 pdf_status ps_run(pdf_problem* h, const pdf_solve_opts* o, int iters, unsigned* bar, int* err, cudaStream_t st,
                   bool* done);
+
+// cluster solve loop (cluster.cu)
+pdf_status cl_run(pdf_problem* h, const pdf_solve_opts* o, int iters, cudaStream_t st, bool* done);
 
 // solve pieces (solve.cu)
 pdf_status sv_cco(pdf_problem* h, const float2* chi, float2* out, int radius, double eps, double eta_max,

@@ -436,7 +436,11 @@ pdf_status sv_solve(pdf_problem* h, const pdf_solve_opts* o, float2* chi_out, fl
     }
   } else {
     bool persisted = false;
-    if (o->use_graph == 2) {
+    if (o->use_graph == 3) {
+      if ((s = cl_run(h, o, o->iters, st, &persisted)) != PDF_OK) return s;
+      if (persisted) it = o->iters;
+    }
+    if (!persisted && o->use_graph >= 2) {
       if ((s = ps_run(h, o, o->iters, h->bar, h->perr, st, &persisted)) != PDF_OK) return s;
       if (persisted) it = o->iters;
     }

@@ -121,10 +121,13 @@ typedef struct pdf_solve_opts {
   int32_t cco_radius;        /* guided-filter box radius (default 2)                           */
   double cco_eps;            /* guided-filter regulariser (default 1e-2)                       */
   double cco_eta_max, cco_tau, cco_delta;  /* Eq. (11): 0.1, 3, 0.5                            */
-  int32_t use_graph;         /* 0 = launch every kernel, 1 = run the iteration loop as a CUDA
-                                graph (default), 2 = one persistent cooperative launch for the
-                                whole loop when the problem qualifies (register-FFT path, FP32,
-                                square padding), else the graph; results agree to FP32 rounding */
+  int32_t use_graph;         /* how the iteration loop runs (results agree to FP32 rounding):
+                                0 = one launch per kernel; 1 = a CUDA graph of the kernels;
+                                2 = one persistent cooperative launch for the whole loop;
+                                3 = one cooperative launch of thread-block clusters, one cluster
+                                per incidence, for the whole loop (default).  2 and 3 need the
+                                register-FFT path in FP32 with square padding (3: padding <= 128
+                                and Ni * cluster size <= SM count); otherwise the graph runs     */
   int32_t history_every;     /* > 0: every n iterations write a row of 8 doubles to history: the
                                 6 loss terms, RelErr of chi-hat and of its CCO image (NaN-free
                                 only with chi_true; the loop then runs without a CUDA graph)    */
@@ -138,7 +141,7 @@ typedef struct pdf_solve_report {
   double relerr;             /* ||chi - chi_true|| / ||chi_true|| before CCO (NaN without truth) */
   double relerr_cco;         /* same after CCO                                                 */
   int32_t used_warm_start;   /* init == 3: 1 if alpha0 was kept, 0 if BP + CSI was used        */
-  int32_t reserved;
+  int32_t loop_mode;         /* the loop form that ran (see use_graph): 0, 1, 2 or 3           */
 } pdf_solve_report;
 
 void pdf_solve_opts_default(pdf_solve_opts* o);

@@ -319,7 +319,6 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
   h->alpha = h->grad = nullptr;
   h->tc = nullptr;
   h->cl_nd = nullptr;
-  h->cl_lp = nullptr;
   h->esca_host_pinned = nullptr;
   h->graph_exec = nullptr;
   h->cap_stream = nullptr;
@@ -603,7 +602,7 @@ extern "C" void pdf_solve_opts_default(pdf_solve_opts* o) {
   o->cco_eta_max = 0.1;
   o->cco_tau = 3.0;
   o->cco_delta = 0.5;
-  o->use_graph = 1;
+  o->use_graph = 3;
 }
 
 extern "C" pdf_status pdf_solve(pdf_problem* h, const pdf_solve_opts* o, void* chi_out, void* chi_raw_out,

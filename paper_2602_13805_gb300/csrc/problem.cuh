@@ -89,8 +89,7 @@ struct pdf_problem {
   float2* alpha_alt;     // [ni][ky][kx] warm-start candidate
   int* used_warm;        // device flag
   unsigned* bar;         // grid-barrier counter of the persistent and cluster loops
-  float* cl_nd;          // cluster loop: per-incidence pixel sums (lazily allocated)
-  FF* cl_lp;             // cluster loop: loss partials
+  float4* cl_nd;         // cluster loop: per-incidence pixel sums (lazily allocated)
   int* perr;             // its timeout flag
   float2* small1;        // [ni][nr] scratch
   float2* small2;

@@ -413,6 +413,7 @@ pdf_status sv_solve(pdf_problem* h, const pdf_solve_opts* o, float2* chi_out, fl
   PDF_CUDA(cudaMemsetAsync(h->adam_v, 0, sizeof(float) * 2 * NA, st));
   PDF_CUDA(cudaMemsetAsync(h->adam_t, 0, sizeof(int), st));
   int it = 0;
+  int loop_mode = 0;                  // which loop form ran (reported)
   if (o->history_every > 0) {
     for (; it < o->iters; ++it) {
       if ((s = iteration(h, o, st)) != PDF_OK) return s;
@@ -438,14 +439,21 @@ pdf_status sv_solve(pdf_problem* h, const pdf_solve_opts* o, float2* chi_out, fl
     bool persisted = false;
     if (o->use_graph == 3) {
       if ((s = cl_run(h, o, o->iters, st, &persisted)) != PDF_OK) return s;
-      if (persisted) it = o->iters;
+      if (persisted) {
+        it = o->iters;
+        loop_mode = 3;
+      }
     }
-    if (!persisted && o->use_graph >= 2) {
+    if (!persisted && o->use_graph == 2) {
       if ((s = ps_run(h, o, o->iters, h->bar, h->perr, st, &persisted)) != PDF_OK) return s;
-      if (persisted) it = o->iters;
+      if (persisted) {
+        it = o->iters;
+        loop_mode = 2;
+      }
     }
     if (!persisted && o->use_graph && o->iters >= GRAPH_UNROLL) {
       if ((s = build_graph(h, o)) != PDF_OK) return s;
+      loop_mode = 1;
       for (; it + h->graph_iters <= o->iters; it += h->graph_iters) {
         PDF_CUDA(cudaGraphLaunch(h->graph_exec, st));
         pdf_count_launch(h->graph_kernels);
@@ -480,6 +488,7 @@ pdf_status sv_solve(pdf_problem* h, const pdf_solve_opts* o, float2* chi_out, fl
   if (rep) {
     memset(rep, 0, sizeof(*rep));
     rep->iters_run = o->iters;
+    rep->loop_mode = loop_mode;
     PDF_CUDA(cudaMemcpyAsync(rep->terms, h->terms, 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
     double re[4] = {NAN, NAN, NAN, NAN};
     if (o->chi_true) PDF_CUDA(cudaMemcpyAsync(re, h->scratch_d + 40, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -492,7 +501,8 @@ pdf_status sv_solve(pdf_problem* h, const pdf_solve_opts* o, float2* chi_out, fl
     rep->used_warm_start = used;
     if (perr) {
       cudaMemset(h->perr, 0, sizeof(int));
-      return set_err(PDF_ETIMEOUT, "a grid barrier of the persistent solve loop timed out");
+      return set_err(PDF_ETIMEOUT, perr == 2 ? "the cluster solve loop was launched without its cluster shape"
+                                             : "a grid barrier of the persistent solve loop timed out");
     }
     for (int k = 0; k < 6; ++k)
       if (!std::isfinite(rep->terms[k])) rep->nonfinite = 1;

@@ -69,7 +69,7 @@ class pdf_solve_report(ctypes.Structure):
         ("iters_run", ctypes.c_int32), ("nonfinite", ctypes.c_int32),
         ("terms", ctypes.c_double * 6),
         ("relerr", ctypes.c_double), ("relerr_cco", ctypes.c_double),
-        ("used_warm_start", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("used_warm_start", ctypes.c_int32), ("loop_mode", ctypes.c_int32),
     ]
 
 
@@ -328,7 +328,7 @@ class Problem:
         pdf_apply_op(self.h, op, x, out, stream)
         return out
 
-    def solve(self, iters=300, lr=1e-2, init=0, alpha0=None, chi_true=None, apply_cco=True, use_graph=1,
+    def solve(self, iters=300, lr=1e-2, init=0, alpha0=None, chi_true=None, apply_cco=True, use_graph=3,
               history_every=0, stream=None, **kw):
         import torch
         hist = None

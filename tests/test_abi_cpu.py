@@ -45,7 +45,7 @@ def test_struct_layouts_match_header(lib):
     assert abs(c.k0 - 2 * np.pi) < 1e-15
     o = pdf.pdf_solve_opts()
     lib.pdf_solve_opts_default(ctypes.byref(o))
-    assert o.iters == 300 and o.lr == 1e-2 and o.adam_b2 == 0.999 and o.cco_radius == 2 and o.use_graph == 1
+    assert o.iters == 300 and o.lr == 1e-2 and o.adam_b2 == 0.999 and o.cco_radius == 2 and o.use_graph == 3
 
 
 @pytest.mark.parametrize("field,value,status", [

@@ -62,6 +62,12 @@ typedef struct pdf_config {
   int32_t precision;         /* 0 = FP32 contractions, 1 = split-BF16 tensor-core contractions */
   int32_t fft_path;          /* 0 = register-resident warp FFTs (padded lengths 64..512),
                                 1 = generic shared-memory FFT (any padded length 2^a 3^b)      */
+  int32_t fold_gs;           /* 1 (default) = data term through the folded receiver operator
+                                G_S Phi [nr][ky*kx], assembled once at setup with compensated
+                                sums: r_d = (G_S Phi) alpha - E_sca and its adjoint act on the
+                                Fourier coefficients (Eq. 9 and 16 composed); 0 = G_S applied to
+                                the synthesised currents J every iteration (tensor cores at
+                                precision 1).  Same result up to rounding.                      */
 } pdf_config;
 
 /* Fills the paper's defaults (beta = 6, lambdas 1e-3/1e-5/1e-5, tau_B = 0.5, k0 = 2 pi) and
@@ -168,12 +174,20 @@ pdf_status pdf_forward(pdf_problem* h, const void* chi, void* esca_out, void* j_
 int32_t pdf_profile_loss_grad(pdf_problem* h, const void* alpha, int32_t reps, float* ms, int32_t n,
                               void* stream);
 
-/* Name of kernel k of pdf_loss_grad in launch order ("" when out of range), FP32 path. */
+/* Name of kernel k of pdf_loss_grad in launch order ("" when out of range), FP32 path with the
+ * default folded data term (fold_gs = 1). */
 const char* pdf_kernel_name(int32_t k);
 
 /* Name of profiled stage k of pdf_loss_grad for this handle's precision (with precision = 1
  * some stages group a tensor-core GEMM with its operand packing). */
 const char* pdf_stage_name(pdf_problem* h, int32_t k);
+
+/* Phase timestamps of the cluster loop (use_graph = 3), for libraries built with the compile
+ * definition PDF_PHASE_STAMPS only: out[4][16] receives the global-timer readings (ns) that
+ * thread 0 of the first CTA took after each barrier of iterations 5..8 of the last cluster
+ * solve (15 marks per iteration, the 16th unused).  Synchronises the device.  PDF_EUNSUPPORTED
+ * in ordinary builds, whose kernels carry no marks. */
+pdf_status pdf_phase_stamps(uint64_t* out);
 
 /* G_S x without any device allocation, for callers that cannot call cudaMalloc: code whose
  * device memory is already owned by another allocator (a host framework's caching allocator

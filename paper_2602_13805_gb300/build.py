@@ -2,7 +2,9 @@
 
 Compiles each translation unit under csrc/ in parallel with nvcc and links them
 into paper_2602_13805_gb300/libpdf.so.  Run as `python -m paper_2602_13805_gb300.build`
-or through __graft_entry__.build().
+or through __graft_entry__.build().  `--stamps` builds the instrumented variant
+libpdf_stamps.so (compile definition PDF_PHASE_STAMPS: global-timer marks at the barriers of
+the cluster loop, read back with pdf_phase_stamps) in a build folder of its own.
 """
 from __future__ import annotations
 
@@ -31,9 +33,9 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-    cmd = [nvcc(), *ARCH, *FLAGS, "-c", src, "-o", obj]
+def _compile(src: str, verbose: bool, build_dir: str = BUILD, defs=()) -> str:
+    obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
+    cmd = [nvcc(), *ARCH, *FLAGS, *defs, "-c", src, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -44,25 +46,28 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, force: bool = False, stamps: bool = False) -> str:
+    lib = os.path.join(HERE, "libpdf_stamps.so") if stamps else LIB
+    build_dir = BUILD + "_stamps" if stamps else BUILD
+    defs = ("-DPDF_PHASE_STAMPS",) if stamps else ()
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sources()
     deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     deps.append(os.path.join(os.path.dirname(HERE), "include", "pdf.h"))
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
+    if not force and os.path.exists(lib):
+        t = os.path.getmtime(lib)
         if all(os.path.getmtime(p) < t for p in deps) and os.path.getmtime(__file__) < t:
-            return LIB
+            return lib
     with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
-    tmp = LIB + ".tmp"
+        objs = list(ex.map(lambda s: _compile(s, verbose, build_dir, defs), srcs))
+    tmp = lib + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv))
+    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv, stamps="--stamps" in sys.argv))

@@ -192,6 +192,39 @@ __global__ void k_synth_table(float2* W, int K, int n) {
   W[(size_t)j * n + x] = make_float2((float)(c * sc), (float)(s * sc));
 }
 
+// Folded receiver operator G_S Phi (Eq. 16 composed with the synthesis of Eq. 9), in two
+// contractions with float-float accumulation: T[r][jy][x] = sum_y Wy[jy][y] G_S[r][y][x], then
+// gsf[r][jy][jx] = sum_x T[r][jy][x] Wx[jx][x].
+__global__ void k_fold_y(const float2* __restrict__ gs, const float2* __restrict__ wy, float2* __restrict__ T,
+                         int nx, int ny, int ky) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, jy = blockIdx.y, r = blockIdx.z;
+  if (x >= nx) return;
+  FF re = FF{0.f, 0.f}, im = FF{0.f, 0.f};
+  const float2* g = gs + (size_t)r * ny * nx + x;
+  for (int y = 0; y < ny; ++y) {
+    const float2 w = wy[(size_t)jy * ny + y], v = g[(size_t)y * nx];
+    re = ff_add(ff_add(re, w.x * v.x), -(w.y * v.y));
+    im = ff_add(ff_add(im, w.x * v.y), w.y * v.x);
+  }
+  T[((size_t)r * ky + jy) * nx + x] = make_float2(re.hi + re.lo, im.hi + im.lo);
+}
+
+__global__ void k_fold_x(const float2* __restrict__ T, const float2* __restrict__ wx, float2* __restrict__ gsf,
+                         int nx, int ky, int kx) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+  if (j >= ky * kx) return;
+  const int jy = j / kx, jx = j - jy * kx;
+  const float2* t = T + ((size_t)r * ky + jy) * nx;
+  const float2* w = wx + (size_t)jx * nx;
+  FF re = FF{0.f, 0.f}, im = FF{0.f, 0.f};
+  for (int x = 0; x < nx; ++x) {
+    const float2 v = t[x], u = w[x];
+    re = ff_add(ff_add(re, v.x * u.x), -(v.y * u.y));
+    im = ff_add(ff_add(im, v.x * u.y), v.y * u.x);
+  }
+  gsf[(size_t)r * ky * kx + j] = make_float2(re.hi + re.lo, im.hi + im.lo);
+}
+
 // Deterministic single-block sum of n doubles into out[0].
 __global__ void k_sum(const double* in, int n, double* out) {
   __shared__ double red[32];
@@ -230,6 +263,7 @@ extern "C" void pdf_config_default(pdf_config* c) {
   c->eps_tv = 1e-8;
   c->eps_abs = 1e-12;
   c->q_min = 1e-6;
+  c->fold_gs = 1;
 }
 
 static void free_all(pdf_problem* h) {
@@ -287,6 +321,7 @@ static pdf_status validate(const pdf_config* c) {
   if (c->inc_kind != 0 && c->inc_kind != 1) return set_err(PDF_EINVAL, "inc_kind must be 0 or 1");
   if (c->precision != 0 && c->precision != 1) return set_err(PDF_EINVAL, "precision must be 0 or 1");
   if (c->fft_path != 0 && c->fft_path != 1) return set_err(PDF_EINVAL, "fft_path must be 0 or 1");
+  if (c->fold_gs != 0 && c->fold_gs != 1) return set_err(PDF_EINVAL, "fold_gs must be 0 or 1");
   if (c->tau_b <= 0 || c->eps_tv < 0 || c->eps_abs < 0 || c->q_min < 0)
     return set_err(PDF_EINVAL, "tau_b > 0 and non-negative eps/q_min required");
   int M = c->nx * c->ny;
@@ -366,7 +401,7 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
   // SIMT G_S product: about two CTAs per SM, 32..256 pixels each (multiple of 32)
   d.gs_chunk = std::min(256, std::max(32, ((d.M + 303) / 304 + 31) / 32 * 32));
   d.n_gs_chunks = (d.M + d.gs_chunk - 1) / d.gs_chunk;
-  d.n_reg_blocks = (d.M + 255) / 256;
+  d.n_reg_blocks = (d.M + 127) / 128;
   if ((st = hp_check_limits(d)) != PDF_OK) {
     free_all(h);
     return st;
@@ -485,6 +520,17 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
   k_synth_table<<<dim3((d.nx + 127) / 128, d.kx), 128, 0, s>>>(wx, d.kx, d.nx);
   k_synth_table<<<dim3((d.ny + 127) / 128, d.ky), 128, 0, s>>>(wy, d.ky, d.ny);
   pdf_count_launch(10);
+  d.fold = cfg->fold_gs;
+  d.gsf = nullptr;
+  if (d.fold) {
+    float2 *gsf, *tfold;
+    TRY(dalloc(h, &gsf, (size_t)NR * d.ky * d.kx));
+    TRY(dalloc(h, &tfold, (size_t)NR * d.ky * d.nx));
+    k_fold_y<<<dim3((d.nx + 63) / 64, d.ky, d.nr), 64, 0, s>>>(gs, wy, tfold, d.nx, d.ny, d.ky);
+    k_fold_x<<<dim3((d.ky * d.kx + 127) / 128, d.nr), 128, 0, s>>>(tfold, wx, gsf, d.nx, d.ky, d.kx);
+    pdf_count_launch(2);
+    d.gsf = gsf;
+  }
   {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -662,6 +708,8 @@ extern "C" int32_t pdf_profile_loss_grad(pdf_problem* h, const void* alpha, int3
   return K;
 }
 
-extern "C" const char* pdf_kernel_name(int32_t k) { return hp_kernel_name(k, 0); }
+extern "C" const char* pdf_kernel_name(int32_t k) { return hp_kernel_name(k, 0, 1); }
 
-extern "C" const char* pdf_stage_name(pdf_problem* h, int32_t k) { return hp_kernel_name(k, h ? h->cfg.precision : 0); }
+extern "C" const char* pdf_stage_name(pdf_problem* h, int32_t k) {
+  return hp_kernel_name(k, h ? h->cfg.precision : 0, h ? h->d.fold : 1);
+}

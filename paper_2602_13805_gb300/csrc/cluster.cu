@@ -7,17 +7,18 @@
 //   2. column DFT, x G_D spectrum, inverse column DFT on its columns; rows < ny go back
 //      to their row owners over DSMEM                                                  | cluster barrier
 //   3. inverse row DFT -> G_D J, s = beta J + E_inc + G_D J; this incidence's per-pixel
-//      contributions beta J conj(s), |s|^2 to a global array (double-buffered by iteration);
-//      partial G_S J_p over its pixels sent to every CTA of the cluster                  | GRID barrier
+//      contributions beta J conj(s), |s|^2 to a global array (double-buffered by iteration) | GRID barrier
 //   4. R-hat, chi-hat (Eq. 6, 7) for its rows and one halo row each side from the sums over all
 //      incidences; the TV / bridge pieces of Eq. 18-19 once per pixel; state residual (Eq. 15),
-//      data residual r_d,p (Eq. 16), regulariser cotangent -> w; adjoint inputs u, v;
-//      G_S^H r_d,p; row DFT of u -> column owners                                       | cluster barrier
+//      regulariser cotangent -> w; adjoint inputs u, v; row DFT of u -> column owners    | cluster barrier
 //   5. column convolution with the conjugated spectrum (G_D^H) -> row owners             | cluster barrier
-//   6. inverse row DFT, dL/dJ = v + G_D^H u + G_S^H term, analysis along x (a warp
-//      reduce-scatter over the row), partial analysis along y over its rows -> every CTA | cluster barrier
-//   7. dL/d alpha_p = sum of the partials (same order in every CTA), Adam step on each CTA's copy
-//      of alpha_p (identical in all CTAs of the cluster)
+//   6. inverse row DFT, dL/dJ = v + G_D^H u, analysis along x (a warp reduce-scatter over the
+//      row), partial analysis along y over its rows -> every CTA                          | cluster barrier
+//   7. dL/d alpha_p = sum of the partials (same order in every CTA) + the data term, Adam step on
+//      each CTA's copy of alpha_p (identical in all CTAs of the cluster)
+// The data term goes through the folded receiver operator G_S Phi (held whole in every CTA):
+// r_d,p = (G_S Phi) alpha_p - E_sca,p (Eq. 16) is formed in phase 1 from the current alpha_p and
+// its adjoint (2 / ||E_sca||^2) (G_S Phi)^H r_d,p is added to the gradient in phase 7.
 // The loss value itself is not formed in the loop (the solver evaluates it once at the final
 // iterate); the G_D spectrum slice, the x basis and the y-basis rows stay in shared memory.
 // The formulas are those of the stand-alone kernels (FP32 with compensated sums); only the data
@@ -38,7 +39,6 @@ constexpr int CL_NW = CL_NT / 32;
 
 struct ClusterArgs {
   int iters, C, RB, CB;
-  int gs_smem;            // 1: this CTA's G_S columns [nr][RB nx] are staged in shared memory
   float2* alpha;          // [ni][ky][kx] in / out
   const float2* tab;
   int cap;
@@ -83,9 +83,26 @@ __device__ __forceinline__ void cl_grid_barrier(unsigned* bar, unsigned target, 
   __syncthreads();
 }
 
-// split cluster barrier (all threads of every CTA of the cluster take part)
-__device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" : : : "memory"); }
-__device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" : : : "memory"); }
+// Phase timestamps (instrumented builds, -DPDF_PHASE_STAMPS): thread 0 of CTA 0 records the
+// global timer right after each barrier of iterations CL_STAMP_IT0 .. CL_STAMP_IT0 + 3.  Other
+// builds compile the marks to nothing.
+#define CL_STAMP_IT0 5
+#ifdef PDF_PHASE_STAMPS
+__device__ unsigned long long g_cl_stamps[4][16];
+#define CL_STAMP(i)                                                                             \
+  do {                                                                                          \
+    if (blockIdx.x == 0 && threadIdx.x == 0 && it >= CL_STAMP_IT0 && it < CL_STAMP_IT0 + 4) {   \
+      unsigned long long t_;                                                                    \
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_));                                    \
+      g_cl_stamps[it - CL_STAMP_IT0][i] = t_;                                                   \
+    }                                                                                           \
+  } while (0)
+#else
+#define CL_STAMP(i) \
+  do {              \
+  } while (0)
+#endif
+
 
 // One padded line per warp through the register FFT.  The transforms are called out of line (one
 // copy of each in the kernel): the loop body then stays small enough for the instruction cache.
@@ -112,22 +129,6 @@ __device__ __noinline__ Line<P> line_conv(Line<P> x, Line<P> g, const float2* __
   return x;
 }
 
-// Warp reduce-scatter of 16 complex values: on return lane l holds in a[0] the sum over the
-// warp of the values with index l >> 1 (each halving step keeps the half selected by one lane bit).
-__device__ __forceinline__ void warp_reduce_scatter16(float2 (&a)[16], int lane) {
-#pragma unroll
-  for (int st = 0; st < 4; ++st) {
-    const int h = 16 >> st, n = 8 >> st;
-    const bool up = (lane & h) != 0;
-#pragma unroll
-    for (int i = 0; i < n; ++i) {
-      const float2 send = up ? a[i] : a[i + n];
-      const float2 keep = up ? a[i + n] : a[i];
-      a[i] = keep + shfl_xor2(send, h);
-    }
-  }
-  a[0] = a[0] + shfl_xor2(a[0], 1);
-}
 
 template <int P>
 __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a) {
@@ -169,8 +170,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
   float* itv = mgs + HP;                     // [TP] 1 / t (TV magnitude)                 (phase 4)
   float* sge = itv + TP;                     // [TP] sigmoid * exp (bridge term)          (phase 4)
   float* sgs = sge + TP;                     // [GP] sigmoid, own rows                    (phase 4)
-  float2* dpart = gpart + NU;                // [C][nr] partial G_S J_p of all ranks
-  float2* rd = dpart + C * nr;               // [nr]
+  float2* rd = gpart + NU;                   // [nr] data residual r_d,p
   float2* es = rd + nr;                      // [nr]
   float2* T2 = es + nr;                      // [RB][kx] synthesis / analysis temporary
   float2* wys = T2 + RB * kx;                // [ky][RB] rows y0 .. y0+RB-1 of the y basis
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
   float2* wxs = ghs + CB * P;                // [kx][nx] x basis
   float* am = (float*)(wxs + kx * nx);       // [2 NA]
   float* av = am + 2 * NA;                   // [2 NA]
-  float2* Gs = (float2*)(av + 2 * NA);       // [nr][GP] when a.gs_smem
+  float2* gsf = (float2*)(av + 2 * NA);      // [nr][NA] folded receiver operator
 
   // ---- one-time loads ----
 #pragma unroll 1
@@ -202,22 +202,15 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
   for (int i = threadIdx.x; i < CB * P; i += CL_NT) ghs[i] = d.ghat_perm[(size_t)c0 * P + i];
 #pragma unroll 1
   for (int i = threadIdx.x; i < kx * nx; i += CL_NT) wxs[i] = d.wx[i];
-  if (a.gs_smem)
 #pragma unroll 1
-    for (int i = threadIdx.x; i < nr * GP; i += CL_NT) {
-      const int r = i / GP, j = i - r * GP;
-      Gs[i] = d.gs[(size_t)r * M + y0 * nx + j];
-    }
-  // G_S entry of receiver r at own pixel j (j = local row * nx + x): staged copy or global rows
-  const float2* gsb = a.gs_smem ? Gs : d.gs + (size_t)y0 * nx;
-  const int gss = a.gs_smem ? GP : M;
-  auto gsv = [&](int r, int j) -> float2 { return gsb[(size_t)r * gss + j]; };
+  for (int i = threadIdx.x; i < nr * NA; i += CL_NT) gsf[i] = d.gsf[i];
   const float ke = d.invn[0], ks = d.invn[1];
   const float2 beta = d.beta, bc = cconj(d.beta);
   const unsigned nblocks = gridDim.x;
   cl.sync();
 
   for (int it = 0; it < a.iters; ++it) {
+    CL_STAMP(0);
     float4* nd = a.nd + (size_t)(it & 1) * ni * M;
     // ===== 1. synthesis of own rows, row DFT, scatter to column owners =====
 #pragma unroll 1
@@ -228,7 +221,17 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
       for (int jy = 0; jy < ky; ++jy) acc = acc + cmul(wys[jy * RB + yl], al[jy * kx + jx]);
       T2[i] = acc;
     }
+#pragma unroll 1
+    for (int r = warp; r < nr; r += CL_NW) {                             // r_d,p = (G_S Phi) alpha_p - E_sca,p
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 4
+      for (int j = lane; j < NA; j += 32) acc = acc + cmul(gsf[r * NA + j], al[j]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc = acc + shfl_xor2(acc, o);
+      if (lane == 0) rd[r] = acc - es[r];
+    }
     __syncthreads();
+    CL_STAMP(1);
 #pragma unroll 1
     for (int i = threadIdx.x; i < GP; i += CL_NT) {                    // J = T' Wx on own pixels (Eq. 9)
       const int yl = i / nx, x = i - yl * nx;
@@ -238,6 +241,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
       Js[i] = s;
     }
     __syncthreads();
+    CL_STAMP(2);
 #pragma unroll 1
     for (int yl = warp; yl < RB; yl += CL_NW) {
       Line<P> L;
@@ -255,6 +259,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
       }
     }
     cl.sync();
+    CL_STAMP(3);
     // ===== 2. column convolution, results back to row owners =====
 #pragma unroll 1
     for (int lc = warp; lc < CB; lc += CL_NW) {
@@ -278,6 +283,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
       }
     }
     cl.sync();
+    CL_STAMP(4);
     // ===== 3. inverse row DFT, s, per-incidence contributions, partial G_S J_p =====
 #pragma unroll 1
     for (int yl = warp; yl < RB; yl += CL_NW) {
@@ -292,6 +298,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
       }
     }
     __syncthreads();
+    CL_STAMP(5);
 #pragma unroll 1
     for (int i = threadIdx.x; i < GP; i += CL_NT) {
       const int yl = i / nx, x = i - yl * nx;
@@ -301,35 +308,9 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
       const float2 n = cmul(beta, cmulc(J, s));
       __stcg(&nd[(size_t)p * M + y0 * nx + i], make_float4(n.x, n.y, cabs2(s), 0.f));
     }
-#pragma unroll 1
-    for (int r = warp; r < nr; r += CL_NW) {                              // partial (G_S J_p)[r] over own pixels
-      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-      int i = lane;
-#pragma unroll 4
-      for (; i + 32 < GP; i += 64) {
-        a0 = a0 + cmul(gsv(r, i), Js[i]);
-        a1 = a1 + cmul(gsv(r, i + 32), Js[i + 32]);
-      }
-      if (i < GP) a0 = a0 + cmul(gsv(r, i), Js[i]);
-      float2 acc = a0 + a1;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc = acc + shfl_xor2(acc, o);
-      if (lane < C) {
-        float2* dst = cl.map_shared_rank(dpart, lane);
-        dst[k * nr + r] = acc;
-      }
-    }
-    cl_arrive();                                                         // DSMEM partials visible after cl_wait
     cl_grid_barrier(a.bar, (unsigned)(it + 1) * nblocks, a.err);
-    cl_wait();
+    CL_STAMP(6);
     // ===== 4. R-hat, chi-hat (own rows + halo), residuals, regulariser cotangent, adjoint inputs =====
-#pragma unroll 1
-    for (int r = threadIdx.x; r < nr; r += CL_NT) {                    // data residual of this incidence
-      float2 acc = make_float2(0.f, 0.f);
-#pragma unroll 1
-      for (int q = 0; q < C; ++q) acc = acc + dpart[q * nr + r];          // same order in every CTA
-      rd[r] = acc - es[r];
-    }
 #pragma unroll 1
     for (int i = threadIdx.x; i < HP; i += CL_NT) {
       const int hy = i / nx, x = i - hy * nx, y = y0 + hy - 1;
@@ -359,6 +340,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
       if (hy >= 1 && hy <= RB) Dl[(hy - 1) * nx + x] = clamped ? -Df : Df;
     }
     __syncthreads();
+    CL_STAMP(7);
     // TV and bridge pieces at (y, x) for rows y0-1 .. y0+RB-1, each computed once (Eq. 18, 19)
 #pragma unroll 1
     for (int i = threadIdx.x; i < TP; i += CL_NT) {
@@ -379,6 +361,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
       if (hy >= 1) sgs[i - nx] = sg;
     }
     __syncthreads();
+    CL_STAMP(8);
     // state residual, cotangent on chi -> w, u (into rowb) and v + G_S^H r_d (into vs)
 #pragma unroll 1
     for (int li = threadIdx.x; li < GP; li += CL_NT) {
@@ -418,13 +401,10 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
       const float2 cs = cmul(cmul(wc, beta), J) - (2.f * cmul(wc, Rv).x) * s;
       rowb[yl * P + x] = ke * cmulc(r, Rv) + cs;                         // u
       const float2 omr = make_float2(1.f - Rv.x, Rv.y);
-      const float2 vv = ke * cmul(cmul(make_float2(-bc.x, -bc.y), omr), r) + cmul(bc, cmul(w, s) + cs);
-      float2 gh = make_float2(0.f, 0.f);
-#pragma unroll 4
-      for (int q = 0; q < nr; ++q) gh = gh + cmulc(rd[q], gsv(q, li));
-      vs[li] = vv + ks * gh;
+      vs[li] = ke * cmul(cmul(make_float2(-bc.x, -bc.y), omr), r) + cmul(bc, cmul(w, s) + cs);   // v
     }
     __syncthreads();
+    CL_STAMP(9);
 #pragma unroll 1
     for (int yl = warp; yl < RB; yl += CL_NW) {                          // row DFT of u -> column owners
       Line<P> L;
@@ -442,6 +422,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
       }
     }
     cl.sync();
+    CL_STAMP(10);
     // ===== 5. column convolution with the conjugated spectrum =====
 #pragma unroll 1
     for (int lc = warp; lc < CB; lc += CL_NW) {
@@ -465,6 +446,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
       }
     }
     cl.sync();
+    CL_STAMP(11);
     // ===== 6. inverse row DFT, dL/dJ, analysis along x (warp reduce-scatter), partial analysis along y =====
 #pragma unroll 1
     for (int yl = warp; yl < RB; yl += CL_NW) {
@@ -495,6 +477,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
       }
     }
     __syncthreads();
+    CL_STAMP(12);
 #pragma unroll 1
     for (int i = threadIdx.x; i < NA; i += CL_NT) {
       const int jy = i / kx, jx = i - jy * kx;
@@ -508,18 +491,24 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
       }
     }
     cl.sync();
+    CL_STAMP(13);
     // ===== 7. gradient and Adam step on this CTA's copy of alpha_p =====
 #pragma unroll 1
     for (int i = threadIdx.x; i < NA; i += CL_NT) {
       float2 g = make_float2(0.f, 0.f);
 #pragma unroll 1
       for (int q = 0; q < C; ++q) g = g + gpart[q * NA + i];
+      float2 gd = make_float2(0.f, 0.f);
+#pragma unroll 4
+      for (int r = 0; r < nr; ++r) gd = gd + cmulc(rd[r], gsf[r * NA + i]);
+      g = g + ks * gd;                                                   // data term, Eq. 16
       float2 ap = al[i];
       ph_adam(0, &ap.x, &g.x, &am[2 * i], &av[2 * i], 1, it + 1, a.tab, a.cap, a.b1, a.b2, a.eps);
       ph_adam(0, &ap.y, &g.y, &am[2 * i + 1], &av[2 * i + 1], 1, it + 1, a.tab, a.cap, a.b1, a.b2, a.eps);
       al[i] = ap;
     }
     __syncthreads();
+    CL_STAMP(14);
   }
   if (k == 0)
 #pragma unroll 1
@@ -530,16 +519,14 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
 // ---------------------------------------------------------------------------
 // host
 // ---------------------------------------------------------------------------
-static size_t cluster_smem(const Dev& d, int C, int RB, int CB, int P, bool gs) {
+static size_t cluster_smem(const Dev& d, int C, int RB, int CB, int P) {
   const size_t NA = (size_t)d.ky * d.kx, GP = (size_t)RB * d.nx, HP = (size_t)(RB + 2) * d.nx,
                TP = (size_t)(RB + 1) * d.nx;
   const size_t nscr = 2 * GP + HP + 2 * TP;
   const size_t NU = std::max((size_t)C * NA, (nscr + 1) / 2);
-  const size_t f2 = P + (size_t)RB * P + (size_t)CB * (d.ny + 1) + 4 * GP + 2 * HP + NA + NU + (size_t)C * d.nr +
-                    2 * (size_t)d.nr + (size_t)RB * d.kx + (size_t)d.ky * RB + (size_t)CB * P + (size_t)d.kx * d.nx;
-  size_t b = f2 * sizeof(float2) + 4 * NA * sizeof(float);
-  if (gs) b += (size_t)d.nr * GP * sizeof(float2);
-  return b;
+  const size_t f2 = P + (size_t)RB * P + (size_t)CB * (d.ny + 1) + 4 * GP + 2 * HP + NA + NU + 2 * (size_t)d.nr +
+                    (size_t)RB * d.kx + (size_t)d.ky * RB + (size_t)CB * P + (size_t)d.kx * d.nx + (size_t)d.nr * NA;
+  return f2 * sizeof(float2) + 4 * NA * sizeof(float);
 }
 
 // dynamic shared memory limit of the cluster kernel (227 KB per block; no static use)
@@ -590,12 +577,23 @@ static pdf_status launch_cluster(pdf_problem* h, ClusterArgs a, size_t smem, cud
   return PDF_OK;
 }
 
+extern "C" pdf_status pdf_phase_stamps(uint64_t* out) {
+#ifdef PDF_PHASE_STAMPS
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_cl_stamps, sizeof(g_cl_stamps));
+  if (e != cudaSuccess) return cuda_err(e, "cudaMemcpyFromSymbol(phase stamps)");
+  return PDF_OK;
+#else
+  (void)out;
+  return set_err(PDF_EUNSUPPORTED, "phase stamps need a library built with PDF_PHASE_STAMPS");
+#endif
+}
+
 // Runs `iters` Adam iterations of h->alpha with the cluster kernel.  *done = false (nothing
 // launched) when not eligible.
 pdf_status cl_run(pdf_problem* h, const pdf_solve_opts* o, int iters, cudaStream_t st, bool* done) {
   *done = false;
   const Dev& d = h->d;
-  if (!d.fast || h->tc || d.Px != d.Py || d.Px > 128 || iters < 1 || d.kx > 64) return PDF_OK;
+  if (!d.fast || h->tc || !d.fold || d.Px != d.Py || d.Px > 128 || iters < 1 || d.kx > 64) return PDF_OK;
   int dev = 0, sms = 0, coop = 0;
   PDF_CUDA(cudaGetDevice(&dev));
   PDF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -623,12 +621,7 @@ pdf_status cl_run(pdf_problem* h, const pdf_solve_opts* o, int iters, cudaStream
     a.C = c;
     a.RB = d.ny / c;
     a.CB = d.Px / c;
-    size_t smem = cluster_smem(d, c, a.RB, a.CB, d.Px, true);
-    a.gs_smem = 1;
-    if (smem > CL_SMEM_MAX) {
-      smem = cluster_smem(d, c, a.RB, a.CB, d.Px, false);
-      a.gs_smem = 0;
-    }
+    const size_t smem = cluster_smem(d, c, a.RB, a.CB, d.Px);
     if (smem > CL_SMEM_MAX) continue;
     if (d.Px == 64) s = launch_cluster<64>(h, a, smem, st, done);
     else if (d.Px == 128) s = launch_cluster<128>(h, a, smem, st, done);

@@ -123,6 +123,30 @@ __device__ __forceinline__ FF ff_block_sum(FF v, FF* scratch) {
   return r;
 }
 
+// N sums over the block in one pass (valid in thread 0).  `scratch` needs 32 N FF of shared memory.
+template <int N>
+__device__ __forceinline__ void ff_block_sum_multi(FF (&v)[N], FF* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int s = 0; s < N; ++s) v[s] = ff_add(v[s], ff_shfl_xor(v[s], o));
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int s = 0; s < N; ++s) scratch[s * 32 + wid] = v[s];
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int s = 0; s < N; ++s) v[s] = lane < nw ? scratch[s * 32 + lane] : FF{0.f, 0.f};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int s = 0; s < N; ++s) v[s] = ff_add(v[s], ff_shfl_xor(v[s], o));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // FFT plan: P = product of radices (each 2, 3 or 4), Stockham ordering
 // ---------------------------------------------------------------------------

@@ -72,7 +72,7 @@ pdf_status fp_configure() {
 size_t fp_smem_synth(const Dev& d) { return ((size_t)d.Px + (size_t)d.ky * d.kx) * sizeof(float2); }
 size_t fp_smem_col(const Dev& d) { return ((size_t)d.Py + (size_t)FCOLS * (d.ny + 1)) * sizeof(float2); }
 size_t fp_smem_state(const Dev& d) { return (size_t)d.Px * sizeof(float2) * 2 + 3 * FW * (size_t)d.Px * sizeof(float); }
-size_t fp_smem_ana(const Dev& d) { return ((size_t)d.Px + (size_t)FW * d.nx) * sizeof(float2); }
+size_t fp_smem_ana(const Dev& d) { return (size_t)d.Px * sizeof(float2); }
 
 pdf_status fp_synth_rowfft(const Dev& d, const float2* alpha, float2* Jout, int do_fft, cudaStream_t st) {
 #define L(P) kf_synth_rowfft<P><<<frow_grid(d), FT, fp_smem_synth(d), st>>>(d, alpha, Jout, do_fft)

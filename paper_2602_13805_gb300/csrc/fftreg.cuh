@@ -89,6 +89,23 @@ __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
   return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
 }
 
+// Warp reduce-scatter of 16 complex values: on return lane l holds in a[0] the sum over the
+// warp of the values with index l >> 1 (each halving step keeps the half selected by one lane bit).
+__device__ __forceinline__ void warp_reduce_scatter16(float2 (&a)[16], int lane) {
+#pragma unroll
+  for (int st = 0; st < 4; ++st) {
+    const int h = 16 >> st, n = 8 >> st;
+    const bool up = (lane & h) != 0;
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      const float2 send = up ? a[i] : a[i + n];
+      const float2 keep = up ? a[i + n] : a[i];
+      a[i] = keep + shfl_xor2(send, h);
+    }
+  }
+  a[0] = a[0] + shfl_xor2(a[0], 1);
+}
+
 template <int P> struct WarpFFT {
   static constexpr int R = P / 32;
 

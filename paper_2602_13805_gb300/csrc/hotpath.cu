@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_adj_rowifft_ana(Dev d, const fl
       const int rr = i / d.nx, x = i - rr * d.nx;
       if (rr < nrow) {
         const size_t idx = (size_t)p * d.M + (y0 + rr) * d.nx + x;
-        g[rr * d.Px + x] = g[rr * d.Px + x] + d.v[idx] + d.gsh[idx];
+        g[rr * d.Px + x] = d.fold ? g[rr * d.Px + x] + d.v[idx] : g[rr * d.Px + x] + d.v[idx] + d.gsh[idx];
       }
     }
   } else {
@@ -349,6 +349,104 @@ __global__ void __launch_bounds__(256) k_ana_y(Dev d, const float2* T2, float2* 
 }
 
 // terms[6] = L, State, Data, Bound, TV, Bridge from the partial sums
+// Data residual through the folded operator (Eq. 16 with J = Phi alpha, Eq. 9):
+// r_d[p][r] = sum_j gsf[r][j] alpha[p][j] - E_sca[p][r].  Each warp takes `opw` consecutive
+// outputs o = p nr + r (8 warps per block), its lanes stride over j; the block's float-float
+// sum of |r_d|^2 goes to lp[block].
+__global__ void __launch_bounds__(256) k_gsf_fwd(Dev d, const float2* __restrict__ alpha,
+                                                 const float2* __restrict__ esca, float2* __restrict__ rd, FF* lp,
+                                                 int opw) {
+  __shared__ FF red_gf[32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int NA = d.ky * d.kx, nout = d.ni * d.nr;
+  FF a2 = FF{0.f, 0.f};
+  const int o0 = (blockIdx.x * 8 + warp) * opw;
+  for (int o = o0; o < min(o0 + opw, nout); ++o) {
+    const int p = o / d.nr, r = o - p * d.nr;
+    const float2* g = d.gsf + (size_t)r * NA;
+    const float2* al = alpha + (size_t)p * NA;
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (int j = lane; j < NA; j += 32) acc = acc + cmul(__ldg(&g[j]), __ldg(&al[j]));
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) acc = acc + shfl_xor2(acc, m);
+    if (lane == 0) {
+      const float2 v = acc - esca[o];
+      rd[o] = v;
+      a2 = ff_add(a2, cabs2(v));
+    }
+  }
+  const FF t = ff_block_sum(a2, red_gf);
+  if (lp && threadIdx.x == 0) lp[blockIdx.x] = t;
+}
+
+// Adjoint data term on the coefficients: g[p][j] += (2 / ||E_sca||^2) sum_r conj(gsf[r][j]) r_d[p][r].
+// Block (jb, p): 32 coefficients; its 8 warps take every 8th receiver and their partial sums are
+// added in warp order.
+__global__ void __launch_bounds__(256) k_gsf_adj(Dev d, const float2* __restrict__ rd, float2* __restrict__ g) {
+  __shared__ float2 part[8][32];
+  const int NA = d.ky * d.kx, p = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * 32 + lane;
+  float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+  if (j < NA) {
+    const float2* rp = rd + (size_t)p * d.nr;
+    int r = warp;
+#pragma unroll 4
+    for (; r + 8 < d.nr; r += 16) {
+      a0 = a0 + cmulc(__ldg(&rp[r]), __ldg(&d.gsf[(size_t)r * NA + j]));
+      a1 = a1 + cmulc(__ldg(&rp[r + 8]), __ldg(&d.gsf[(size_t)(r + 8) * NA + j]));
+    }
+    if (r < d.nr) a0 = a0 + cmulc(__ldg(&rp[r]), __ldg(&d.gsf[(size_t)r * NA + j]));
+  }
+  part[warp][lane] = a0 + a1;
+  __syncthreads();
+  if (warp == 0 && j < NA) {
+    float2 s = part[0][lane];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) s = s + part[w][lane];
+    const size_t i = (size_t)p * NA + j;
+    g[i] = g[i] + d.invn[1] * s;
+  }
+}
+
+// Analysis along y (second half of Phi^H): out[p][jy][jx] = sum_y T2[p][y][jx] conj(Wy[jy][y]).
+// Block (p, jy group of 8) stages T2[p] and the 8 rows of Wy in shared memory; warp jl owns
+// coefficient row jy = 8 blockIdx.y + jl, its lanes the jx (kx <= 64).
+__global__ void __launch_bounds__(256) k_ana_y_sm(Dev d, const float2* __restrict__ T2, float2* __restrict__ out) {
+  extern __shared__ float2 smy[];
+  const int p = blockIdx.x, jl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ny = d.ny, kx = d.kx, jy0 = blockIdx.y * 8;
+  float2* Ts = smy;                 // [ny][kx]
+  float2* Ws = smy + ny * kx;       // [8][ny]
+  const float2* T = T2 + (size_t)p * ny * kx;
+  for (int i = threadIdx.x; i < ny * kx; i += blockDim.x) Ts[i] = T[i];
+  for (int i = threadIdx.x; i < 8 * ny; i += blockDim.x) {
+    const int a = i / ny, y = i - a * ny;
+    Ws[i] = jy0 + a < d.ky ? d.wy[(size_t)(jy0 + a) * ny + y] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int jy = jy0 + jl;
+  if (jy >= d.ky) return;
+  float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+  const float2* w = Ws + jl * ny;
+#pragma unroll 4
+  for (int y = 0; y < ny; ++y) {
+    const float2 wv = w[y];
+    if (lane < kx) a0 = a0 + cmulc(Ts[y * kx + lane], wv);
+    if (lane + 32 < kx) a1 = a1 + cmulc(Ts[y * kx + lane + 32], wv);
+  }
+  float2* o = out + ((size_t)p * d.ky + jy) * kx;
+  if (lane < kx) o[lane] = a0;
+  if (lane + 32 < kx) o[lane + 32] = a1;
+}
+
+static size_t sm_ana_y(const Dev& d) { return ((size_t)d.ny * d.kx + 8 * (size_t)d.ny) * sizeof(float2); }
+static bool ana_y_sm_ok(const Dev& d) { return d.kx <= 64 && sm_ana_y(d) <= 100 * 1024; }
+
+// outputs per warp of k_gsf_fwd, so that its block count stays within the loss-partial strip
+static int gsf_opw(const Dev& d) { return std::max(1, (d.ni * d.nr + 8 * PDF_LP_STRIDE - 1) / (8 * PDF_LP_STRIDE)); }
+static int gsf_blocks(const Dev& d) { return (d.ni * d.nr + 8 * gsf_opw(d) - 1) / (8 * gsf_opw(d)); }
+
 __global__ void k_finalize(Dev d, double* terms, int n_state, int n_data, int n_reg, int* step_inc) {
   ph_finalize(d, terms, n_state, n_data, n_reg, step_inc);
 }
@@ -384,6 +482,7 @@ pdf_status hp_configure_kernels() {
   cudaFuncSetAttribute(k_gsh, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_adj_rowfft, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_adj_rowifft_ana, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_ana_y_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(e, "cudaFuncSetAttribute");
   return PDF_OK;
@@ -392,7 +491,7 @@ pdf_status hp_configure_kernels() {
 static inline dim3 row_grid(const Dev& d) { return dim3((d.ny + ROWS_PER_CTA - 1) / ROWS_PER_CTA, d.ni); }
 static inline dim3 col_grid(const Dev& d) { return dim3((d.Px + COL_CW - 1) / COL_CW, d.ni); }
 
-int hp_kernels_per_loss_grad(const pdf_problem* h) { return h->tc ? 11 : 12; }
+int hp_kernels_per_loss_grad(const pdf_problem* h) { return (h->tc || h->d.fold) ? 11 : 12; }
 
 pdf_status hp_check_limits(const Dev& d) {
   const size_t lim = 200 * 1024;
@@ -413,7 +512,18 @@ static const char* kLossGradStagesTC[] = {
     "tc_synth(synth1+gemm+post)", "k_colconv", "k_rowifft_state", "tc_gs(gemm+reduce)", "k_reg",
     "k_adj_rowfft", "k_colconv(conj)", "tc_gsh(gemm)", "tc_adj(rowifft+gemm)", "k_ana_y", "k_finalize"};
 
-const char* hp_kernel_name(int k, int precision) {
+static const char* kLossGradKernelsFold[] = {
+    "k_synth_rowfft", "k_colconv", "k_rowifft_state", "k_gsf_fwd", "k_reg", "k_adj_rowfft",
+    "k_colconv(conj)", "k_adj_rowifft_ana", "k_ana_y", "k_gsf_adj", "k_finalize"};
+static const char* kLossGradStagesTCFold[] = {
+    "tc_synth(synth1+gemm+post)", "k_colconv", "k_rowifft_state", "k_gsf_fwd", "k_reg", "k_adj_rowfft",
+    "k_colconv(conj)", "tc_adj(rowifft+gemm)", "k_ana_y", "k_gsf_adj", "k_finalize"};
+
+const char* hp_kernel_name(int k, int precision, int fold) {
+  if (fold) {
+    if (k < 0 || k >= 11) return "";
+    return precision == 1 ? kLossGradStagesTCFold[k] : kLossGradKernelsFold[k];
+  }
   if (precision == 1) return (k >= 0 && k < 11) ? kLossGradStagesTC[k] : "";
   return (k >= 0 && k < 12) ? kLossGradKernels[k] : "";
 }
@@ -422,7 +532,7 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
                         int* step_inc, cudaEvent_t* ev) {
   Dev& d = h->d;
   const int nout = d.ni * d.nr;
-  const int n_data_blocks = (nout + 255) / 256;
+  const int n_data_blocks = d.fold ? gsf_blocks(d) : (nout + 255) / 256;
   const bool tc = h->tc != nullptr;
   pdf_status s;
   int k = 0;
@@ -451,7 +561,10 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
     k_rowifft_state<<<d.ny, ROW_THREADS, sm_row(d), st>>>(d);
   }
   mark();
-  if (tc) {
+  if (d.fold) {
+    k_gsf_fwd<<<n_data_blocks, 256, 0, st>>>(d, alpha, d.esca, d.rd, d.lpart + LP_DATA * PDF_LP_STRIDE,
+                                              gsf_opw(d));
+  } else if (tc) {
     if ((s = tc_gs_fwd(h, nullptr, d.esca, d.rd, d.lpart + LP_DATA * PDF_LP_STRIDE, 1, st)) != PDF_OK) return s;
   } else {
     k_gs_partial<<<d.n_gs_chunks, 256, sm_gs(d), st>>>(d, d.J, d.gspart);
@@ -460,7 +573,7 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
                                                 d.lpart + LP_DATA * PDF_LP_STRIDE);
   }
   mark();
-  k_reg<<<d.n_reg_blocks, 256, 0, st>>>(d);
+  k_reg<<<d.n_reg_blocks, 128, 0, st>>>(d);
   mark();
   // adjoint
   if (d.fast) {
@@ -477,13 +590,17 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
   mark();
   const float2* T2 = d.T2;
   if (tc) {
-    if ((s = tc_gsh(h, nullptr, 1, st)) != PDF_OK) return s;
-    mark();
+    if (!d.fold) {
+      if ((s = tc_gsh(h, nullptr, 1, st)) != PDF_OK) return s;
+      mark();
+    }
     if ((s = tc_adj_ana(h, st)) != PDF_OK) return s;
     T2 = (const float2*)h->tc->c_ana;
   } else {
-    k_gsh<<<(d.M + GSH_CHUNK - 1) / GSH_CHUNK, 256, sm_gsh(d), st>>>(d, d.rd, d.gsh, 0.f, 1);
-    mark();
+    if (!d.fold) {
+      k_gsh<<<(d.M + GSH_CHUNK - 1) / GSH_CHUNK, 256, sm_gsh(d), st>>>(d, d.rd, d.gsh, 0.f, 1);
+      mark();
+    }
     if (d.fast) {
       if ((s = fp_adj_rowifft_ana(d, nullptr, 0, st)) != PDF_OK) return s;
     } else {
@@ -492,11 +609,18 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
   }
   mark();
   float2* g = grad ? grad : h->grad;
-  k_ana_y<<<dim3(d.ky, d.ni), 256, 0, st>>>(d, T2, g);
+  if (ana_y_sm_ok(d))
+    k_ana_y_sm<<<dim3(d.ni, (d.ky + 7) / 8), 256, sm_ana_y(d), st>>>(d, T2, g);
+  else
+    k_ana_y<<<dim3(d.ky, d.ni), 256, 0, st>>>(d, T2, g);
   mark();
+  if (d.fold) {
+    k_gsf_adj<<<dim3((d.ky * d.kx + 31) / 32, d.ni), 256, 0, st>>>(d, d.rd, g);
+    mark();
+  }
   k_finalize<<<1, 256, 0, st>>>(d, terms ? terms : h->terms, d.ny, n_data_blocks, d.n_reg_blocks, step_inc);
   mark();
-  pdf_count_launch(tc ? 7 : 12);
+  pdf_count_launch(d.fold ? (tc ? 9 : 11) : (tc ? 7 : 12));
   PDF_LAUNCHED("pdf_loss_grad");
   return PDF_OK;
 }
@@ -568,7 +692,10 @@ pdf_status hp_analysis(pdf_problem* h, const float2* in, float2* out, cudaStream
   } else {
     k_adj_rowifft_ana<<<row_grid(d), ROW_THREADS, sm_row(d), st>>>(d, in, 1);
   }
-  k_ana_y<<<dim3(d.ky, d.ni), 256, 0, st>>>(d, T2, out);
+  if (ana_y_sm_ok(d))
+    k_ana_y_sm<<<dim3(d.ni, (d.ky + 7) / 8), 256, sm_ana_y(d), st>>>(d, T2, out);
+  else
+    k_ana_y<<<dim3(d.ky, d.ni), 256, 0, st>>>(d, T2, out);
   pdf_count_launch(2);
   PDF_LAUNCHED("analysis");
   return PDF_OK;

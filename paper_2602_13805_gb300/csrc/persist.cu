@@ -187,7 +187,7 @@ pdf_status ps_run(pdf_problem* h, const pdf_solve_opts* o, int iters, unsigned* 
                   bool* done) {
   *done = false;
   const Dev& d = h->d;
-  if (!d.fast || h->tc || d.Px != d.Py || iters < 1) return PDF_OK;
+  if (!d.fast || h->tc || d.fold || d.Px != d.Py || iters < 1) return PDF_OK;   // unfolded data term only
   PersistArgs a;
   a.iters = iters;
   a.alpha = h->alpha;

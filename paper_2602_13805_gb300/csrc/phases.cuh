@@ -288,40 +288,57 @@ template <int PX>
 __device__ __forceinline__ void ph_adj_rowifft_ana(const Dev& d, int bx, int by, float2* sm, const float2* in,
                                                    int mode) {
   constexpr int R = PX / 32;
-    float2* tw = sm;
-  float2* g = sm + PX;                   // [FW][nx]
+  float2* tw = sm;
   const int p = by, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int y0 = bx * FW;
-  const int y = y0 + warp;
+  const int y = bx * FW + warp;
   load_tw<PX>(tw, d.twx);
   __syncthreads();
   if (y < d.ny) {
     const size_t row = (size_t)p * d.ny + y;
+    float2 g[R];
     if (mode == 0) {
-      float2 v[R];
 #pragma unroll
-      for (int k = 0; k < R; ++k) v[k] = d.A[row * PX + k * 32 + lane];
-      WarpFFT<PX>::inverse(v, tw, lane);
+      for (int k = 0; k < R; ++k) g[k] = d.A[row * PX + k * 32 + lane];
+      WarpFFT<PX>::inverse(g, tw, lane);
 #pragma unroll
       for (int m = 0; m < R; ++m) {
         const int x = lane + 32 * m;
         if (x < d.nx) {
           const size_t idx = row * d.nx + x;
-          g[warp * d.nx + x] = v[m] + d.v[idx] + d.gsh[idx];
+          g[m] = d.fold ? g[m] + d.v[idx] : g[m] + d.v[idx] + d.gsh[idx];
+        } else {
+          g[m] = make_float2(0.f, 0.f);
         }
       }
     } else {
-      for (int x = lane; x < d.nx; x += 32) g[warp * d.nx + x] = in[row * d.nx + x];
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int x = lane + 32 * m;
+        g[m] = x < d.nx ? in[row * d.nx + x] : make_float2(0.f, 0.f);
+      }
+    }
+    // analysis along x: T2[p][y][jx] = sum_x g[x] conj(Wx[jx][x]), 16 coefficients per warp
+    // reduce-scatter (lanes read Wx rows contiguously)
+    for (int j0 = 0; j0 < d.kx; j0 += 16) {
+      float2 acc[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc[j] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        if (32 * m >= d.nx) break;               // warp-uniform: the remaining slots are padding
+        const int x = lane + 32 * m;
+        if (x < d.nx) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (j0 + j < d.kx) acc[j] = acc[j] + cmulc(g[m], __ldg(&d.wx[(size_t)(j0 + j) * d.nx + x]));
+        }
+      }
+      warp_reduce_scatter16(acc, lane);
+      const int jx = j0 + (lane >> 1);
+      if ((lane & 1) == 0 && jx < d.kx) d.T2[row * d.kx + jx] = acc[0];
     }
   }
   __syncthreads();
-  const int nrow = min(FW, d.ny - y0);
-  for (int i = threadIdx.x; i < nrow * d.kx; i += blockDim.x) {
-    const int rr = i / d.kx, jx = i - rr * d.kx;
-    float2 acc = make_float2(0.f, 0.f);
-    for (int x = 0; x < d.nx; ++x) acc = acc + cmulc(g[rr * d.nx + x], __ldg(&d.wx[jx * d.nx + x]));
-    d.T2[((size_t)p * d.ny + y0 + rr) * d.kx + jx] = acc;
-  }
 }
 
 
@@ -538,7 +555,7 @@ __device__ __forceinline__ TVB tvb_at(const Dev& d, int y, int x) {
 
 
 __device__ __forceinline__ void ph_reg(const Dev& d, int bx) {
-  __shared__ FF red_rg[32];
+  __shared__ FF red_rg[3 * 32];
   const int n = bx * blockDim.x + threadIdx.x;
   float lb = 0.f, ltv = 0.f, lbr = 0.f;
   if (n < d.M) {
@@ -577,13 +594,12 @@ __device__ __forceinline__ void ph_reg(const Dev& d, int bx) {
     }
     d.w[n] = w;
   }
-  const FF tb = ff_block_sum(ff_make(lb), red_rg);
-  const FF tt = ff_block_sum(ff_make(ltv), red_rg);
-  const FF tr = ff_block_sum(ff_make(lbr), red_rg);
+  FF t3[3] = {ff_make(lb), ff_make(ltv), ff_make(lbr)};
+  ff_block_sum_multi<3>(t3, red_rg);
   if (threadIdx.x == 0) {
-    d.lpart[LP_BOUND * PDF_LP_STRIDE + bx] = tb;
-    d.lpart[LP_TV * PDF_LP_STRIDE + bx] = tt;
-    d.lpart[LP_BRIDGE * PDF_LP_STRIDE + bx] = tr;
+    d.lpart[LP_BOUND * PDF_LP_STRIDE + bx] = t3[0];
+    d.lpart[LP_TV * PDF_LP_STRIDE + bx] = t3[1];
+    d.lpart[LP_BRIDGE * PDF_LP_STRIDE + bx] = t3[2];
   }
 }
 
@@ -611,14 +627,18 @@ __device__ __forceinline__ void ph_ana_y(const Dev& d, int bx, int by, const flo
 
 
 __device__ __forceinline__ void ph_finalize(const Dev& d, double* terms, int n_state, int n_data, int n_reg, int* step_inc) {
-  __shared__ FF red_fn[32];
+  __shared__ FF red_fn[5 * 32];
   const int cnt[5] = {n_state, n_data, n_reg, n_reg, n_reg};
-  double tot[5];
+  FF a[5];
+#pragma unroll
   for (int s = 0; s < 5; ++s) {
-    FF a = FF{0.f, 0.f};
-    for (int i = threadIdx.x; i < cnt[s]; i += blockDim.x) a = ff_add(a, d.lpart[s * PDF_LP_STRIDE + i]);
-    tot[s] = ff_to_d(ff_block_sum(a, red_fn));
+    a[s] = FF{0.f, 0.f};
+    for (int i = threadIdx.x; i < cnt[s]; i += blockDim.x) a[s] = ff_add(a[s], d.lpart[s * PDF_LP_STRIDE + i]);
   }
+  ff_block_sum_multi<5>(a, red_fn);
+  double tot[5];
+#pragma unroll
+  for (int s = 0; s < 5; ++s) tot[s] = ff_to_d(a[s]);
   if (threadIdx.x == 0) {
     const double st = tot[0] / d.norms[0], da = tot[1] / d.norms[1];
     terms[1] = st;

@@ -34,6 +34,8 @@ struct Dev {
   const float2* ghat_perm; // [Px][Py] the same in the register FFT's digit-reversed order (fast path)
   const float2* einc;    // [ni][M]
   const float2* gs;      // [nr][M]
+  const float2* gsf;     // [nr][ky*kx] folded receiver operator G_S Phi (when fold)
+  int fold;              // 1: data term through gsf on the coefficients
   const float2* wx;      // [kx][nx] exp(+2 pi i f_k x / nx) / sqrt(nx)
   const float2* wy;      // [ky][ny]
   const float2* esca;    // [ni][nr]
@@ -130,7 +132,7 @@ pdf_status hp_configure_kernels();
 pdf_status hp_check_limits(const Dev& d);
 pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, double* terms, cudaStream_t st,
                         int* step_inc = nullptr, cudaEvent_t* ev = nullptr);
-const char* hp_kernel_name(int k, int precision);
+const char* hp_kernel_name(int k, int precision, int fold);
 __global__ void k_ana_y(Dev d, const float2* T2, float2* out);
 pdf_status hp_gd(pdf_problem* h, const float2* in, float2* out, int adjoint, cudaStream_t st);
 pdf_status hp_gs(pdf_problem* h, const float2* in, float2* out, const float2* subtract, FF* sumsq, cudaStream_t st);

@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_tc_adj_rowifft(Dev d, TC t) {
       const int n = (y0 + rr) * d.nx + x;
       const size_t idx = (size_t)p * d.M + n;
       const float* c = t.c_adj + (size_t)n * 2 * d.ni + 2 * p;
-      const float2 v = g[rr * d.Px + x] + d.v[idx] + make_float2(ks * c[0], ks * c[1]);
+      const float2 v = d.fold ? g[rr * d.Px + x] + d.v[idx] : g[rr * d.Px + x] + d.v[idx] + make_float2(ks * c[0], ks * c[1]);
       put_gja(t, p * d.ny + y0 + rr, x, v);
     }
   }
@@ -206,7 +206,7 @@ __global__ void k_tc_gja_combine(Dev d, TC t, const float2* __restrict__ gdh) {
   const int y = n / d.nx, x = n - y * d.nx;
   const float ks = d.invn[1];
   const float* c = t.c_adj + (size_t)n * 2 * d.ni + 2 * p;
-  put_gja(t, p * d.ny + y, x, gdh[i] + d.v[i] + make_float2(ks * c[0], ks * c[1]));
+  put_gja(t, p * d.ny + y, x, d.fold ? gdh[i] + d.v[i] : gdh[i] + d.v[i] + make_float2(ks * c[0], ks * c[1]));
 }
 
 __global__ void k_tc_field_to_gja(Dev d, TC t, const float2* __restrict__ X) {

@@ -47,6 +47,7 @@ class pdf_config(ctypes.Structure):
         ("tau_b", ctypes.c_double), ("eps_tv", ctypes.c_double), ("eps_abs", ctypes.c_double),
         ("q_min", ctypes.c_double),
         ("precision", ctypes.c_int32), ("fft_path", ctypes.c_int32),
+        ("fold_gs", ctypes.c_int32),
     ]
 
 
@@ -79,7 +80,8 @@ EXPORTS = ("pdf_config_default", "pdf_setup", "pdf_set_data", "pdf_loss_grad", "
            "pdf_solve_opts_default", "pdf_solve", "pdf_forward", "pdf_launch_count", "pdf_destroy",
            "pdf_last_error", "pdf_profile_loss_grad", "pdf_kernel_name", "pdf_gs_apply_static",
            "pdf_stage_name", "pdf_mlp_create", "pdf_mlp_destroy", "pdf_mlp_set_params", "pdf_mlp_get_params",
-           "pdf_mlp_forward", "pdf_mlp_loss_grad", "pdf_mlp_train_step", "pdf_mlp_error_flag")
+           "pdf_mlp_forward", "pdf_mlp_loss_grad", "pdf_mlp_train_step", "pdf_mlp_error_flag",
+           "pdf_phase_stamps")
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -113,6 +115,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pdf_destroy.restype = None
     lib.pdf_profile_loss_grad.argtypes = [vp, vp, i32, ctypes.POINTER(ctypes.c_float), i32, vp]
     lib.pdf_profile_loss_grad.restype = i32
+    lib.pdf_phase_stamps.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
+    lib.pdf_phase_stamps.restype = ctypes.c_int
     lib.pdf_kernel_name.argtypes = [i32]
     lib.pdf_kernel_name.restype = ctypes.c_char_p
     lib.pdf_stage_name.argtypes = [vp, i32]
@@ -172,7 +176,7 @@ def _stream(stream) -> Optional[int]:
 
 def make_config(nx, ny, side_x, side_y, k0, tx, rx, kx, ky, beta=6.0 + 0j, inc_kind=0, precision=0,
                 lambda_bound=1e-3, lambda_tv=1e-5, lambda_bridge=1e-5, tau_b=0.5, eps_tv=1e-8, eps_abs=1e-12,
-                q_min=1e-6, fft_path=0):
+                q_min=1e-6, fft_path=0, fold_gs=1):
     """Returns (pdf_config, keep-alive antenna arrays)."""
     lib = load()
     c = pdf_config()
@@ -190,6 +194,7 @@ def make_config(nx, ny, side_x, side_y, k0, tx, rx, kx, ky, beta=6.0 + 0j, inc_k
     c.tau_b, c.eps_tv, c.eps_abs, c.q_min = tau_b, eps_tv, eps_abs, q_min
     c.precision = precision
     c.fft_path = fft_path
+    c.fold_gs = fold_gs
     return c, (tx, rx)
 
 

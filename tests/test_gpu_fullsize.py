@@ -30,15 +30,15 @@ def big(request):
     return w, esca, a, t_ref, g_ref
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_fullsize_loss_gradient(big, precision):
+@pytest.mark.parametrize("precision,fold", [(0, 1), (1, 1), (0, 0), (1, 0)])
+def test_fullsize_loss_gradient(big, precision, fold):
     from paper_2602_13805_gb300 import pdf
     w, esca, a, t_ref, g_ref = big
-    prob = pdf.Problem.from_workload(w, esca=esca, precision=precision)
+    prob = pdf.Problem.from_workload(w, esca=esca, precision=precision, fold_gs=fold)
     terms, grad = prob.loss_grad(torch.from_numpy(a).cuda())
     t = terms.cpu().numpy()
     eg = rel(grad.cpu().numpy(), g_ref)
-    print(w.name, precision, "loss rel", abs(t[0] - t_ref[0]) / abs(t_ref[0]), "grad rel", eg)
+    print(w.name, precision, fold, "loss rel", abs(t[0] - t_ref[0]) / abs(t_ref[0]), "grad rel", eg)
     for k in range(3):
         assert abs(t[k] - t_ref[k]) <= TOL_FP32 * abs(t_ref[k])
     assert eg < TOL_FP32

@@ -20,10 +20,14 @@ def _w(name, over):
     return scenes.workload(base, **over)
 
 
-# register-FFT path (default) on every geometry, and the generic shared-memory FFT on two
+# register-FFT path (default) on every geometry, the generic shared-memory FFT on two, and the
+# unfolded data term (G_S applied to J every evaluation) on two
 PARITY_CASES = [(n, o, {}) for n, o in SMALL_CASES] + [("c2", dict(), {})] + [
     ("g24x20-smemfft", dict(nx=24, ny=20, ni=5, nr=7, kx=7, ky=5), dict(fft_path=1)),
     ("c1-smemfft", dict(), dict(fft_path=1)),
+    ("c1-unfolded", dict(), dict(fold_gs=0)),
+    ("c2-unfolded", dict(), dict(fold_gs=0)),
+    ("g24x20-smemfft-unfolded", dict(nx=24, ny=20, ni=5, nr=7, kx=7, ky=5), dict(fft_path=1, fold_gs=0)),
 ]
 
 
@@ -166,10 +170,15 @@ def test_solve_parity_relerr():
     # loop runs the same phase code inlined into one kernel (different FMA contraction is allowed)
     out_eager = prob.solve(iters=w.iters, chi_true=chi_t, use_graph=0)
     out_graph = prob.solve(iters=w.iters, chi_true=chi_t, use_graph=1)
-    out_pers = prob.solve(iters=w.iters, chi_true=chi_t, use_graph=2)
     assert torch.equal(out_eager["alpha"], out_graph["alpha"])
+    prob.close()
+    # the persistent loop implements the unfolded data term (G_S applied to J)
+    prob = c.problem(fold_gs=0)
+    out_eager = prob.solve(iters=w.iters, chi_true=chi_t, use_graph=0)
+    out_pers = prob.solve(iters=w.iters, chi_true=chi_t, use_graph=2)
     scale = out_eager["alpha"].abs().max().item()
     assert (out_eager["alpha"] - out_pers["alpha"]).abs().max().item() < 1e-6 * scale
+    assert abs(out_pers["relerr_cco"] - ref["relerr_cco"]) < 1e-3
     prob.close()
 
 
@@ -177,7 +186,7 @@ def test_solve_parity_relerr():
 def test_persistent_loop_matches_graph(name):
     w = scenes.workload(name, iters=40)
     c = Case(w)
-    prob = c.problem()
+    prob = c.problem(fold_gs=0)
     chi_t = _dev(c.chi.astype(np.complex64))
     a = prob.solve(iters=w.iters, chi_true=chi_t, use_graph=1)
     b = prob.solve(iters=w.iters, chi_true=chi_t, use_graph=2)
@@ -186,6 +195,24 @@ def test_persistent_loop_matches_graph(name):
     assert (a["alpha"] - b["alpha"]).abs().max().item() < 1e-6 * a["alpha"].abs().max().item()
     assert abs(a["relerr_cco"] - b["relerr_cco"]) < 1e-6
     prob.close()
+
+
+@pytest.mark.parametrize("name", ["c1", "c2", "cP"])
+def test_folded_data_term_matches_unfolded(name):
+    # (G_S Phi) alpha and its adjoint on the coefficients vs G_S applied to J = Phi alpha
+    w = scenes.workload(name)
+    c = Case(w)
+    a = _dev(c.alpha(scale=0.3, seed=5))
+    p0, p1 = c.problem(fold_gs=0), c.problem(fold_gs=1)
+    t0, g0 = p0.loss_grad(a)
+    t1, g1 = p1.loss_grad(a)
+    t0, t1 = t0.cpu().numpy(), t1.cpu().numpy()
+    print(name, "data term rel", abs(t1[2] - t0[2]) / abs(t0[2]), "grad rel", rel(g1.cpu().numpy(), g0.cpu().numpy()))
+    assert abs(t1[2] - t0[2]) <= 2e-6 * abs(t0[2])
+    np.testing.assert_allclose(t1, t0, rtol=2e-6)
+    assert rel(g1.cpu().numpy(), g0.cpu().numpy()) < 2e-6
+    p0.close()
+    p1.close()
 
 
 def test_torch_adam_matches_library_adam():

@@ -21,13 +21,16 @@ def _dev(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
-@pytest.fixture(scope="module", params=[("g24x20", dict(nx=24, ny=20, ni=5, nr=7, kx=7, ky=5)),
-                                        ("c1", dict()), ("c2", None)], ids=lambda c: c[0])
+# fold 0: G_S and G_S^H as tensor-core GEMMs on the synthesised currents; fold 1 (default): the
+# data term through the folded operator, the tensor cores then carry synthesis and analysis
+@pytest.fixture(scope="module", params=[("g24x20", dict(nx=24, ny=20, ni=5, nr=7, kx=7, ky=5), 0),
+                                        ("c1", dict(), 0), ("c2", None, 0), ("c1-fold", dict(), 1),
+                                        ("c2-fold", None, 1)], ids=lambda c: c[0])
 def case(request):
-    name, over = request.param
+    name, over, fold = request.param
     w = scenes.workload("c2") if over is None else scenes.workload("c1", **over)
     c = Case(w)
-    c.prob = c.problem(precision=1)
+    c.prob = c.problem(precision=1, fold_gs=fold)
     yield c
     c.prob.close()
 

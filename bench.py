@@ -179,7 +179,7 @@ def run_ours(args, rank, world, local):
         w = scenes.workload(args.workload, iters=args.iters)
     seed = rank
     chi_true = scenes.make_scene(w, seed)
-    prob = pdf.Problem.from_workload(w, precision=args.precision)
+    prob = pdf.Problem.from_workload(w, precision=args.precision, fold_gs=args.fold)
     chi_d = torch.from_numpy(chi_true.astype(np.complex64)).cuda()
     esca_clean, _, fwd_iters = prob.forward(chi_d, tol=1e-5, max_iter=3000)
     esca = scenes.add_awgn(esca_clean.cpu().numpy().astype(np.complex128), w.noise,
@@ -307,6 +307,7 @@ def run_ours(args, rank, world, local):
             "config": {"workload": f"{w.name}: {w.nx}x{w.ny} grid, {w.side} lambda DOI, Ni={w.ni}, Nr={w.nr}, "
                                    f"K={w.kx}x{w.ky}, {w.iters} Adam iterations, BP+CSI init, CCO",
                        "iters": w.iters, "lr": args.lr, "precision": args.precision, "loop": args.loop,
+                       "fold_gs": args.fold,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed between reconstructions (512 MB write); working set L2-resident within one"},
             "iters_per_s": w.iters * args.steps * world / (total_ms * 1e-3),
@@ -387,8 +388,8 @@ def run_warm(args):
     from paper_2602_13805_gb300 import pdf
     from paper_2602_13805_gb300.warmstart import WarmStartMLP, generate, predict_alpha, train
     w = scenes.workload(args.workload)
-    prob = pdf.Problem.from_workload(w)
-    chosen = pdf.Problem.from_workload(w, precision=args.precision)
+    prob = pdf.Problem.from_workload(w, fold_gs=args.fold)
+    chosen = pdf.Problem.from_workload(w, precision=args.precision, fold_gs=args.fold)
     t0 = time.perf_counter()
     train_set = generate(prob, w, args.train_scenes, seed0=1000)
     test_set = generate(prob, w, args.test_scenes, seed0=0)
@@ -484,6 +485,8 @@ def main():
     ap.add_argument("--loop", type=int, default=3, choices=[0, 1, 2, 3],
                     help="0 eager launches, 1 CUDA graph, 2 persistent cooperative kernel, "
                          "3 cluster kernel (default; the graph where the problem does not qualify)")
+    ap.add_argument("--fold", type=int, default=1, choices=[0, 1],
+                    help="1 data term through the folded operator G_S Phi (default), 0 G_S applied to J")
     ap.add_argument("--train-scenes", type=int, default=20000)
     ap.add_argument("--test-scenes", type=int, default=10)
     ap.add_argument("--train-steps", type=int, default=3000)

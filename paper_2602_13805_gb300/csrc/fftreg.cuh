@@ -110,33 +110,55 @@ template <int P> struct WarpFFT {
   static constexpr int R = P / 32;
 
   // natural order in (v[m] = x[lane + 32 m]) -> digit-reversed out (v[k1] = X[k1 + R brev5(lane)])
+  // Each butterfly is branch-free: the upper lane of a pair computes (p - v) w, the lower one
+  // (v + p) 1, i.e. (s v + p) w' with s = -1 / +1 and w' = w / 1 per lane; the last stage has w = 1.
   static __device__ __forceinline__ void forward(float2 (&v)[R], const float2* __restrict__ tw, int lane) {
     SmallDFT<R, false>::run(v);
 #pragma unroll
     for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], tw[lane * k1]);
 #pragma unroll
     for (int h = 16; h >= 1; h >>= 1) {
-      const float2 w = tw[(lane & (h - 1)) * (16 / h) * R];
       const bool hi = lane & h;
+      const float s = hi ? -1.f : 1.f;
+      if (h > 1) {
+        const float2 wt = tw[(lane & (h - 1)) * (16 / h) * R];
+        const float2 w = hi ? wt : make_float2(1.f, 0.f);
 #pragma unroll
-      for (int k = 0; k < R; ++k) {
-        const float2 p = shfl_xor2(v[k], h);
-        v[k] = hi ? cmul(p - v[k], w) : v[k] + p;
+        for (int k = 0; k < R; ++k) {
+          const float2 p = shfl_xor2(v[k], h);
+          v[k] = cmul(make_float2(fmaf(s, v[k].x, p.x), fmaf(s, v[k].y, p.y)), w);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+          const float2 p = shfl_xor2(v[k], h);
+          v[k] = make_float2(fmaf(s, v[k].x, p.x), fmaf(s, v[k].y, p.y));
+        }
       }
     }
   }
 
-  // digit-reversed in -> natural order out, unnormalised inverse
+  // digit-reversed in -> natural order out, unnormalised inverse (same branch-free butterflies)
   static __device__ __forceinline__ void inverse(float2 (&v)[R], const float2* __restrict__ tw, int lane) {
 #pragma unroll
     for (int h = 1; h <= 16; h <<= 1) {
-      const float2 w = cconj(tw[(lane & (h - 1)) * (16 / h) * R]);
       const bool hi = lane & h;
+      const float s = hi ? -1.f : 1.f;
+      if (h > 1) {
+        const float2 wt = cconj(tw[(lane & (h - 1)) * (16 / h) * R]);
+        const float2 w = hi ? wt : make_float2(1.f, 0.f);
 #pragma unroll
-      for (int k = 0; k < R; ++k) {
-        const float2 t = hi ? cmul(v[k], w) : v[k];
-        const float2 p = shfl_xor2(t, h);
-        v[k] = hi ? p - t : t + p;
+        for (int k = 0; k < R; ++k) {
+          const float2 t = cmul(v[k], w);
+          const float2 p = shfl_xor2(t, h);
+          v[k] = make_float2(fmaf(s, t.x, p.x), fmaf(s, t.y, p.y));
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+          const float2 p = shfl_xor2(v[k], h);
+          v[k] = make_float2(fmaf(s, v[k].x, p.x), fmaf(s, v[k].y, p.y));
+        }
       }
     }
 #pragma unroll

@@ -60,14 +60,14 @@ __device__ __forceinline__ void ph_synth_rowfft(const Dev& d, int bx, int by, fl
 #pragma unroll
     for (int m = 0; m < R; ++m) {
       const int x = lane + 32 * m;
-      if (x < d.nx) v[m] = v[m] + cmul(T, __ldg(&d.wx[jx * d.nx + x]));
+      if (2 * m < R && x < d.nx) v[m] = v[m] + cmul(T, __ldg(&d.wx[jx * d.nx + x]));
     }
   }
   const size_t row = (size_t)p * d.ny + y;
 #pragma unroll
   for (int m = 0; m < R; ++m) {
     const int x = lane + 32 * m;
-    if (x < d.nx) Jout[row * d.nx + x] = v[m];
+    if (2 * m < R && x < d.nx) Jout[row * d.nx + x] = v[m];
   }
   if (!do_fft) return;
   WarpFFT<PX>::forward(v, tw, lane);
@@ -90,7 +90,7 @@ __device__ __forceinline__ void ph_rowfft_field(const Dev& d, int bx, int by, fl
 #pragma unroll
   for (int m = 0; m < R; ++m) {
     const int x = lane + 32 * m;
-    v[m] = x < d.nx ? in[row * d.nx + x] : make_float2(0.f, 0.f);
+    v[m] = (2 * m < R && x < d.nx) ? in[row * d.nx + x] : make_float2(0.f, 0.f);
   }
   WarpFFT<PX>::forward(v, tw, lane);
 #pragma unroll
@@ -115,7 +115,7 @@ __device__ __forceinline__ void ph_rowifft_field(const Dev& d, int bx, int by, f
 #pragma unroll
   for (int m = 0; m < R; ++m) {
     const int x = lane + 32 * m;
-    if (x < d.nx) out[row * d.nx + x] = v[m];
+    if (2 * m < R && x < d.nx) out[row * d.nx + x] = v[m];
   }
 }
 
@@ -141,7 +141,7 @@ __device__ __forceinline__ void ph_colconv(const Dev& d, int bx, int by, float2*
 #pragma unroll
     for (int m = 0; m < R; ++m) {
       const int y = lane + 32 * m;
-      v[m] = y < d.ny ? tile[c * LS + y] : make_float2(0.f, 0.f);
+      v[m] = (2 * m < R && y < d.ny) ? tile[c * LS + y] : make_float2(0.f, 0.f);
     }
     WarpFFT<PY>::forward(v, tw, lane);
     const float2* g = d.ghat_perm + (size_t)cx * PY;
@@ -155,7 +155,7 @@ __device__ __forceinline__ void ph_colconv(const Dev& d, int bx, int by, float2*
 #pragma unroll
     for (int m = 0; m < R; ++m) {
       const int y = lane + 32 * m;
-      if (y < d.ny) tile[c * LS + y] = v[m];
+      if (2 * m < R && y < d.ny) tile[c * LS + y] = v[m];
     }
   }
   __syncthreads();
@@ -195,7 +195,7 @@ __device__ __forceinline__ void ph_rowifft_state(const Dev& d, int bx, float2* s
 #pragma unroll
     for (int m = 0; m < R; ++m) {
       const int x = lane + 32 * m;
-      if (x < d.nx) {
+      if (2 * m < R && x < d.nx) {
         const size_t idx = row * d.nx + x;
         const float2 J = d.J[idx];
         const float2 s = cmul(d.beta, J) + d.einc[idx] + v[m];
@@ -208,7 +208,7 @@ __device__ __forceinline__ void ph_rowifft_state(const Dev& d, int bx, float2* s
     }
   }
 #pragma unroll
-  for (int m = 0; m < R; ++m) {
+  for (int m = 0; m < R / 2; ++m) {                    // slots m >= R/2 are padding (P >= 2 nx)
     const int x = lane + 32 * m;
     part[(0 * FW + warp) * PX + x] = nr[m].s - nr[m].c;
     part[(1 * FW + warp) * PX + x] = ni[m].s - ni[m].c;
@@ -266,7 +266,7 @@ __device__ __forceinline__ void ph_adj_rowfft(const Dev& d, int bx, int by, floa
   for (int m = 0; m < R; ++m) {
     const int x = lane + 32 * m;
     v[m] = make_float2(0.f, 0.f);
-    if (x < d.nx) {
+    if (2 * m < R && x < d.nx) {
       const int n = y * d.nx + x;
       const size_t idx = row * d.nx + x;
       const float2 w = d.w[n], Rr = d.R[n];
@@ -303,7 +303,7 @@ __device__ __forceinline__ void ph_adj_rowifft_ana(const Dev& d, int bx, int by,
 #pragma unroll
       for (int m = 0; m < R; ++m) {
         const int x = lane + 32 * m;
-        if (x < d.nx) {
+        if (2 * m < R && x < d.nx) {
           const size_t idx = row * d.nx + x;
           g[m] = d.fold ? g[m] + d.v[idx] : g[m] + d.v[idx] + d.gsh[idx];
         } else {
@@ -314,7 +314,7 @@ __device__ __forceinline__ void ph_adj_rowifft_ana(const Dev& d, int bx, int by,
 #pragma unroll
       for (int m = 0; m < R; ++m) {
         const int x = lane + 32 * m;
-        g[m] = x < d.nx ? in[row * d.nx + x] : make_float2(0.f, 0.f);
+        g[m] = (2 * m < R && x < d.nx) ? in[row * d.nx + x] : make_float2(0.f, 0.f);
       }
     }
     // analysis along x: T2[p][y][jx] = sum_x g[x] conj(Wx[jx][x]), 16 coefficients per warp
@@ -325,9 +325,9 @@ __device__ __forceinline__ void ph_adj_rowifft_ana(const Dev& d, int bx, int by,
       for (int j = 0; j < 16; ++j) acc[j] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int m = 0; m < R; ++m) {
-        if (32 * m >= d.nx) break;               // warp-uniform: the remaining slots are padding
+        if (2 * m >= R || 32 * m >= d.nx) break;  // slots m >= R/2 are padding (P >= 2 nx)
         const int x = lane + 32 * m;
-        if (x < d.nx) {
+        if (2 * m < R && x < d.nx) {
 #pragma unroll
           for (int j = 0; j < 16; ++j)
             if (j0 + j < d.kx) acc[j] = acc[j] + cmulc(g[m], __ldg(&d.wx[(size_t)(j0 + j) * d.nx + x]));

@@ -217,7 +217,8 @@ pdf_status pdf_gs_apply_static(const void* gs, const void* x, void* out, int32_t
  * --------------------------------------------------------------------------------------------- */
 typedef struct pdf_mlp pdf_mlp;
 
-/* nlayers linear layers, sizes[0..nlayers] the widths; batch_max <= 4096.  Weights start at 0:
+/* nlayers (1..8) linear layers, sizes[0..nlayers] the widths (1..2^20, each weight matrix and each
+ * batch_max x width activation below 2^31 elements); batch_max <= 4096.  Weights start at 0:
  * set them with pdf_mlp_set_params.  PDF_EINVAL on bad sizes, PDF_ENOMEM. */
 pdf_status pdf_mlp_create(int32_t nlayers, const int32_t* sizes, int32_t batch_max, pdf_mlp** out);
 void pdf_mlp_destroy(pdf_mlp* m);

@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(FT) kf_rowifft_field(Dev d, float2* out) {
   ph_rowifft_field<PX>(d, blockIdx.x, blockIdx.y, sm, out);
 }
 template <int PY>
-__global__ void __launch_bounds__(FT, 2) kf_colconv(Dev d, int conj) {
+__global__ void __launch_bounds__(FT, (PY <= 384 ? 3 : 2)) kf_colconv(Dev d, int conj) {
   extern __shared__ float2 sm[];
   ph_colconv<PY>(d, blockIdx.x, blockIdx.y, sm, conj);
 }
@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(FT) kf_adj_rowfft(Dev d) {
   ph_adj_rowfft<PX>(d, blockIdx.x, blockIdx.y, sm);
 }
 template <int PX>
-__global__ void __launch_bounds__(FT) kf_adj_rowifft_ana(Dev d, const float2* in, int mode) {
+__global__ void __launch_bounds__(FT, (PX <= 384 ? 3 : 2)) kf_adj_rowifft_ana(Dev d, const float2* in, int mode) {
   extern __shared__ float2 sm[];
   ph_adj_rowifft_ana<PX>(d, blockIdx.x, blockIdx.y, sm, in, mode);
 }

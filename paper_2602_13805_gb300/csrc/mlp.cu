@@ -175,8 +175,12 @@ extern "C" pdf_status pdf_mlp_create(int32_t nlayers, const int32_t* sizes, int3
   *out = nullptr;
   if (nlayers < 1 || nlayers > MLP_MAX_LAYERS) return set_err(PDF_EINVAL, "pdf_mlp_create: 1..8 layers");
   if (batch_max < 1 || batch_max > 4096) return set_err(PDF_EINVAL, "pdf_mlp_create: batch in [1, 4096]");
-  for (int l = 0; l <= nlayers; ++l)
-    if (sizes[l] < 1 || sizes[l] > 65536) return set_err(PDF_EINVAL, "pdf_mlp_create: layer sizes in [1, 65536]");
+  for (int l = 0; l <= nlayers; ++l) {
+    if (sizes[l] < 1 || sizes[l] > (1 << 20)) return set_err(PDF_EINVAL, "pdf_mlp_create: layer sizes in [1, 2^20]");
+    if ((size_t)batch_max * sizes[l] >= ((size_t)1 << 31) ||
+        (l < nlayers && (size_t)sizes[l] * sizes[l + 1] >= ((size_t)1 << 31)))
+      return set_err(PDF_EINVAL, "pdf_mlp_create: a weight matrix or activation exceeds 2^31 elements");
+  }
   pdf_mlp* m = new pdf_mlp();
   m->nl = nlayers;
   m->bmax = batch_max;

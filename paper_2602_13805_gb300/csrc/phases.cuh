@@ -54,6 +54,7 @@ __device__ __forceinline__ void ph_synth_rowfft(const Dev& d, int bx, int by, fl
   float2 v[R];
 #pragma unroll
   for (int m = 0; m < R; ++m) v[m] = make_float2(0.f, 0.f);
+#pragma unroll 4
   for (int jx = 0; jx < d.kx; ++jx) {
     const float2 src = jx < 32 ? t0 : t1;
     const float2 T = make_float2(__shfl_sync(0xffffffffu, src.x, jx & 31), __shfl_sync(0xffffffffu, src.y, jx & 31));

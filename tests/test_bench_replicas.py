@@ -1,0 +1,64 @@
+"""The N > 1 path of bench.py on CPU: world_size-2 gloo ranks, replicas only.
+
+Each rank times its own reconstructions; the job time is the slowest rank's (all-reduce MAX) and
+the whole-job figure is per reconstruction over all ranks.  The reference arm runs on rank 0 only.
+"""
+import os
+import socket
+import types
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+import bench  # noqa: E402
+
+
+def _free_port():
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        assert bench.dist_env() == (rank, world, rank)
+        # rank r timed 5 reconstructions in 100 + 50 r ms, end to end 120 + 10 r ms per step
+        res = bench.combine_ranks(100.0 + 50.0 * rank, 120.0 + 10.0 * rank, 5, world, "cpu")
+        args = types.SimpleNamespace(workload="c1", cpu_iters=1, warmup=0, steps=1)
+        ref = bench.run_reference(args, rank, world) if rank != 0 else "skipped"
+        out.put((rank, res, ref))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_replicas_take_the_slowest_rank():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = {}
+    for _ in range(world):
+        rank, res, ref = q.get(timeout=120)
+        got[rank] = (res, ref)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank in range(world):
+        per_recon, e2e, total = got[rank][0]
+        assert total == 150.0                       # slowest rank
+        assert per_recon == 150.0 / (5 * world)     # whole-job throughput
+        assert e2e == 130.0 / world
+    assert got[1][1] is None                        # reference arm: rank 0 only, others do no work
+
+
+def test_single_rank_needs_no_collective():
+    per_recon, e2e, total = bench.combine_ranks(80.0, 90.0, 4, 1, "cpu")
+    assert (per_recon, e2e, total) == (20.0, 90.0, 80.0)

@@ -3,6 +3,7 @@
 #include <algorithm>
 
 #include "fft.cuh"
+#include "phases.cuh"
 #include "problem.cuh"
 #include "tc.cuh"
 
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_tc_synth_post(Dev d, TC t, floa
       const int y = y0 + rr;
       v = cs[(size_t)y * ncs + p * d.nx + x];
       Jout[((size_t)p * d.ny + y) * d.nx + x] = v;
-      put_jb(t, p, y * d.nx + x, v);
+      if (!d.fold) put_jb(t, p, y * d.nx + x, v);       // G_S GEMM operand (unfolded data term)
     }
     b0[i] = v;
   }
@@ -103,6 +104,35 @@ __global__ void __launch_bounds__(ROW_THREADS) k_tc_synth_post(Dev d, TC t, floa
     const int rr = i / d.Px, x = i - rr * d.Px;
     if (rr < nrow) d.A[((size_t)p * d.ny + y0 + rr) * d.Px + x] = res[i];
   }
+}
+
+// Register-FFT form of the synthesis epilogue: one warp per row of C_syn -> J (and JB when the
+// data term is unfolded), then the padded row DFT straight into A (no J round trip).
+template <int PX>
+__global__ void __launch_bounds__(FT) k_tc_synth_post_fast(Dev d, TC t, float2* __restrict__ Jout) {
+  constexpr int R = PX / 32;
+  __shared__ float2 tw[PX];
+  const int p = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int y = blockIdx.x * FW + warp;
+  load_tw<PX>(tw, d.twx);
+  __syncthreads();
+  if (y >= d.ny) return;
+  const float2* cs = (const float2*)t.c_syn + (size_t)y * d.ni * d.nx + (size_t)p * d.nx;
+  const size_t row = (size_t)p * d.ny + y;
+  float2 v[R];
+#pragma unroll
+  for (int m = 0; m < R; ++m) {
+    const int x = lane + 32 * m;
+    v[m] = make_float2(0.f, 0.f);
+    if (2 * m < R && x < d.nx) {                       // slots m >= R/2 are padding (P >= 2 nx)
+      v[m] = cs[x];
+      Jout[row * d.nx + x] = v[m];
+      if (!d.fold) put_jb(t, p, y * d.nx + x, v[m]);
+    }
+  }
+  WarpFFT<PX>::forward(v, tw, lane);
+#pragma unroll
+  for (int k = 0; k < R; ++k) d.A[row * PX + k * 32 + lane] = v[k];
 }
 
 __global__ void k_tc_field_to_jb(Dev d, TC t, const float2* __restrict__ X) {
@@ -209,6 +239,39 @@ __global__ void k_tc_gja_combine(Dev d, TC t, const float2* __restrict__ gdh) {
   put_gja(t, p * d.ny + y, x, d.fold ? gdh[i] + d.v[i] : gdh[i] + d.v[i] + make_float2(ks * c[0], ks * c[1]));
 }
 
+// Register-FFT form of the adjoint packing: inverse row DFT of A (G_D^H u) + v (+ the G_S^H
+// term when unfolded), packed straight into the analysis GEMM's A operand.
+template <int PX>
+__global__ void __launch_bounds__(FT) k_tc_adj_fast(Dev d, TC t) {
+  constexpr int R = PX / 32;
+  __shared__ float2 tw[PX];
+  const int p = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int y = blockIdx.x * FW + warp;
+  load_tw<PX>(tw, d.twx);
+  __syncthreads();
+  if (y >= d.ny) return;
+  const size_t row = (size_t)p * d.ny + y;
+  const float ks = d.invn[1];
+  float2 v[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) v[k] = d.A[row * PX + k * 32 + lane];
+  WarpFFT<PX>::inverse(v, tw, lane);
+#pragma unroll
+  for (int m = 0; m < R; ++m) {
+    const int x = lane + 32 * m;
+    if (2 * m < R && x < d.nx) {
+      const int n = y * d.nx + x;
+      const size_t idx = row * d.nx + x;
+      float2 g = v[m] + d.v[idx];
+      if (!d.fold) {
+        const float* c = t.c_adj + (size_t)n * 2 * d.ni + 2 * p;
+        g = g + make_float2(ks * c[0], ks * c[1]);
+      }
+      put_gja(t, p * d.ny + y, x, g);
+    }
+  }
+}
+
 __global__ void k_tc_field_to_gja(Dev d, TC t, const float2* __restrict__ X) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)d.ni * d.M) return;
@@ -306,16 +369,24 @@ pdf_status tc_synth(pdf_problem* h, const float2* alpha, float2* Jout, int do_ff
   pdf_count_launch(1);
   pdf_status s = umma_gemm(t.wya, t.tb, 1, 1, t.c_syn, 2 * d.ni * d.nx, 0, t.err, st);
   if (s != PDF_OK) return s;
-  const int gen_fft = do_fft && !d.fast;
+  if (do_fft && d.fast) {
+    const dim3 g((d.ny + FW - 1) / FW, d.ni);
+    switch (d.Px) {
+      case 64: k_tc_synth_post_fast<64><<<g, FT, 0, st>>>(d, t, Jout); break;
+      case 128: k_tc_synth_post_fast<128><<<g, FT, 0, st>>>(d, t, Jout); break;
+      case 256: k_tc_synth_post_fast<256><<<g, FT, 0, st>>>(d, t, Jout); break;
+      case 384: k_tc_synth_post_fast<384><<<g, FT, 0, st>>>(d, t, Jout); break;
+      case 512: k_tc_synth_post_fast<512><<<g, FT, 0, st>>>(d, t, Jout); break;
+      default: return set_err(PDF_EUNSUPPORTED, "register FFT length");
+    }
+    pdf_count_launch(1);
+    PDF_LAUNCHED("tensor-core synthesis epilogue + row DFT");
+    return PDF_OK;
+  }
   k_tc_synth_post<<<dim3((d.ny + ROWS_PER_CTA - 1) / ROWS_PER_CTA, d.ni), ROW_THREADS, sm_row_tc(d), st>>>(
-      d, t, Jout, gen_fft);
+      d, t, Jout, do_fft);
   pdf_count_launch(1);
   PDF_LAUNCHED("tensor-core synthesis");
-  if (do_fft && d.fast) {
-    pdf_status q = fp_rowfft_field(d, Jout, st);
-    pdf_count_launch(1);
-    if (q != PDF_OK) return q;
-  }
   return PDF_OK;
 }
 
@@ -359,11 +430,17 @@ pdf_status tc_adj_ana(pdf_problem* h, cudaStream_t st) {
   Dev& d = h->d;
   TC& t = *h->tc;
   if (d.fast) {
-    pdf_status q = fp_rowifft_field(d, h->tmpA, st);
-    if (q != PDF_OK) return q;
-    k_tc_gja_combine<<<(unsigned)(((size_t)d.ni * d.M + 255) / 256), 256, 0, st>>>(d, t, h->tmpA);
-    pdf_count_launch(2);
-    PDF_LAUNCHED("tensor-core adjoint combine");
+    const dim3 g((d.ny + FW - 1) / FW, d.ni);
+    switch (d.Px) {
+      case 64: k_tc_adj_fast<64><<<g, FT, 0, st>>>(d, t); break;
+      case 128: k_tc_adj_fast<128><<<g, FT, 0, st>>>(d, t); break;
+      case 256: k_tc_adj_fast<256><<<g, FT, 0, st>>>(d, t); break;
+      case 384: k_tc_adj_fast<384><<<g, FT, 0, st>>>(d, t); break;
+      case 512: k_tc_adj_fast<512><<<g, FT, 0, st>>>(d, t); break;
+      default: return set_err(PDF_EUNSUPPORTED, "register FFT length");
+    }
+    pdf_count_launch(1);
+    PDF_LAUNCHED("tensor-core adjoint row IFFT + packing");
     return umma_gemm(t.gja, t.wxb, 1, 1, t.c_ana, 2 * d.kx, 0, t.err, st);
   }
   k_tc_adj_rowifft<<<dim3((d.ny + ROWS_PER_CTA - 1) / ROWS_PER_CTA, d.ni), ROW_THREADS, sm_row_tc(d), st>>>(d, t);

@@ -428,6 +428,20 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
   TRY(dalloc(h, &d.A, NI * d.ny * (size_t)d.Px));
   TRY(dalloc(h, &d.s, NI * M));
   TRY(dalloc(h, &d.r, NI * M));
+  d.nsg = 0;
+  d.sgA = nullptr;
+  d.sgB = nullptr;
+  if (d.fast) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaGetLastError();
+    d.nsg = fp_choose_nsg(d, sms > 0 ? sms : 152);
+    if (d.nsg > 0) {
+      TRY(dalloc(h, &d.sgA, (size_t)d.nsg * M));
+      TRY(dalloc(h, &d.sgB, (size_t)d.nsg * M));
+    }
+  }
   TRY(dalloc(h, &d.v, NI * M));
   TRY(dalloc(h, &d.gsh, NI * M));
   TRY(dalloc(h, &d.R, M));

@@ -3,6 +3,8 @@
 // warp FFT's digit-reversed order, columns are processed in that order too, and the G_D
 // spectrum is stored pre-permuted ([Px][Py], column-major), so no data are ever reordered.
 // Kernel roles and fused epilogues are those of hotpath.cu (same Eq. references).
+#include <algorithm>
+
 #include "phases.cuh"
 
 template <int PX>
@@ -30,10 +32,18 @@ __global__ void __launch_bounds__(FT) kf_rowifft_state(Dev d) {
   extern __shared__ float2 sm[];
   ph_rowifft_state<PX>(d, blockIdx.x, sm);
 }
-template <int PX>
+template <int PX, bool FUSED_R>
 __global__ void __launch_bounds__(FT) kf_adj_rowfft(Dev d) {
   __shared__ float2 sm[PX];
-  ph_adj_rowfft<PX>(d, blockIdx.x, blockIdx.y, sm);
+  ph_adj_rowfft<PX, FUSED_R>(d, blockIdx.x, blockIdx.y, sm);
+}
+template <int PX>
+__global__ void __launch_bounds__(FT) kf_rowifft_sums(Dev d) {
+  extern __shared__ float2 sm[];
+  ph_rowifft_sums<PX>(d, blockIdx.x, blockIdx.y, sm);
+}
+__global__ void __launch_bounds__(128) k_state_combine(Dev d) {
+  ph_state_combine(d, blockIdx.x * blockDim.x + threadIdx.x);
 }
 template <int PX>
 __global__ void __launch_bounds__(FT, (PX <= 384 ? 3 : 2)) kf_adj_rowifft_ana(Dev d, const float2* in, int mode) {
@@ -61,7 +71,8 @@ pdf_status fp_configure() {
   cudaFuncSetAttribute(kf_synth_rowfft<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);  \
   cudaFuncSetAttribute(kf_colconv<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);       \
   cudaFuncSetAttribute(kf_rowifft_state<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024); \
-  cudaFuncSetAttribute(kf_adj_rowifft_ana<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  cudaFuncSetAttribute(kf_adj_rowifft_ana<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024); \
+  cudaFuncSetAttribute(kf_rowifft_sums<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
   CFG(64) CFG(128) CFG(256) CFG(384) CFG(512)
 #undef CFG
   cudaError_t e = cudaGetLastError();
@@ -73,6 +84,7 @@ size_t fp_smem_synth(const Dev& d) { return ((size_t)d.Px + (size_t)d.ky * d.kx)
 size_t fp_smem_col(const Dev& d) { return ((size_t)d.Py + (size_t)FCOLS * (d.ny + 1)) * sizeof(float2); }
 size_t fp_smem_state(const Dev& d) { return (size_t)d.Px * sizeof(float2) * 2 + 3 * FW * (size_t)d.Px * sizeof(float); }
 size_t fp_smem_ana(const Dev& d) { return (size_t)d.Px * sizeof(float2); }
+size_t fp_smem_sums(const Dev& d) { return (size_t)d.Px * sizeof(float2) + 3 * FW * (size_t)(d.Px / 2) * sizeof(float); }
 
 pdf_status fp_synth_rowfft(const Dev& d, const float2* alpha, float2* Jout, int do_fft, cudaStream_t st) {
 #define L(P) kf_synth_rowfft<P><<<frow_grid(d), FT, fp_smem_synth(d), st>>>(d, alpha, Jout, do_fft)
@@ -98,18 +110,47 @@ pdf_status fp_colconv(const Dev& d, int conj, cudaStream_t st) {
 #undef L
   return PDF_OK;
 }
+// State pass: split over incidence groups (d.nsg > 0: row IFFT + group sums, then a per-pixel
+// combine; r and L_State come with the adjoint row DFT) or one CTA per row over all incidences.
 pdf_status fp_rowifft_state(const Dev& d, cudaStream_t st) {
+  if (d.nsg > 0) {
+#define L(P) kf_rowifft_sums<P><<<dim3(d.ny, d.nsg), FT, fp_smem_sums(d), st>>>(d)
+    FAST_SWITCH(d.Px, L)
+#undef L
+    k_state_combine<<<(d.M + 127) / 128, 128, 0, st>>>(d);
+    pdf_count_launch(1);
+    return PDF_OK;
+  }
 #define L(P) kf_rowifft_state<P><<<d.ny, FT, fp_smem_state(d), st>>>(d)
   FAST_SWITCH(d.Px, L)
 #undef L
   return PDF_OK;
 }
 pdf_status fp_adj_rowfft(const Dev& d, cudaStream_t st) {
-#define L(P) kf_adj_rowfft<P><<<frow_grid(d), FT, 0, st>>>(d)
+  if (d.nsg > 0) {
+#define L(P) kf_adj_rowfft<P, true><<<frow_grid(d), FT, 0, st>>>(d)
+    FAST_SWITCH(d.Px, L)
+#undef L
+    return PDF_OK;
+  }
+#define L(P) kf_adj_rowfft<P, false><<<frow_grid(d), FT, 0, st>>>(d)
   FAST_SWITCH(d.Px, L)
 #undef L
   return PDF_OK;
 }
+
+// Incidence groups of the split state pass: FW incidences per group (one per warp), as long as
+// the adjoint's L_State partials (one per CTA) fit the partial strip; 0 keeps the
+// one-CTA-per-row pass.
+int fp_choose_nsg(const Dev& d, int sms) {
+  (void)sms;
+  const dim3 g = frow_grid(d);
+  if ((size_t)g.x * g.y > PDF_LP_STRIDE) return 0;
+  return (d.ni + FW - 1) / FW;
+}
+
+// number of L_State partials written per loss-and-gradient evaluation on this path
+int fp_n_state(const Dev& d) { return d.nsg > 0 ? (int)(frow_grid(d).x * frow_grid(d).y) : d.ny; }
 pdf_status fp_adj_rowifft_ana(const Dev& d, const float2* in, int mode, cudaStream_t st) {
 #define L(P) kf_adj_rowifft_ana<P><<<frow_grid(d), FT, fp_smem_ana(d), st>>>(d, in, mode)
   FAST_SWITCH(d.Px, L)

@@ -496,7 +496,7 @@ int hp_kernels_per_loss_grad(const pdf_problem* h) { return (h->tc || h->d.fold)
 pdf_status hp_check_limits(const Dev& d) {
   const size_t lim = 200 * 1024;
   if (d.fast && (fp_smem_synth(d) > 100 * 1024 || fp_smem_col(d) > 100 * 1024 || fp_smem_state(d) > 100 * 1024 ||
-                 fp_smem_ana(d) > 100 * 1024))
+                 fp_smem_ana(d) > 100 * 1024 || fp_smem_sums(d) > 100 * 1024))
     return set_err(PDF_EUNSUPPORTED, "problem too large for the register-FFT tiling");
   if (sm_row(d) > lim || sm_synth(d) > lim || sm_col(d) > lim || sm_gs(d) > lim || sm_gsh(d) > lim)
     return set_err(PDF_EUNSUPPORTED, "problem too large for the shared-memory tiling (reduce ni, nr or kx*ky)");
@@ -618,7 +618,8 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
     k_gsf_adj<<<dim3((d.ky * d.kx + 31) / 32, d.ni), 256, 0, st>>>(d, d.rd, g);
     mark();
   }
-  k_finalize<<<1, 256, 0, st>>>(d, terms ? terms : h->terms, d.ny, n_data_blocks, d.n_reg_blocks, step_inc);
+  k_finalize<<<1, 256, 0, st>>>(d, terms ? terms : h->terms, d.fast ? fp_n_state(d) : d.ny, n_data_blocks,
+                                d.n_reg_blocks, step_inc);
   mark();
   pdf_count_launch(d.fold ? (tc ? 9 : 11) : (tc ? 7 : 12));
   PDF_LAUNCHED("pdf_loss_grad");

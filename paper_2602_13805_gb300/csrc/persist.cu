@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(FT) k_persist(Dev d, PersistArgs a) {
     PDF_BARRIER();
     // adjoint
     for (int vb = b0; vb < nrow + n_gsh; vb += G) {
-      if (vb < nrow) ph_adj_rowfft<P>(d, vb % rgx, vb / rgx, sm);
+      if (vb < nrow) ph_adj_rowfft<P, false>(d, vb % rgx, vb / rgx, sm);
       else ph_gsh(d, vb - nrow, sm, d.rd, d.gsh, 0.f, 1);
       __syncthreads();
     }

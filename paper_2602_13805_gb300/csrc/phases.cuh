@@ -250,38 +250,130 @@ __device__ __forceinline__ void ph_rowifft_state(const Dev& d, int bx, float2* s
 }
 
 
+// Split state pass, part 1 (block = row y, incidence group g of at most FW incidences, one per
+// warp): inverse row DFT -> G_D J, s = beta J + E_inc + G_D J (Eq. 6), and the group's per-pixel
+// float-float sums of beta J conj(s) and |s|^2.
 template <int PX>
+__device__ __forceinline__ void ph_rowifft_sums(const Dev& d, int y, int g, float2* sm) {
+  constexpr int R = PX / 32, H = PX / 2;
+  float2* tw = sm;
+  float* part = (float*)(sm + PX);             // [3][FW][PX / 2]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  load_tw<PX>(tw, d.twx);
+  __syncthreads();
+  const int p = g * FW + warp;
+  if (p < d.ni) {
+    const size_t row = (size_t)p * d.ny + y;
+    float2 v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = d.A[row * PX + k * 32 + lane];
+    WarpFFT<PX>::inverse(v, tw, lane);
+#pragma unroll
+    for (int m = 0; m < R / 2; ++m) {                  // slots m >= R/2 are padding (P >= 2 nx)
+      const int x = lane + 32 * m;
+      float3 c = make_float3(0.f, 0.f, 0.f);
+      if (x < d.nx) {
+        const size_t idx = row * d.nx + x;
+        const float2 J = d.J[idx];
+        const float2 s = cmul(d.beta, J) + d.einc[idx] + v[m];
+        d.s[idx] = s;
+        const float2 n = cmul(d.beta, cmulc(J, s));
+        c = make_float3(n.x, n.y, cabs2(s));
+      }
+      part[(0 * FW + warp) * H + x] = c.x;
+      part[(1 * FW + warp) * H + x] = c.y;
+      part[(2 * FW + warp) * H + x] = c.z;
+    }
+  } else {
+    for (int x = lane; x < H; x += 32)
+      part[(0 * FW + warp) * H + x] = part[(1 * FW + warp) * H + x] = part[(2 * FW + warp) * H + x] = 0.f;
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < d.nx; x += blockDim.x) {
+    FF a = FF{0.f, 0.f}, b = FF{0.f, 0.f}, c = FF{0.f, 0.f};
+    for (int w = 0; w < FW; ++w) {
+      a = ff_add(a, part[(0 * FW + w) * H + x]);
+      b = ff_add(b, part[(1 * FW + w) * H + x]);
+      c = ff_add(c, part[(2 * FW + w) * H + x]);
+    }
+    const size_t o = (size_t)g * d.M + (size_t)y * d.nx + x;
+    d.sgA[o] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    d.sgB[o] = make_float2(c.hi, c.lo);
+  }
+}
+
+// Split state pass, part 2 (thread per pixel): the group sums in group order -> R-hat (Eq. 6),
+// chi-hat (Eq. 7), D and the clamp flag.
+__device__ __forceinline__ void ph_state_combine(const Dev& d, int n) {
+  if (n >= d.M) return;
+  FF a = FF{0.f, 0.f}, b = FF{0.f, 0.f}, c = FF{0.f, 0.f};
+#pragma unroll 8
+  for (int g = 0; g < d.nsg; ++g) {
+    const float4 A = d.sgA[(size_t)g * d.M + n];
+    const float2 B = d.sgB[(size_t)g * d.M + n];
+    a = ff_add(a, FF{A.x, A.y});
+    b = ff_add(b, FF{A.z, A.w});
+    c = ff_add(c, FF{B.x, B.y});
+  }
+  const float cf = c.hi + c.lo;
+  const float2 Rv = make_float2((a.hi + a.lo) / cf, (b.hi + b.lo) / cf);
+  bool cl;
+  const float2 chi = chi_of_R_f(Rv, d.beta, d.q_min, &cl);
+  d.R[n] = Rv;
+  d.chi[n] = chi;
+  d.D[n] = cf;
+  d.clamp[n] = cl ? 1 : 0;
+}
+
+// Adjoint inputs and the row DFT of u.  FUSED_R: the state residual r = R-hat s - beta J (Eq. 15)
+// is formed here rather than read back, and this block's float-float sum of |r|^2 goes to the
+// L_State partials (slot by * gridDim.x + bx).
+template <int PX, bool FUSED_R>
 __device__ __forceinline__ void ph_adj_rowfft(const Dev& d, int bx, int by, float2* sm) {
   constexpr int R = PX / 32;
+  __shared__ FF red_ar[32];
   float2* tw = sm;
   const int p = by, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int y = bx * FW + warp;
   load_tw<PX>(tw, d.twx);
   __syncthreads();
-  if (y >= d.ny) return;
-  const float ke = d.invn[0];
-  const float2 bc = cconj(d.beta);
-  const size_t row = (size_t)p * d.ny + y;
-  float2 v[R];
+  KS acc;
+  if (y < d.ny) {
+    const float ke = d.invn[0];
+    const float2 bc = cconj(d.beta);
+    const size_t row = (size_t)p * d.ny + y;
+    float2 v[R];
 #pragma unroll
-  for (int m = 0; m < R; ++m) {
-    const int x = lane + 32 * m;
-    v[m] = make_float2(0.f, 0.f);
-    if (2 * m < R && x < d.nx) {
-      const int n = y * d.nx + x;
-      const size_t idx = row * d.nx + x;
-      const float2 w = d.w[n], Rr = d.R[n];
-      const float2 J = d.J[idx], s = d.s[idx], r = d.r[idx];
-      const float2 wc = cconj(w);
-      const float2 cs = cmul(cmul(wc, d.beta), J) - (2.f * cmul(wc, Rr).x) * s;
-      v[m] = ke * cmulc(r, Rr) + cs;
-      const float2 omr = make_float2(1.f - Rr.x, Rr.y);
-      d.v[idx] = ke * cmul(cmul(make_float2(-bc.x, -bc.y), omr), r) + cmul(bc, cmul(w, s) + cs);
+    for (int m = 0; m < R; ++m) {
+      const int x = lane + 32 * m;
+      v[m] = make_float2(0.f, 0.f);
+      if (2 * m < R && x < d.nx) {
+        const int n = y * d.nx + x;
+        const size_t idx = row * d.nx + x;
+        const float2 w = d.w[n], Rr = d.R[n];
+        const float2 J = d.J[idx], s = d.s[idx];
+        float2 r;
+        if (FUSED_R) {
+          r = cmul(Rr, s) - cmul(d.beta, J);
+          acc.add(cabs2(r));
+        } else {
+          r = d.r[idx];
+        }
+        const float2 wc = cconj(w);
+        const float2 cs = cmul(cmul(wc, d.beta), J) - (2.f * cmul(wc, Rr).x) * s;
+        v[m] = ke * cmulc(r, Rr) + cs;
+        const float2 omr = make_float2(1.f - Rr.x, Rr.y);
+        d.v[idx] = ke * cmul(cmul(make_float2(-bc.x, -bc.y), omr), r) + cmul(bc, cmul(w, s) + cs);
+      }
     }
-  }
-  WarpFFT<PX>::forward(v, tw, lane);
+    WarpFFT<PX>::forward(v, tw, lane);
 #pragma unroll
-  for (int k = 0; k < R; ++k) d.A[row * PX + k * 32 + lane] = v[k];
+    for (int k = 0; k < R; ++k) d.A[row * PX + k * 32 + lane] = v[k];
+  }
+  if (FUSED_R) {
+    const FF t = ff_block_sum(ff_add(FF{acc.s, 0.f}, -acc.c), red_ar);
+    if (threadIdx.x == 0) d.lpart[LP_STATE * PDF_LP_STRIDE + by * gridDim.x + bx] = t;
+  }
 }
 
 

@@ -46,6 +46,9 @@ struct Dev {
   float2* A;             // [ni][ny][Px] row-transformed padded planes
   float2* s;             // [ni][M] beta J + E_inc + G_D J
   float2* r;             // [ni][M] state residual
+  int nsg;               // > 0: state pass split over nsg incidence groups (register-FFT path)
+  float4* sgA;           // [nsg][M] per-group float-float sums of beta J conj(s) (re hi, re lo, im hi, im lo)
+  float2* sgB;           // [nsg][M] per-group float-float sums of |s|^2
   float2* v;             // [ni][M] pointwise part of dL/dJ
   float2* gsh;           // [ni][M] scaled G_S^H r_d
   float2* R;             // [M]
@@ -156,6 +159,9 @@ size_t fp_smem_synth(const Dev& d);
 size_t fp_smem_col(const Dev& d);
 size_t fp_smem_state(const Dev& d);
 size_t fp_smem_ana(const Dev& d);
+size_t fp_smem_sums(const Dev& d);
+int fp_n_state(const Dev& d);
+int fp_choose_nsg(const Dev& d, int sms);
 
 // persistent solve loop (persist.cu)
 pdf_status ps_run(pdf_problem* h, const pdf_solve_opts* o, int iters, unsigned* bar, int* err, cudaStream_t st,

@@ -349,65 +349,104 @@ __global__ void __launch_bounds__(256) k_ana_y(Dev d, const float2* T2, float2* 
 }
 
 // terms[6] = L, State, Data, Bound, TV, Bridge from the partial sums
-// Data residual through the folded operator (Eq. 16 with J = Phi alpha, Eq. 9):
-// r_d[p][r] = sum_j gsf[r][j] alpha[p][j] - E_sca[p][r].  Each warp takes `opw` consecutive
-// outputs o = p nr + r (8 warps per block), its lanes stride over j; the block's float-float
-// sum of |r_d|^2 goes to lp[block].
-__global__ void __launch_bounds__(256) k_gsf_fwd(Dev d, const float2* __restrict__ alpha,
-                                                 const float2* __restrict__ esca, float2* __restrict__ rd, FF* lp,
-                                                 int opw) {
-  __shared__ FF red_gf[32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int NA = d.ky * d.kx, nout = d.ni * d.nr;
-  FF a2 = FF{0.f, 0.f};
-  const int o0 = (blockIdx.x * 8 + warp) * opw;
-  for (int o = o0; o < min(o0 + opw, nout); ++o) {
-    const int p = o / d.nr, r = o - p * d.nr;
-    const float2* g = d.gsf + (size_t)r * NA;
-    const float2* al = alpha + (size_t)p * NA;
-    float2 acc = make_float2(0.f, 0.f);
-#pragma unroll 4
-    for (int j = lane; j < NA; j += 32) acc = acc + cmul(__ldg(&g[j]), __ldg(&al[j]));
-#pragma unroll
-    for (int m = 16; m > 0; m >>= 1) acc = acc + shfl_xor2(acc, m);
-    if (lane == 0) {
-      const float2 v = acc - esca[o];
-      rd[o] = v;
-      a2 = ff_add(a2, cabs2(v));
+// Data residual through the folded operator (Eq. 16 with J = Phi alpha, Eq. 9) as a tiled
+// product: block (rb, pb, s) computes the partial sums over coefficients j in chunk s of
+// sum_j gsf[r][j] alpha[p][j] for 32 receivers x 8 incidences (one output per thread), staging
+// 64-coefficient slices of both operands in shared memory; k_gsf_reduce adds the chunks in order.
+__global__ void __launch_bounds__(256) k_gsf_fwd(Dev d, const float2* __restrict__ alpha, float2* __restrict__ part,
+                                                 int kc) {
+  __shared__ float2 sG[32][65];
+  __shared__ float2 sA[8][64];
+  const int NA = d.ky * d.kx;
+  const int ri = threadIdx.x & 31, pi = threadIdx.x >> 5;
+  const int r = blockIdx.x * 32 + ri, p = blockIdx.y * 8 + pi;
+  const int j0 = blockIdx.z * kc, j1 = min(j0 + kc, NA);
+  float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+  for (int c0 = j0; c0 < j1; c0 += 64) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < 32 * 64; i += 256) {
+      const int rr = i >> 6, jj = i & 63, rg = blockIdx.x * 32 + rr, jg = c0 + jj;
+      sG[rr][jj] = (rg < d.nr && jg < j1) ? __ldg(&d.gsf[(size_t)rg * NA + jg]) : make_float2(0.f, 0.f);
     }
+    for (int i = threadIdx.x; i < 8 * 64; i += 256) {
+      const int pp = i >> 6, jj = i & 63, pg = blockIdx.y * 8 + pp, jg = c0 + jj;
+      sA[pp][jj] = (pg < d.ni && jg < j1) ? __ldg(&alpha[(size_t)pg * NA + jg]) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int jj = 0; jj < 64; jj += 2) {
+      a0 = a0 + cmul(sG[ri][jj], sA[pi][jj]);
+      a1 = a1 + cmul(sG[ri][jj + 1], sA[pi][jj + 1]);
+    }
+  }
+  if (r < d.nr && p < d.ni) part[((size_t)blockIdx.z * d.ni + p) * d.nr + r] = a0 + a1;
+}
+
+// r_d[o] = sum of the nsplit chunk partials (float-float, chunk order) - E_sca[o]; per-block
+// float-float sums of |r_d|^2 to lp[block].
+__global__ void __launch_bounds__(256) k_gsf_reduce(Dev d, const float2* __restrict__ part, int nsplit,
+                                                    const float2* __restrict__ esca, float2* __restrict__ rd, FF* lp) {
+  __shared__ FF red_gf[32];
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nout = d.ni * d.nr;
+  FF a2 = FF{0.f, 0.f};
+  if (o < nout) {
+    FF sx = FF{0.f, 0.f}, sy = FF{0.f, 0.f};
+    for (int s = 0; s < nsplit; ++s) {
+      const float2 v = part[(size_t)s * nout + o];
+      sx = ff_add(sx, v.x);
+      sy = ff_add(sy, v.y);
+    }
+    sx = ff_add(sx, -esca[o].x);
+    sy = ff_add(sy, -esca[o].y);
+    const float2 v = make_float2(sx.hi + sx.lo, sy.hi + sy.lo);
+    rd[o] = v;
+    a2 = ff_make(cabs2(v));
   }
   const FF t = ff_block_sum(a2, red_gf);
   if (lp && threadIdx.x == 0) lp[blockIdx.x] = t;
 }
 
-// Adjoint data term on the coefficients: g[p][j] += (2 / ||E_sca||^2) sum_r conj(gsf[r][j]) r_d[p][r].
-// Block (jb, p): 32 coefficients; its 8 warps take every 8th receiver and their partial sums are
-// added in warp order.
+// Adjoint data term on the coefficients: g[p][j] += (2 / ||E_sca||^2) sum_r conj(gsf[r][j]) r_d[p][r],
+// tiled as 32 coefficients x 8 incidences per block with 32-receiver slices in shared memory.
 __global__ void __launch_bounds__(256) k_gsf_adj(Dev d, const float2* __restrict__ rd, float2* __restrict__ g) {
-  __shared__ float2 part[8][32];
-  const int NA = d.ky * d.kx, p = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j = blockIdx.x * 32 + lane;
+  __shared__ float2 sG[32][33];
+  __shared__ float2 sR[8][32];
+  const int NA = d.ky * d.kx;
+  const int ji = threadIdx.x & 31, pi = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + ji, p = blockIdx.y * 8 + pi;
   float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-  if (j < NA) {
-    const float2* rp = rd + (size_t)p * d.nr;
-    int r = warp;
-#pragma unroll 4
-    for (; r + 8 < d.nr; r += 16) {
-      a0 = a0 + cmulc(__ldg(&rp[r]), __ldg(&d.gsf[(size_t)r * NA + j]));
-      a1 = a1 + cmulc(__ldg(&rp[r + 8]), __ldg(&d.gsf[(size_t)(r + 8) * NA + j]));
+  for (int r0 = 0; r0 < d.nr; r0 += 32) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < 32 * 32; i += 256) {
+      const int rr = i >> 5, jj = i & 31, rg = r0 + rr, jg = blockIdx.x * 32 + jj;
+      sG[rr][jj] = (rg < d.nr && jg < NA) ? __ldg(&d.gsf[(size_t)rg * NA + jg]) : make_float2(0.f, 0.f);
     }
-    if (r < d.nr) a0 = a0 + cmulc(__ldg(&rp[r]), __ldg(&d.gsf[(size_t)r * NA + j]));
+    {
+      const int pp = threadIdx.x >> 5, rr = threadIdx.x & 31, pg = blockIdx.y * 8 + pp, rg = r0 + rr;
+      sR[pp][rr] = (pg < d.ni && rg < d.nr) ? rd[(size_t)pg * d.nr + rg] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < 32; rr += 2) {
+      a0 = a0 + cmulc(sR[pi][rr], sG[rr][ji]);
+      a1 = a1 + cmulc(sR[pi][rr + 1], sG[rr + 1][ji]);
+    }
   }
-  part[warp][lane] = a0 + a1;
-  __syncthreads();
-  if (warp == 0 && j < NA) {
-    float2 s = part[0][lane];
-#pragma unroll
-    for (int w = 1; w < 8; ++w) s = s + part[w][lane];
+  if (j < NA && p < d.ni) {
     const size_t i = (size_t)p * NA + j;
-    g[i] = g[i] + d.invn[1] * s;
+    g[i] = g[i] + d.invn[1] * (a0 + a1);
   }
 }
+
+// coefficient chunk length and count of the tiled forward product (the partials reuse the
+// split-K buffer of the unfolded G_S product, [n_gs_chunks][ni][nr])
+static int gsf_kc(const Dev& d) {
+  const int NA = d.ky * d.kx;
+  const int s = std::max(1, std::min((NA + 63) / 64, d.n_gs_chunks));
+  return ((NA + s - 1) / s + 63) / 64 * 64;
+}
+static int gsf_nsplit(const Dev& d) { return (d.ky * d.kx + gsf_kc(d) - 1) / gsf_kc(d); }
 
 // Analysis along y (second half of Phi^H): out[p][jy][jx] = sum_y T2[p][y][jx] conj(Wy[jy][y]).
 // Block (p, jy group of 8) stages T2[p] and the 8 rows of Wy in shared memory; warp jl owns
@@ -429,11 +468,23 @@ __global__ void __launch_bounds__(256) k_ana_y_sm(Dev d, const float2* __restric
   if (jy >= d.ky) return;
   float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
   const float2* w = Ws + jl * ny;
+  if (kx <= 32) {                                   // four chains over y mod 4, then combined
+    float2 b[4] = {a0, a0, a0, a0};
+    int y = 0;
+    for (; y + 3 < ny; y += 4)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (lane < kx) b[q] = b[q] + cmulc(Ts[(y + q) * kx + lane], w[y + q]);
+    for (; y < ny; ++y)
+      if (lane < kx) b[0] = b[0] + cmulc(Ts[y * kx + lane], w[y]);
+    a0 = (b[0] + b[1]) + (b[2] + b[3]);
+  } else {
 #pragma unroll 4
-  for (int y = 0; y < ny; ++y) {
-    const float2 wv = w[y];
-    if (lane < kx) a0 = a0 + cmulc(Ts[y * kx + lane], wv);
-    if (lane + 32 < kx) a1 = a1 + cmulc(Ts[y * kx + lane + 32], wv);
+    for (int y = 0; y < ny; ++y) {
+      const float2 wv = w[y];
+      if (lane < kx) a0 = a0 + cmulc(Ts[y * kx + lane], wv);
+      if (lane + 32 < kx) a1 = a1 + cmulc(Ts[y * kx + lane + 32], wv);
+    }
   }
   float2* o = out + ((size_t)p * d.ky + jy) * kx;
   if (lane < kx) o[lane] = a0;
@@ -443,9 +494,6 @@ __global__ void __launch_bounds__(256) k_ana_y_sm(Dev d, const float2* __restric
 static size_t sm_ana_y(const Dev& d) { return ((size_t)d.ny * d.kx + 8 * (size_t)d.ny) * sizeof(float2); }
 static bool ana_y_sm_ok(const Dev& d) { return d.kx <= 64 && sm_ana_y(d) <= 100 * 1024; }
 
-// outputs per warp of k_gsf_fwd, so that its block count stays within the loss-partial strip
-static int gsf_opw(const Dev& d) { return std::max(1, (d.ni * d.nr + 8 * PDF_LP_STRIDE - 1) / (8 * PDF_LP_STRIDE)); }
-static int gsf_blocks(const Dev& d) { return (d.ni * d.nr + 8 * gsf_opw(d) - 1) / (8 * gsf_opw(d)); }
 
 __global__ void k_finalize(Dev d, double* terms, int n_state, int n_data, int n_reg, int* step_inc) {
   ph_finalize(d, terms, n_state, n_data, n_reg, step_inc);
@@ -532,7 +580,7 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
                         int* step_inc, cudaEvent_t* ev) {
   Dev& d = h->d;
   const int nout = d.ni * d.nr;
-  const int n_data_blocks = d.fold ? gsf_blocks(d) : (nout + 255) / 256;
+  const int n_data_blocks = (nout + 255) / 256;
   const bool tc = h->tc != nullptr;
   pdf_status s;
   int k = 0;
@@ -562,8 +610,9 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
   }
   mark();
   if (d.fold) {
-    k_gsf_fwd<<<n_data_blocks, 256, 0, st>>>(d, alpha, d.esca, d.rd, d.lpart + LP_DATA * PDF_LP_STRIDE,
-                                              gsf_opw(d));
+    k_gsf_fwd<<<dim3((d.nr + 31) / 32, (d.ni + 7) / 8, gsf_nsplit(d)), 256, 0, st>>>(d, alpha, d.gspart, gsf_kc(d));
+    k_gsf_reduce<<<n_data_blocks, 256, 0, st>>>(d, d.gspart, gsf_nsplit(d), d.esca, d.rd,
+                                                 d.lpart + LP_DATA * PDF_LP_STRIDE);
   } else if (tc) {
     if ((s = tc_gs_fwd(h, nullptr, d.esca, d.rd, d.lpart + LP_DATA * PDF_LP_STRIDE, 1, st)) != PDF_OK) return s;
   } else {
@@ -615,13 +664,13 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
     k_ana_y<<<dim3(d.ky, d.ni), 256, 0, st>>>(d, T2, g);
   mark();
   if (d.fold) {
-    k_gsf_adj<<<dim3((d.ky * d.kx + 31) / 32, d.ni), 256, 0, st>>>(d, d.rd, g);
+    k_gsf_adj<<<dim3((d.ky * d.kx + 31) / 32, (d.ni + 7) / 8), 256, 0, st>>>(d, d.rd, g);
     mark();
   }
-  k_finalize<<<1, 256, 0, st>>>(d, terms ? terms : h->terms, d.fast ? fp_n_state(d) : d.ny, n_data_blocks,
+  k_finalize<<<1, 1024, 0, st>>>(d, terms ? terms : h->terms, d.fast ? fp_n_state(d) : d.ny, n_data_blocks,
                                 d.n_reg_blocks, step_inc);
   mark();
-  pdf_count_launch(d.fold ? (tc ? 9 : 11) : (tc ? 7 : 12));
+  pdf_count_launch(d.fold ? (tc ? 10 : 12) : (tc ? 7 : 12));
   PDF_LAUNCHED("pdf_loss_grad");
   return PDF_OK;
 }

@@ -180,6 +180,15 @@ def fp32_peak_tflops(peaks):
     return 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
 
 
+def bench_config(w, args, world):
+    """The workload description shared by both arms of the benchmark."""
+    return {"workload": f"{w.name}: {w.nx}x{w.ny} grid, {w.side} lambda DOI, Ni={w.ni}, Nr={w.nr}, "
+                        f"K={w.kx}x{w.ky}, {w.iters} Adam iterations, BP+CSI init, CCO",
+            "iters": w.iters, "lr": args.lr, "precision": args.precision, "loop": args.loop,
+            "fold_gs": args.fold, "parallelism": "replicas" if world > 1 else "single",
+            "l2": "flushed between reconstructions (512 MB write); working set L2-resident within one"}
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_2602_13805_gb300 import pdf
@@ -314,12 +323,7 @@ def run_ours(args, rank, world, local):
             "dtype": "c64 (fp32 complex), fp64 reductions" if args.precision == 0 else
                      "c64 FFT path + split-BF16 tensor-core contractions (fp32 accumulate), fp64 reductions",
             "data": "synthetic (seeded scene, GPU forward solver, AWGN)",
-            "config": {"workload": f"{w.name}: {w.nx}x{w.ny} grid, {w.side} lambda DOI, Ni={w.ni}, Nr={w.nr}, "
-                                   f"K={w.kx}x{w.ky}, {w.iters} Adam iterations, BP+CSI init, CCO",
-                       "iters": w.iters, "lr": args.lr, "precision": args.precision, "loop": args.loop,
-                       "fold_gs": args.fold,
-                       "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "flushed between reconstructions (512 MB write); working set L2-resident within one"},
+            "config": bench_config(w, args, world),
             "iters_per_s": w.iters * args.steps * world / (total_ms * 1e-3),
             "relerr": rep.relerr, "relerr_cco": rep.relerr_cco, "final_loss": rep.terms[0],
             "e2e": {"value": e2e_per_recon, "unit": "ms", "h2d_bytes_per_step": int(esca.nbytes),
@@ -472,8 +476,7 @@ def run_reference(args, rank, world):
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded scene, oracle forward solver, AWGN)",
-            "config": {"workload": f"{w.name}: {w.nx}x{w.ny}, Ni={w.ni}, Nr={w.nr}, K={w.kx}x{w.ky}, "
-                                   f"{w.iters} Adam iterations"},
+            "config": bench_config(w, args, world),
             "cpu_baseline": {"value": v, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"per step: BP+CSI init + {iters} Adam iterations scaled to {w.iters}"},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

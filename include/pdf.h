@@ -189,6 +189,14 @@ const char* pdf_stage_name(pdf_problem* h, int32_t k);
  * in ordinary builds, whose kernels carry no marks. */
 pdf_status pdf_phase_stamps(uint64_t* out);
 
+/* The cluster sizes the cluster loop (use_graph = 3) would consider for this handle, in order of
+ * preference: for each, out[4 i + 0..3] = cluster size C, shared-memory bytes per CTA, how many
+ * such clusters the device can hold at once (-1 when the plan exceeds the shared-memory limit or
+ * the query failed), and 1 when all ni clusters fit (the solve takes the first such row).
+ * Returns the number of rows (0: the problem does not qualify; the graph loop runs) or a
+ * negative pdf_status.  Makes no launch. */
+int32_t pdf_cluster_plan(pdf_problem* h, int32_t* out, int32_t nmax);
+
 /* G_S x without any device allocation, for callers that cannot call cudaMalloc: code whose
  * device memory is already owned by another allocator (a host framework's caching allocator
  * that has reserved the GPU), or latency-critical loops where an allocation, which can

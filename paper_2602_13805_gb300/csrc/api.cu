@@ -565,6 +565,16 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
     }
     d.ghat_perm = gp;
   }
+  d.what = nullptr;
+  if (d.fast && d.Px <= 128) {                       // sizes the cluster loop can take
+    float2* wt;
+    TRY(dalloc(h, &wt, (size_t)d.kx * d.Px));
+    if ((st = fp_row_dft_table(d, wt, s)) != PDF_OK) {
+      free_all(h);
+      return st;
+    }
+    d.what = wt;
+  }
   d.einc = einc;
   d.gs = gs;
   d.wx = wx;

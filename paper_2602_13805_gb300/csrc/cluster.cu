@@ -2,30 +2,32 @@
 //
 // One thread-block cluster per incidence p; CTA k of the cluster owns grid rows
 // [k RB, (k+1) RB) and padded columns [k CB, (k+1) CB).  Per iteration:
-//   1. synthesis of its rows (Eq. 9) and their padded row DFT (register warp FFT); each row's
-//      spectrum is stored straight into the column owners' shared memory (DSMEM)      | cluster barrier
-//   2. column DFT, x G_D spectrum, inverse column DFT on its columns; rows < ny go back
-//      to their row owners over DSMEM                                                  | cluster barrier
+//   1. synthesis (Eq. 9): T' = Wy^T alpha_p for all rows, J on its rows, and the padded row DFT
+//      of J at its own columns directly as T' what (what = the row DFT of the x basis), so the
+//      forward transform needs no exchange; r_d,p = (G_S Phi) alpha_p - E_sca,p (Eq. 16)
+//   2. column DFT, x G_D spectrum, inverse column DFT on its columns; rows < ny go to their row
+//      owners' shared memory (DSMEM)                                                   | cluster barrier
 //   3. inverse row DFT -> G_D J, s = beta J + E_inc + G_D J; this incidence's per-pixel
 //      contributions beta J conj(s), |s|^2 to a global array (double-buffered by iteration) | GRID barrier
 //   4. R-hat, chi-hat (Eq. 6, 7) for its rows and one halo row each side from the sums over all
 //      incidences; the TV / bridge pieces of Eq. 18-19 once per pixel; state residual (Eq. 15),
 //      regulariser cotangent -> w; adjoint inputs u, v; row DFT of u -> column owners    | cluster barrier
-//   5. column convolution with the conjugated spectrum (G_D^H) -> row owners             | cluster barrier
-//   6. inverse row DFT, dL/dJ = v + G_D^H u, analysis along x (a warp reduce-scatter over the
-//      row), partial analysis along y over its rows -> every CTA                          | cluster barrier
-//   7. dL/d alpha_p = sum of the partials (same order in every CTA) + the data term, Adam step on
-//      each CTA's copy of alpha_p (identical in all CTAs of the cluster)
-// The data term goes through the folded receiver operator G_S Phi (held whole in every CTA):
-// r_d,p = (G_S Phi) alpha_p - E_sca,p (Eq. 16) is formed in phase 1 from the current alpha_p and
-// its adjoint (2 / ||E_sca||^2) (G_S Phi)^H r_d,p is added to the gradient in phase 7.
+//   5. column convolution with the conjugated spectrum (G_D^H), result kept at the column owner
+//   6. analysis (Phi^H) of dL/dJ = v + G_D^H u: the G_D^H u part as the column data times
+//      conj(what) (the x-analysis of an inverse row DFT) over its columns and all rows, v over
+//      its rows, then the y-analysis -> partial dL/d alpha_p to every CTA of the cluster | cluster barrier
+//   7. dL/d alpha_p = sum of the partials (same order in every CTA), Adam step on each CTA's copy
+//      of alpha_p (identical in all CTAs of the cluster)
+// The data term goes through the folded operator G_S Phi, its receivers split over the cluster:
+// CTA k holds rows r = k + C t, forms r_d,p there in phase 1 and adds (2/||E_sca||^2)(G_S Phi)^H r_d,p
+// over those rows to its phase-6 partial.
 // The loss value itself is not formed in the loop (the solver evaluates it once at the final
-// iterate); the G_D spectrum slice, the x basis and the y-basis rows stay in shared memory.
-// The formulas are those of the stand-alone kernels (FP32 with compensated sums); only the data
-// movement and the summation order differ.  Every wait is bounded: a grid barrier that runs out
-// of time sets the error flag, after which no CTA waits at a grid barrier again; the loop runs to
-// its end (cluster barriers need no timeout: a cluster is always co-scheduled) and the host
-// reports the flag.  Co-residency of all clusters comes from the cooperative launch.
+// iterate); the folded operator, the G_D spectrum slice, the bases and the row-DFT table stay in
+// shared memory.  The formulas are those of the stand-alone kernels (FP32 with compensated sums);
+// the data movement and the summation order differ.  Every wait is bounded: a grid barrier that
+// runs out of time sets the error flag, after which no CTA waits at a grid barrier again; the loop
+// runs to its end (cluster barriers need no timeout: a cluster is always co-scheduled) and the
+// host reports the flag.  Co-residency of all clusters comes from the cooperative launch.
 #include <algorithm>
 
 #include <cooperative_groups.h>
@@ -170,15 +172,18 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
   float* itv = mgs + HP;                     // [TP] 1 / t (TV magnitude)                 (phase 4)
   float* sge = itv + TP;                     // [TP] sigmoid * exp (bridge term)          (phase 4)
   float* sgs = sge + TP;                     // [GP] sigmoid, own rows                    (phase 4)
-  float2* rd = gpart + NU;                   // [nr] data residual r_d,p
-  float2* es = rd + nr;                      // [nr]
-  float2* T2 = es + nr;                      // [RB][kx] synthesis / analysis temporary
-  float2* wys = T2 + RB * kx;                // [ky][RB] rows y0 .. y0+RB-1 of the y basis
-  float2* ghs = wys + ky * RB;               // [CB][P] this CTA's columns of the G_D spectrum
+  const int NRK = (nr - k + C - 1) / C;      // receivers r = k + C t owned by this CTA
+  float2* rd = gpart + NU;                   // [NRK] data residual r_d,p at own receivers
+  float2* es = rd + nr;                      // [NRK]
+  float2* T2 = es + nr;                      // [RB][kx] x-analysis of v on own rows
+  float2* Tall = T2 + RB * kx;               // [ny][kx] T' of all rows (phase 1), column-side x-analysis (phase 6)
+  float2* wyf = Tall + ny * kx;              // [ky][ny] y basis
+  float2* whs = wyf + ky * ny;               // [kx][CB] row DFT of the x basis at this CTA's columns
+  float2* ghs = whs + kx * CB;               // [CB][P] this CTA's columns of the G_D spectrum
   float2* wxs = ghs + CB * P;                // [kx][nx] x basis
   float* am = (float*)(wxs + kx * nx);       // [2 NA]
   float* av = am + 2 * NA;                   // [2 NA]
-  float2* gsf = (float2*)(av + 2 * NA);      // [nr][NA] folded receiver operator
+  float2* gsf = (float2*)(av + 2 * NA);      // [NRK][NA] folded receiver operator, own receivers
 
   // ---- one-time loads ----
 #pragma unroll 1
@@ -192,18 +197,23 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
 #pragma unroll 1
   for (int i = threadIdx.x; i < GP; i += CL_NT) Es[i] = d.einc[(size_t)p * M + y0 * nx + i];
 #pragma unroll 1
-  for (int i = threadIdx.x; i < nr; i += CL_NT) es[i] = d.esca[(size_t)p * nr + i];
+  for (int t = threadIdx.x; t < NRK; t += CL_NT) es[t] = d.esca[(size_t)p * nr + k + C * t];
 #pragma unroll 1
-  for (int i = threadIdx.x; i < ky * RB; i += CL_NT) {
-    const int jy = i / RB, yl = i - jy * RB;
-    wys[i] = d.wy[jy * ny + y0 + yl];
+  for (int i = threadIdx.x; i < ky * ny; i += CL_NT) wyf[i] = d.wy[i];
+#pragma unroll 1
+  for (int i = threadIdx.x; i < kx * CB; i += CL_NT) {
+    const int jx = i / CB, lc = i - jx * CB;
+    whs[i] = d.what[(size_t)jx * P + c0 + lc];
   }
 #pragma unroll 1
   for (int i = threadIdx.x; i < CB * P; i += CL_NT) ghs[i] = d.ghat_perm[(size_t)c0 * P + i];
 #pragma unroll 1
   for (int i = threadIdx.x; i < kx * nx; i += CL_NT) wxs[i] = d.wx[i];
 #pragma unroll 1
-  for (int i = threadIdx.x; i < nr * NA; i += CL_NT) gsf[i] = d.gsf[i];
+  for (int i = threadIdx.x; i < NRK * NA; i += CL_NT) {
+    const int t = i / NA, j = i - t * NA;
+    gsf[i] = d.gsf[(size_t)(k + C * t) * NA + j];
+  }
   const float ke = d.invn[0], ks = d.invn[1];
   const float2 beta = d.beta, bc = cconj(d.beta);
   const unsigned nblocks = gridDim.x;
@@ -212,53 +222,46 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
   for (int it = 0; it < a.iters; ++it) {
     CL_STAMP(0);
     float4* nd = a.nd + (size_t)(it & 1) * ni * M;
-    // ===== 1. synthesis of own rows, row DFT, scatter to column owners =====
+    // ===== 1. synthesis (Eq. 9): T' of all rows, J on own rows, the padded row DFT of J on own columns =====
 #pragma unroll 1
-    for (int i = threadIdx.x; i < RB * kx; i += CL_NT) {               // T'[yl][jx] = sum_jy Wy[jy][y] al[jy][jx]
-      const int yl = i / kx, jx = i - yl * kx;
+    for (int i = threadIdx.x; i < ny * kx; i += CL_NT) {               // T'[y][jx] = sum_jy Wy[jy][y] al[jy][jx]
+      const int y = i / kx, jx = i - y * kx;
       float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 4
-      for (int jy = 0; jy < ky; ++jy) acc = acc + cmul(wys[jy * RB + yl], al[jy * kx + jx]);
-      T2[i] = acc;
+      for (int jy = 0; jy < ky; ++jy) acc = acc + cmul(wyf[jy * ny + y], al[jy * kx + jx]);
+      Tall[i] = acc;
     }
 #pragma unroll 1
-    for (int r = warp; r < nr; r += CL_NW) {                             // r_d,p = (G_S Phi) alpha_p - E_sca,p
+    for (int t = warp; t < NRK; t += CL_NW) {                            // r_d,p = (G_S Phi) alpha_p - E_sca,p, own receivers
       float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 4
-      for (int j = lane; j < NA; j += 32) acc = acc + cmul(gsf[r * NA + j], al[j]);
+      for (int j = lane; j < NA; j += 32) acc = acc + cmul(gsf[t * NA + j], al[j]);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc = acc + shfl_xor2(acc, o);
-      if (lane == 0) rd[r] = acc - es[r];
+      if (lane == 0) rd[t] = acc - es[t];
     }
     __syncthreads();
     CL_STAMP(1);
 #pragma unroll 1
-    for (int i = threadIdx.x; i < GP; i += CL_NT) {                    // J = T' Wx on own pixels (Eq. 9)
+    for (int i = threadIdx.x; i < GP; i += CL_NT) {                    // J = T' Wx on own pixels
       const int yl = i / nx, x = i - yl * nx;
+      const float2* tr = Tall + (y0 + yl) * kx;
       float2 s = make_float2(0.f, 0.f);
 #pragma unroll 4
-      for (int jx = 0; jx < kx; ++jx) s = s + cmul(T2[yl * kx + jx], wxs[jx * nx + x]);
+      for (int jx = 0; jx < kx; ++jx) s = s + cmul(tr[jx], wxs[jx * nx + x]);
       Js[i] = s;
     }
-    __syncthreads();
     CL_STAMP(2);
 #pragma unroll 1
-    for (int yl = warp; yl < RB; yl += CL_NW) {
-      Line<P> L;
-#pragma unroll
-      for (int m = 0; m < R; ++m) {
-        const int x = lane + 32 * m;
-        L.v[m] = x < nx ? Js[yl * nx + x] : make_float2(0.f, 0.f);
-      }
-      L = line_fwd<P>(L, tw, lane);
-#pragma unroll
-      for (int kk = 0; kk < R; ++kk) {
-        const int c = kk * 32 + lane;
-        float2* dst = cl.map_shared_rank(colb, c / CB);
-        dst[(c % CB) * LS + y0 + yl] = L.v[kk];
-      }
+    for (int i = threadIdx.x; i < CB * ny; i += CL_NT) {               // row DFT of J at own columns: T' what
+      const int lc = i / ny, y = i - lc * ny;
+      const float2* tr = Tall + y * kx;
+      float2 s = make_float2(0.f, 0.f);
+#pragma unroll 4
+      for (int jx = 0; jx < kx; ++jx) s = s + cmul(tr[jx], whs[jx * CB + lc]);
+      colb[lc * LS + y] = s;
     }
-    cl.sync();
+    __syncthreads();
     CL_STAMP(3);
     // ===== 2. column convolution, results back to row owners =====
 #pragma unroll 1
@@ -423,7 +426,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     }
     cl.sync();
     CL_STAMP(10);
-    // ===== 5. column convolution with the conjugated spectrum =====
+    // ===== 5. column convolution with the conjugated spectrum, kept at the column owner =====
 #pragma unroll 1
     for (int lc = warp; lc < CB; lc += CL_NW) {
       const float2* g = ghs + lc * P;
@@ -439,37 +442,39 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
 #pragma unroll
       for (int m = 0; m < R; ++m) {
         const int y = lane + 32 * m;
-        if (y < ny) {
-          float2* dst = cl.map_shared_rank(rowb, y / RB);
-          dst[(y % RB) * P + c0 + lc] = L.v[m];
-        }
+        if (y < ny) colb[lc * LS + y] = L.v[m];                          // B = row-spectral G_D^H u, own columns
       }
     }
-    cl.sync();
+    __syncthreads();
     CL_STAMP(11);
-    // ===== 6. inverse row DFT, dL/dJ, analysis along x (warp reduce-scatter), partial analysis along y =====
+    // ===== 6. analysis (Phi^H) of dL/dJ = v + G_D^H u, partial over this CTA's share =====
+    // G_D^H u = inverse row DFT of B, so its x-analysis is B conj(what) summed over the columns
+    // (each CTA: all rows, its columns); v is analysed over this CTA's rows.
 #pragma unroll 1
-    for (int yl = warp; yl < RB; yl += CL_NW) {
-      Line<P> L;
-#pragma unroll
-      for (int kk = 0; kk < R; ++kk) L.v[kk] = rowb[yl * P + kk * 32 + lane];
-      L = line_inv<P>(L, tw, lane);
-#pragma unroll
-      for (int m = 0; m < R; ++m) {
-        const int x = lane + 32 * m;
-        if (x < nx) ss[yl * nx + x] = L.v[m] + vs[yl * nx + x];          // dL/dJ (s is no longer needed)
+    for (int i = threadIdx.x; i < ny * kx; i += CL_NT) {
+      const int jx = i / ny, y = i - jx * ny;                             // lanes along y: column reads contiguous
+      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+      int lc = 0;
+#pragma unroll 4
+      for (; lc + 1 < CB; lc += 2) {
+        a0 = a0 + cmulc(colb[lc * LS + y], whs[jx * CB + lc]);
+        a1 = a1 + cmulc(colb[(lc + 1) * LS + y], whs[jx * CB + lc + 1]);
       }
-      __syncwarp();
+      if (lc < CB) a0 = a0 + cmulc(colb[lc * LS + y], whs[jx * CB + lc]);
+      Tall[y * kx + jx] = a0 + a1;
+    }
+#pragma unroll 1
+    for (int yl = warp; yl < RB; yl += CL_NW) {                          // x-analysis of v: warp per row
       for (int j0 = 0; j0 < kx; j0 += 16) {
         float2 acc[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) acc[j] = make_float2(0.f, 0.f);
 #pragma unroll 1
         for (int x = lane; x < nx; x += 32) {
-          const float2 gj = ss[yl * nx + x];
+          const float2 vv = vs[yl * nx + x];
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            if (j0 + j < kx) acc[j] = acc[j] + cmulc(gj, wxs[(j0 + j) * nx + x]);
+            if (j0 + j < kx) acc[j] = acc[j] + cmulc(vv, wxs[(j0 + j) * nx + x]);
         }
         warp_reduce_scatter16(acc, lane);
         const int jx = j0 + (lane >> 1);
@@ -479,11 +484,23 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     __syncthreads();
     CL_STAMP(12);
 #pragma unroll 1
-    for (int i = threadIdx.x; i < NA; i += CL_NT) {
+    for (int i = threadIdx.x; i < NA; i += CL_NT) {                     // analysis along y
       const int jy = i / kx, jx = i - jy * kx;
-      float2 acc = make_float2(0.f, 0.f);
+      const float2* wr = wyf + jy * ny;
+      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+      int y = 0;
 #pragma unroll 4
-      for (int yl = 0; yl < RB; ++yl) acc = acc + cmulc(T2[yl * kx + jx], wys[jy * RB + yl]);
+      for (; y + 1 < ny; y += 2) {
+        a0 = a0 + cmulc(Tall[y * kx + jx], wr[y]);
+        a1 = a1 + cmulc(Tall[(y + 1) * kx + jx], wr[y + 1]);
+      }
+      if (y < ny) a0 = a0 + cmulc(Tall[y * kx + jx], wr[y]);
+#pragma unroll 4
+      for (int yl = 0; yl < RB; ++yl) a1 = a1 + cmulc(T2[yl * kx + jx], wr[y0 + yl]);
+      float2 gd = make_float2(0.f, 0.f);                                 // data term (Eq. 16), own receivers
+#pragma unroll 4
+      for (int t = 0; t < NRK; ++t) gd = gd + cmulc(rd[t], gsf[t * NA + i]);
+      const float2 acc = (a0 + a1) + ks * gd;
 #pragma unroll 1
       for (int q = 0; q < C; ++q) {
         float2* dst = cl.map_shared_rank(gpart, q);
@@ -498,10 +515,6 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
       float2 g = make_float2(0.f, 0.f);
 #pragma unroll 1
       for (int q = 0; q < C; ++q) g = g + gpart[q * NA + i];
-      float2 gd = make_float2(0.f, 0.f);
-#pragma unroll 4
-      for (int r = 0; r < nr; ++r) gd = gd + cmulc(rd[r], gsf[r * NA + i]);
-      g = g + ks * gd;                                                   // data term, Eq. 16
       float2 ap = al[i];
       ph_adam(0, &ap.x, &g.x, &am[2 * i], &av[2 * i], 1, it + 1, a.tab, a.cap, a.b1, a.b2, a.eps);
       ph_adam(0, &ap.y, &g.y, &am[2 * i + 1], &av[2 * i + 1], 1, it + 1, a.tab, a.cap, a.b1, a.b2, a.eps);
@@ -525,7 +538,8 @@ static size_t cluster_smem(const Dev& d, int C, int RB, int CB, int P) {
   const size_t nscr = 2 * GP + HP + 2 * TP;
   const size_t NU = std::max((size_t)C * NA, (nscr + 1) / 2);
   const size_t f2 = P + (size_t)RB * P + (size_t)CB * (d.ny + 1) + 4 * GP + 2 * HP + NA + NU + 2 * (size_t)d.nr +
-                    (size_t)RB * d.kx + (size_t)d.ky * RB + (size_t)CB * P + (size_t)d.kx * d.nx + (size_t)d.nr * NA;
+                    (size_t)RB * d.kx + (size_t)d.ny * d.kx + (size_t)d.ky * d.ny + (size_t)d.kx * CB +
+                    (size_t)CB * P + (size_t)d.kx * d.nx + (size_t)((d.nr + C - 1) / C) * NA;
   return f2 * sizeof(float2) + 4 * NA * sizeof(float);
 }
 
@@ -538,7 +552,7 @@ static bool cluster_ok(const Dev& d, int sms, int c) {
 }
 
 template <int P>
-static pdf_status launch_cluster(pdf_problem* h, ClusterArgs a, size_t smem, cudaStream_t st, bool* done) {
+static cudaLaunchConfig_t cluster_config(int ni, int C, size_t smem, cudaStream_t st, cudaLaunchAttribute* at) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_cluster_solve<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CL_SMEM_MAX);
@@ -547,34 +561,78 @@ static pdf_status launch_cluster(pdf_problem* h, ClusterArgs a, size_t smem, cud
     attr = true;
   }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(h->d.ni * a.C);
+  cfg.gridDim = dim3(ni * C);
   cfg.blockDim = dim3(CL_NT);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = a.C;
+  at[0].val.clusterDim.x = C;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   at[1].id = cudaLaunchAttributeCooperative;
   at[1].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 2;
-  int nclusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&nclusters, (void*)k_cluster_solve<P>, &cfg) != cudaSuccess ||
-      nclusters < h->d.ni) {
+  return cfg;
+}
+
+// clusters of size C that can be co-resident on this device (-1: the query failed)
+template <int P>
+static int max_active_clusters(int ni, int C, size_t smem) {
+  cudaLaunchAttribute at[2];
+  cudaLaunchConfig_t cfg = cluster_config<P>(ni, C, smem, 0, at);
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, (void*)k_cluster_solve<P>, &cfg) != cudaSuccess) {
     cudaGetLastError();
-    return PDF_OK;                                  // does not fit co-resident: caller falls back
+    return -1;
   }
-  Dev d = h->d;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_cluster_solve<P>, d, a);
-  if (e != cudaSuccess) {
+  return n;
+}
+
+struct ClPlanRow {
+  int C, smem, clusters, usable;
+};
+
+// The cluster sizes cl_run considers, in order, with their shared-memory plan and the number of
+// such clusters the device can hold at once; a row is usable when all ni clusters fit.
+static int cl_plan(const pdf_problem* h, ClPlanRow* rows, int nmax) {
+  const Dev& d = h->d;
+  if (!d.fast || h->tc || !d.fold || !d.what || d.Px != d.Py || d.Px > 128 || d.kx > 64) return 0;
+  int dev = 0, sms = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) {
     cudaGetLastError();
-    return PDF_OK;                                  // launch form unsupported: caller falls back
+    return 0;
   }
-  pdf_count_launch(1);
-  *done = true;
-  return PDF_OK;
+  int n = 0;
+  for (int c = 16; c >= 2 && n < nmax; c >>= 1) {
+    if (!cluster_ok(d, sms, c)) continue;
+    const size_t smem = cluster_smem(d, c, d.ny / c, d.Px / c, d.Px);
+    ClPlanRow r = {c, (int)smem, -1, 0};
+    if (smem <= CL_SMEM_MAX) {
+      r.clusters = d.Px == 64 ? max_active_clusters<64>(d.ni, c, smem) : max_active_clusters<128>(d.ni, c, smem);
+      r.usable = r.clusters >= d.ni;
+    }
+    rows[n++] = r;
+  }
+  return n;
+}
+
+extern "C" int32_t pdf_cluster_plan(pdf_problem* h, int32_t* out, int32_t nmax) {
+  if (!h || !out || nmax < 1) {
+    set_err(PDF_EINVAL, "pdf_cluster_plan: bad arguments");
+    return PDF_EINVAL;
+  }
+  ClPlanRow rows[4];
+  const int n = cl_plan(h, rows, std::min(4, (int)nmax));
+  for (int i = 0; i < n; ++i) {
+    out[4 * i + 0] = rows[i].C;
+    out[4 * i + 1] = rows[i].smem;
+    out[4 * i + 2] = rows[i].clusters;
+    out[4 * i + 3] = rows[i].usable;
+  }
+  return n;
 }
 
 extern "C" pdf_status pdf_phase_stamps(uint64_t* out) {
@@ -593,18 +651,22 @@ extern "C" pdf_status pdf_phase_stamps(uint64_t* out) {
 pdf_status cl_run(pdf_problem* h, const pdf_solve_opts* o, int iters, cudaStream_t st, bool* done) {
   *done = false;
   const Dev& d = h->d;
-  if (!d.fast || h->tc || !d.fold || d.Px != d.Py || d.Px > 128 || iters < 1 || d.kx > 64) return PDF_OK;
-  int dev = 0, sms = 0, coop = 0;
-  PDF_CUDA(cudaGetDevice(&dev));
-  PDF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  PDF_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-  if (!coop) return PDF_OK;
+  if (iters < 1) return PDF_OK;
+  ClPlanRow rows[4];
+  const int n = cl_plan(h, rows, 4);
+  int pick = -1;
+  for (int i = 0; i < n && pick < 0; ++i)
+    if (rows[i].usable) pick = i;
+  if (pick < 0) return PDF_OK;
   if (!h->cl_nd) {
     pdf_status s;
     if ((s = ws_alloc(h, (void**)&h->cl_nd, sizeof(float4) * 2 * (size_t)d.ni * d.M)) != PDF_OK) return s;
   }
   ClusterArgs a;
   a.iters = iters;
+  a.C = rows[pick].C;
+  a.RB = d.ny / a.C;
+  a.CB = d.Px / a.C;
   a.alpha = h->alpha;
   a.tab = h->adam_tab;
   a.cap = h->adam_cap;
@@ -615,17 +677,21 @@ pdf_status cl_run(pdf_problem* h, const pdf_solve_opts* o, int iters, cudaStream
   a.bar = h->bar;
   a.err = h->perr;
   PDF_CUDA(cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st));
-  pdf_status s = PDF_OK;
-  for (int c = 16; c >= 2 && !*done; c >>= 1) {
-    if (!cluster_ok(d, sms, c)) continue;
-    a.C = c;
-    a.RB = d.ny / c;
-    a.CB = d.Px / c;
-    const size_t smem = cluster_smem(d, c, a.RB, a.CB, d.Px);
-    if (smem > CL_SMEM_MAX) continue;
-    if (d.Px == 64) s = launch_cluster<64>(h, a, smem, st, done);
-    else if (d.Px == 128) s = launch_cluster<128>(h, a, smem, st, done);
-    if (s != PDF_OK) return s;
+  cudaLaunchAttribute at[2];
+  const size_t smem = (size_t)rows[pick].smem;
+  cudaError_t e;
+  if (d.Px == 64) {
+    cudaLaunchConfig_t cfg = cluster_config<64>(d.ni, a.C, smem, st, at);
+    e = cudaLaunchKernelEx(&cfg, k_cluster_solve<64>, h->d, a);
+  } else {
+    cudaLaunchConfig_t cfg = cluster_config<128>(d.ni, a.C, smem, st, at);
+    e = cudaLaunchKernelEx(&cfg, k_cluster_solve<128>, h->d, a);
   }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return PDF_OK;                                   // launch form unsupported: the caller falls back
+  }
+  pdf_count_launch(1);
+  *done = true;
   return PDF_OK;
 }

@@ -167,6 +167,35 @@ __global__ void k_perm_ghat(const float2* __restrict__ ghat, float2* __restrict_
   gp[(size_t)cx * Py + cy] = ghat[(size_t)ky * Px + kx];
 }
 
+// Row DFT of the x synthesis basis: what[jx][c] = sum_{x < nx} Wx[jx][x] exp(-2 pi i f(c) x / Px),
+// f(c) the frequency at position c of the register FFT's output order, so that the padded row DFT
+// of J = T' Wx (Eq. 9) is T' what and the x-analysis of an inverse row DFT is a product with
+// conj(what).  FP64, exact angle reduction (integer numerators modulo nx Px).
+__global__ void k_row_dft_table(float2* __restrict__ what, int kx, int nx, int Px) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x, jx = blockIdx.y;
+  if (c >= Px) return;
+  const long f = perm_to_freq(c, Px / 32);
+  const long fj = jx < (kx + 1) / 2 ? jx : nx - kx + jx;
+  const long den = (long)nx * Px;
+  double re = 0.0, im = 0.0;
+  for (int x = 0; x < nx; ++x) {
+    const long num = ((fj * x * Px - f * x * nx) % den + den) % den;
+    double s, co;
+    sincospi(2.0 * (double)num / (double)den, &s, &co);
+    re += co;
+    im += s;
+  }
+  const double sc = 1.0 / sqrt((double)nx);
+  what[(size_t)jx * Px + c] = make_float2((float)(re * sc), (float)(im * sc));
+}
+
+pdf_status fp_row_dft_table(const Dev& d, float2* what, cudaStream_t st) {
+  k_row_dft_table<<<dim3((d.Px + 127) / 128, d.kx), 128, 0, st>>>(what, d.kx, d.nx, d.Px);
+  pdf_count_launch(1);
+  PDF_LAUNCHED("row DFT table of the x basis");
+  return PDF_OK;
+}
+
 pdf_status fp_perm_ghat(const Dev& d, float2* gp, cudaStream_t st) {
   k_perm_ghat<<<dim3((d.Py + 127) / 128, d.Px), 128, 0, st>>>(d.ghat, gp, d.Px, d.Py);
   pdf_count_launch(1);

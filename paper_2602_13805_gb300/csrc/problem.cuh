@@ -32,6 +32,7 @@ struct Dev {
   const float2* twy;     // [Py]
   const float2* ghat;    // [Py][Px] spectrum of the circulant G_D kernel / (Px Py)
   const float2* ghat_perm; // [Px][Py] the same in the register FFT's digit-reversed order (fast path)
+  const float2* what;    // [kx][Px] row DFT of the x basis, columns in that order (cluster loop)
   const float2* einc;    // [ni][M]
   const float2* gs;      // [nr][M]
   const float2* gsf;     // [nr][ky*kx] folded receiver operator G_S Phi (when fold)
@@ -162,6 +163,7 @@ size_t fp_smem_ana(const Dev& d);
 size_t fp_smem_sums(const Dev& d);
 int fp_n_state(const Dev& d);
 int fp_choose_nsg(const Dev& d, int sms);
+pdf_status fp_row_dft_table(const Dev& d, float2* what, cudaStream_t st);
 
 // persistent solve loop (persist.cu)
 pdf_status ps_run(pdf_problem* h, const pdf_solve_opts* o, int iters, unsigned* bar, int* err, cudaStream_t st,

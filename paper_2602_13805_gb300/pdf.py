@@ -81,7 +81,7 @@ EXPORTS = ("pdf_config_default", "pdf_setup", "pdf_set_data", "pdf_loss_grad", "
            "pdf_last_error", "pdf_profile_loss_grad", "pdf_kernel_name", "pdf_gs_apply_static",
            "pdf_stage_name", "pdf_mlp_create", "pdf_mlp_destroy", "pdf_mlp_set_params", "pdf_mlp_get_params",
            "pdf_mlp_forward", "pdf_mlp_loss_grad", "pdf_mlp_train_step", "pdf_mlp_error_flag",
-           "pdf_phase_stamps")
+           "pdf_phase_stamps", "pdf_cluster_plan")
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -117,6 +117,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pdf_profile_loss_grad.restype = i32
     lib.pdf_phase_stamps.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
     lib.pdf_phase_stamps.restype = ctypes.c_int
+    lib.pdf_cluster_plan.argtypes = [vp, ctypes.POINTER(i32), i32]
+    lib.pdf_cluster_plan.restype = i32
     lib.pdf_kernel_name.argtypes = [i32]
     lib.pdf_kernel_name.restype = ctypes.c_char_p
     lib.pdf_stage_name.argtypes = [vp, i32]
@@ -222,6 +224,15 @@ def pdf_loss_grad(h: int, alpha, grad=None, terms=None, stream=None):
 
 def pdf_apply_op(h: int, op: int, x, out, stream=None):
     _check(load().pdf_apply_op(h, op, _ptr(x), _ptr(out), _stream(stream)))
+
+
+def pdf_cluster_plan(h: int):
+    """[(C, smem bytes, co-resident clusters, usable)] the cluster loop would consider for handle h."""
+    buf = (ctypes.c_int32 * 16)()
+    n = load().pdf_cluster_plan(h, buf, 4)
+    if n < 0:
+        _check(n)
+    return [tuple(buf[4 * i: 4 * i + 4]) for i in range(n)]
 
 
 def pdf_solve(h: int, opts: pdf_solve_opts, chi_out=None, chi_raw_out=None, alpha_out=None, report=True,
@@ -346,7 +357,8 @@ class Problem:
         alpha = self._t(self.ni, self.ky, self.kx)
         rep = pdf_solve(self.h, o, chi, chi_raw, alpha, True, stream)
         return dict(chi=chi, chi_raw=chi_raw, alpha=alpha, terms=np.array(rep.terms[:]), relerr=rep.relerr,
-                    relerr_cco=rep.relerr_cco, history=hist, used_warm_start=rep.used_warm_start)
+                    relerr_cco=rep.relerr_cco, history=hist, used_warm_start=rep.used_warm_start,
+                    loop_mode=rep.loop_mode)
 
     def forward(self, chi, tol=1e-6, max_iter=2000, stream=None):
         esca = self._t(self.ni, self.nr)

@@ -16,9 +16,9 @@ import sys
 import numpy as np
 
 PHASES = [
-    "synthesis T' = Wy^T alpha (Eq. 9); r_d = (G_S Phi) alpha - E_sca (Eq. 16)",
-    "synthesis J = T' Wx",
-    "row DFT of J -> column owners (DSMEM) + cluster barrier",
+    "synthesis T' = Wy^T alpha, all rows (Eq. 9); r_d = (G_S Phi) alpha - E_sca (Eq. 16)",
+    "J on own rows",
+    "row DFT of J at own columns (T' what)",
     "column convolution with the G_D spectrum -> row owners + cluster barrier",
     "inverse row DFT (G_D J)",
     "s and the per-incidence sums + grid barrier",
@@ -26,9 +26,9 @@ PHASES = [
     "TV / bridge pieces (Eq. 18, 19)",
     "residual, cotangent on chi, adjoint inputs u, v",
     "row DFT of u -> column owners + cluster barrier",
-    "column convolution with the conjugated spectrum + cluster barrier",
-    "inverse row DFT, dL/dJ, analysis along x",
-    "analysis along y partials -> all CTAs + cluster barrier",
+    "column convolution with the conjugated spectrum (kept local)",
+    "x-analysis: column data x conj(what), v on own rows",
+    "y-analysis partials -> all CTAs + cluster barrier",
     "gradient sum + (G_S Phi)^H r_d + Adam step",
 ]
 

@@ -241,9 +241,17 @@ def test_cluster_loop_matches_graph(name):
     c = Case(w)
     prob = c.problem()
     chi_t = _dev(c.chi.astype(np.complex64))
+    from paper_2602_13805_gb300 import pdf
     a = prob.solve(iters=w.iters, chi_true=chi_t, use_graph=1)
     b = prob.solve(iters=w.iters, chi_true=chi_t, use_graph=3)
     b2 = prob.solve(iters=w.iters, chi_true=chi_t, use_graph=3)
+    plan = pdf.pdf_cluster_plan(prob.h)
+    print(name, "cluster plan (C, smem, co-resident clusters, usable):", plan)
+    assert a["loop_mode"] == 1
+    # the cluster form must have run wherever the device can hold all clusters (c1, cP always)
+    assert b["loop_mode"] == (3 if any(r[3] for r in plan) else 1)
+    if name in ("c1", "cP"):
+        assert b["loop_mode"] == 3
     assert torch.equal(b["alpha"], b2["alpha"])                     # deterministic
     err = (a["alpha"] - b["alpha"]).abs().max().item() / a["alpha"].abs().max().item()
     print(name, "cluster vs graph alpha rel", err, a["relerr_cco"], b["relerr_cco"])
@@ -258,6 +266,7 @@ def test_cluster_loop_vs_oracle():
     c = Case(w)
     prob = c.problem()
     out = prob.solve(iters=w.iters, chi_true=_dev(c.chi.astype(np.complex64)), use_graph=3)
+    assert out["loop_mode"] == 3
     ref = solve.pdf_solve(c.ops, c.esca, w.iters, chi_true=c.chi)
     assert abs(out["relerr_cco"] - ref["relerr_cco"]) < 1e-3
     prob.close()

@@ -10,7 +10,9 @@
 //   3. inverse row DFT -> G_D J, s = beta J + E_inc + G_D J; this incidence's per-pixel
 //      contributions beta J conj(s), |s|^2 to a global array (double-buffered by iteration) | GRID barrier
 //   4. R-hat, chi-hat (Eq. 6, 7) for its rows and one halo row each side from the sums over all
-//      incidences; the TV / bridge pieces of Eq. 18-19 once per pixel; state residual (Eq. 15),
+//      incidences (when those sums are large, each CTA of the grid sums one slice of pixels and
+//      writes R-hat, chi-hat there, and the CTAs read their rows after a second GRID barrier);
+//      the TV / bridge pieces of Eq. 18-19 once per pixel; state residual (Eq. 15),
 //      regulariser cotangent -> w; adjoint inputs u, v; row DFT of u -> column owners    | cluster barrier
 //   5. column convolution with the conjugated spectrum (G_D^H), result kept at the column owner
 //   6. analysis (Phi^H) of dL/dJ = v + G_D^H u: the G_D^H u part as the column data times
@@ -46,6 +48,9 @@ struct ClusterArgs {
   int cap;
   float b1, b2, eps;
   float4* nd;             // [2][ni][M] per-incidence (Re N, Im N, D, unused)
+  float4* rc;             // [M] (R-hat, chi-hat) when the sums are split over the grid
+  float* dsg;             // [M] D, sign = clamp flag, likewise
+  int sl;                 // pixels per CTA slice (0: every CTA sums its own rows)
   unsigned* bar;
   int* err;               // 1: a grid barrier timed out; 2: launched with the wrong cluster shape
 };
@@ -131,6 +136,41 @@ __device__ __noinline__ Line<P> line_conv(Line<P> x, Line<P> g, const float2* __
   return x;
 }
 
+// two columns convolved together (interleaved butterflies; used where a warp owns two columns)
+template <int P> struct Line2 {
+  float2 v[2][P / 32];
+};
+template <int P>
+__device__ __noinline__ Line2<P> line_conv2(Line2<P> x, Line2<P> g, const float2* __restrict__ tw, int lane) {
+  WarpFFTn<P, 2>::forward(x.v, tw, lane);
+#pragma unroll
+  for (int l = 0; l < 2; ++l)
+#pragma unroll
+    for (int k = 0; k < P / 32; ++k) x.v[l][k] = cmul(x.v[l][k], g.v[l][k]);
+  WarpFFTn<P, 2>::inverse(x.v, tw, lane);
+  return x;
+}
+
+// Sums over the ni incidences of one pixel's contributions N = beta J conj(s), D = |s|^2 (stride
+// M float4): compensated, eight loads in flight, pairwise within a batch.  Returns (Re N, Im N, D, 0).
+__device__ __noinline__ float4 cl_pixel_sums(const float4* __restrict__ o, int ni, int M) {
+  float nr_ = 0.f, ni_ = 0.f, dd = 0.f, cr = 0.f, ci = 0.f, cd = 0.f;
+#pragma unroll 1
+  for (int q0 = 0; q0 < ni; q0 += 8) {
+    float4 b[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      b[j] = q0 + j < ni ? __ldcg(o + (size_t)(q0 + j) * M) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float sx = ((b[0].x + b[1].x) + (b[2].x + b[3].x)) + ((b[4].x + b[5].x) + (b[6].x + b[7].x));
+    const float sy = ((b[0].y + b[1].y) + (b[2].y + b[3].y)) + ((b[4].y + b[5].y) + (b[6].y + b[7].y));
+    const float sz = ((b[0].z + b[1].z) + (b[2].z + b[3].z)) + ((b[4].z + b[5].z) + (b[6].z + b[7].z));
+    float t, yv;
+    yv = sx - cr; t = nr_ + yv; cr = (t - nr_) - yv; nr_ = t;
+    yv = sy - ci; t = ni_ + yv; ci = (t - ni_) - yv; ni_ = t;
+    yv = sz - cd; t = dd + yv; cd = (t - dd) - yv; dd = t;
+  }
+  return make_float4(nr_ - cr, ni_ - ci, dd - cd, 0.f);
+}
 
 template <int P>
 __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a) {
@@ -265,23 +305,49 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     CL_STAMP(3);
     // ===== 2. column convolution, results back to row owners =====
 #pragma unroll 1
-    for (int lc = warp; lc < CB; lc += CL_NW) {
-      const float2* g = ghs + lc * P;
-      Line<P> G, L;
+    for (int lc = warp; lc < CB; lc += 2 * CL_NW) {                    // columns lc and lc + NW together
+      const int lc2 = lc + CL_NW;
+      if (lc2 < CB) {
+        Line2<P> G, L;
 #pragma unroll
-      for (int kk = 0; kk < R; ++kk) G.v[kk] = g[kk * 32 + lane];
+        for (int l = 0; l < 2; ++l) {
+          const int c = l ? lc2 : lc;
 #pragma unroll
-      for (int m = 0; m < R; ++m) {
-        const int y = lane + 32 * m;
-        L.v[m] = y < ny ? colb[lc * LS + y] : make_float2(0.f, 0.f);
-      }
-      L = line_conv<P>(L, G, tw, lane);
+          for (int kk = 0; kk < R; ++kk) G.v[l][kk] = ghs[c * P + kk * 32 + lane];
 #pragma unroll
-      for (int m = 0; m < R; ++m) {
-        const int y = lane + 32 * m;
-        if (y < ny) {
-          float2* dst = cl.map_shared_rank(rowb, y / RB);
-          dst[(y % RB) * P + c0 + lc] = L.v[m];
+          for (int m = 0; m < R; ++m) {
+            const int y = lane + 32 * m;
+            L.v[l][m] = y < ny ? colb[c * LS + y] : make_float2(0.f, 0.f);
+          }
+        }
+        L = line_conv2<P>(L, G, tw, lane);
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+          const int y = lane + 32 * m;
+          if (y < ny) {
+            float2* dst = cl.map_shared_rank(rowb, y / RB) + (y % RB) * P + c0;
+            dst[lc] = L.v[0][m];
+            dst[lc2] = L.v[1][m];
+          }
+        }
+      } else {
+        const float2* g = ghs + lc * P;
+        Line<P> G, L;
+#pragma unroll
+        for (int kk = 0; kk < R; ++kk) G.v[kk] = g[kk * 32 + lane];
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+          const int y = lane + 32 * m;
+          L.v[m] = y < ny ? colb[lc * LS + y] : make_float2(0.f, 0.f);
+        }
+        L = line_conv<P>(L, G, tw, lane);
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+          const int y = lane + 32 * m;
+          if (y < ny) {
+            float2* dst = cl.map_shared_rank(rowb, y / RB);
+            dst[(y % RB) * P + c0 + lc] = L.v[m];
+          }
         }
       }
     }
@@ -311,36 +377,68 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
       const float2 n = cmul(beta, cmulc(J, s));
       __stcg(&nd[(size_t)p * M + y0 * nx + i], make_float4(n.x, n.y, cabs2(s), 0.f));
     }
-    cl_grid_barrier(a.bar, (unsigned)(it + 1) * nblocks, a.err);
+    const unsigned nbar = a.sl > 0 ? 2u : 1u;                           // grid barriers per iteration
+    cl_grid_barrier(a.bar, ((unsigned)it * nbar + 1u) * nblocks, a.err);
     CL_STAMP(6);
     // ===== 4. R-hat, chi-hat (own rows + halo), residuals, regulariser cotangent, adjoint inputs =====
+    if (a.sl > 0) {
+      // Sums over incidences split over the grid: CTA b sums pixels [b sl, (b+1) sl) (a thread per
+      // pixel, as below) and writes R-hat, chi-hat and the signed D there; after a second grid
+      // barrier every CTA reads its rows + halo.  Same arithmetic as the per-CTA form.
+      const int pix1 = min((int)blockIdx.x * a.sl + a.sl, M);
 #pragma unroll 1
-    for (int i = threadIdx.x; i < HP; i += CL_NT) {
-      const int hy = i / nx, x = i - hy * nx, y = y0 + hy - 1;
-      if (y < 0 || y >= ny) continue;
-      const float4* o = nd + (size_t)y * nx + x;
-      float nr_ = 0.f, ni_ = 0.f, dd = 0.f, cr = 0.f, ci = 0.f, cd = 0.f;
-      for (int q0 = 0; q0 < ni; q0 += 8) {                                // 8 loads in flight, pairwise
-        float4 b[8];                                                     // sum of the 8, then one
-#pragma unroll                                                           // compensated add per batch
-        for (int j = 0; j < 8; ++j)
-          b[j] = q0 + j < ni ? __ldcg(o + (size_t)(q0 + j) * M) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float sx = ((b[0].x + b[1].x) + (b[2].x + b[3].x)) + ((b[4].x + b[5].x) + (b[6].x + b[7].x));
-        const float sy = ((b[0].y + b[1].y) + (b[2].y + b[3].y)) + ((b[4].y + b[5].y) + (b[6].y + b[7].y));
-        const float sz = ((b[0].z + b[1].z) + (b[2].z + b[3].z)) + ((b[4].z + b[5].z) + (b[6].z + b[7].z));
-        float t, yv;
-        yv = sx - cr; t = nr_ + yv; cr = (t - nr_) - yv; nr_ = t;
-        yv = sy - ci; t = ni_ + yv; ci = (t - ni_) - yv; ni_ = t;
-        yv = sz - cd; t = dd + yv; cd = (t - dd) - yv; dd = t;
+      for (int j = blockIdx.x * a.sl + threadIdx.x; j < pix1; j += CL_NT) {
+        const float4 sm4 = cl_pixel_sums(nd + j, ni, M);
+        const float Df = sm4.z;
+        const float2 Rv = make_float2(sm4.x / Df, sm4.y / Df);
+        bool clamped;
+        const float2 chi = chi_of_R_f(Rv, beta, d.q_min, &clamped);
+        __stcg(a.rc + j, make_float4(Rv.x, Rv.y, chi.x, chi.y));
+        __stcg(a.dsg + j, clamped ? -Df : Df);
       }
-      const float Df = dd - cd;
-      const float2 Rv = make_float2((nr_ - cr) / Df, (ni_ - ci) / Df);
-      bool clamped;
-      const float2 chi = chi_of_R_f(Rv, beta, d.q_min, &clamped);
-      Rh[i] = Rv;
-      Ch[i] = chi;
-      mgs[i] = sqrtf(cabs2(chi) + d.eps_abs);
-      if (hy >= 1 && hy <= RB) Dl[(hy - 1) * nx + x] = clamped ? -Df : Df;
+      cl_grid_barrier(a.bar, ((unsigned)it * 2u + 2u) * nblocks, a.err);
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+      for (int i0 = threadIdx.x; i0 < HP; i0 += 4 * CL_NT) {             // own rows + halo, four loads in flight
+        float4 v[4];
+        float dv[4];
+        bool ok[4], own[4];
+        int ix[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + u * CL_NT, hy = i / nx, x = i - hy * nx, y = y0 + hy - 1;
+          ok[u] = i < HP && y >= 0 && y < ny;
+          own[u] = ok[u] && hy >= 1 && hy <= RB;
+          ix[u] = y * nx + x;
+          v[u] = ok[u] ? __ldcg(a.rc + ix[u]) : z4;
+          dv[u] = own[u] ? __ldcg(a.dsg + ix[u]) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (ok[u]) {
+            const int i = i0 + u * CL_NT;
+            const float2 chi = make_float2(v[u].z, v[u].w);
+            Rh[i] = make_float2(v[u].x, v[u].y);
+            Ch[i] = chi;
+            mgs[i] = sqrtf(cabs2(chi) + d.eps_abs);
+            if (own[u]) Dl[i - nx] = dv[u];
+          }
+      }
+    } else {
+#pragma unroll 1
+      for (int i = threadIdx.x; i < HP; i += CL_NT) {
+        const int hy = i / nx, x = i - hy * nx, y = y0 + hy - 1;
+        if (y < 0 || y >= ny) continue;
+        const float4 sm4 = cl_pixel_sums(nd + (size_t)y * nx + x, ni, M);
+        const float Df = sm4.z;
+        const float2 Rv = make_float2(sm4.x / Df, sm4.y / Df);
+        bool clamped;
+        const float2 chi = chi_of_R_f(Rv, beta, d.q_min, &clamped);
+        Rh[i] = Rv;
+        Ch[i] = chi;
+        mgs[i] = sqrtf(cabs2(chi) + d.eps_abs);
+        if (hy >= 1 && hy <= RB) Dl[(hy - 1) * nx + x] = clamped ? -Df : Df;
+      }
     }
     __syncthreads();
     CL_STAMP(7);
@@ -428,21 +526,46 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     CL_STAMP(10);
     // ===== 5. column convolution with the conjugated spectrum, kept at the column owner =====
 #pragma unroll 1
-    for (int lc = warp; lc < CB; lc += CL_NW) {
-      const float2* g = ghs + lc * P;
-      Line<P> G, L;
+    for (int lc = warp; lc < CB; lc += 2 * CL_NW) {                    // columns lc and lc + NW together
+      const int lc2 = lc + CL_NW;
+      if (lc2 < CB) {
+        Line2<P> G, L;
 #pragma unroll
-      for (int kk = 0; kk < R; ++kk) G.v[kk] = cconj(g[kk * 32 + lane]);
+        for (int l = 0; l < 2; ++l) {
+          const int c = l ? lc2 : lc;
 #pragma unroll
-      for (int m = 0; m < R; ++m) {
-        const int y = lane + 32 * m;
-        L.v[m] = y < ny ? colb[lc * LS + y] : make_float2(0.f, 0.f);
-      }
-      L = line_conv<P>(L, G, tw, lane);
+          for (int kk = 0; kk < R; ++kk) G.v[l][kk] = cconj(ghs[c * P + kk * 32 + lane]);
 #pragma unroll
-      for (int m = 0; m < R; ++m) {
-        const int y = lane + 32 * m;
-        if (y < ny) colb[lc * LS + y] = L.v[m];                          // B = row-spectral G_D^H u, own columns
+          for (int m = 0; m < R; ++m) {
+            const int y = lane + 32 * m;
+            L.v[l][m] = y < ny ? colb[c * LS + y] : make_float2(0.f, 0.f);
+          }
+        }
+        L = line_conv2<P>(L, G, tw, lane);
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+          const int y = lane + 32 * m;
+          if (y < ny) {
+            colb[lc * LS + y] = L.v[0][m];                                // B = row-spectral G_D^H u, own columns
+            colb[lc2 * LS + y] = L.v[1][m];
+          }
+        }
+      } else {
+        const float2* g = ghs + lc * P;
+        Line<P> G, L;
+#pragma unroll
+        for (int kk = 0; kk < R; ++kk) G.v[kk] = cconj(g[kk * 32 + lane]);
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+          const int y = lane + 32 * m;
+          L.v[m] = y < ny ? colb[lc * LS + y] : make_float2(0.f, 0.f);
+        }
+        L = line_conv<P>(L, G, tw, lane);
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+          const int y = lane + 32 * m;
+          if (y < ny) colb[lc * LS + y] = L.v[m];
+        }
       }
     }
     __syncthreads();
@@ -658,15 +781,25 @@ pdf_status cl_run(pdf_problem* h, const pdf_solve_opts* o, int iters, cudaStream
   for (int i = 0; i < n && pick < 0; ++i)
     if (rows[i].usable) pick = i;
   if (pick < 0) return PDF_OK;
-  if (!h->cl_nd) {
-    pdf_status s;
-    if ((s = ws_alloc(h, (void**)&h->cl_nd, sizeof(float4) * 2 * (size_t)d.ni * d.M)) != PDF_OK) return s;
-  }
   ClusterArgs a;
   a.iters = iters;
   a.C = rows[pick].C;
   a.RB = d.ny / a.C;
   a.CB = d.Px / a.C;
+  // Sums over incidences: each CTA reads ni x (RB + 2) x nx float4 when it forms R-hat on its own
+  // rows, all CTAs at once, and the phase is bound by L2 bandwidth; the split form costs a second
+  // grid barrier and two more L2 round trips instead.  Measured on GB300 (per iteration): 32x32,
+  // Ni = 8, 8-CTA clusters (24 KB per CTA) 10.5 us per CTA vs 12.3 us split; 64x64, Ni = 16, 4-CTA
+  // clusters (295 KB) 31.6 vs 29.6 us; 64x64, Ni = 36 (663 KB) 35.6 vs 30.7 us.
+  const int nb = d.ni * a.C;
+  const size_t rep_bytes = (size_t)d.ni * (a.RB + 2) * d.nx * sizeof(float4);
+  a.sl = rep_bytes > 128 * 1024 ? (d.M + nb - 1) / nb : 0;
+  if ((uint64_t)iters * 2 * nb >= 0xffffffffull) return PDF_OK;  // barrier counter range
+  if (!h->cl_nd) {
+    pdf_status s;
+    const size_t bytes = sizeof(float4) * (2 * (size_t)d.ni + 1) * d.M + sizeof(float) * (size_t)d.M;
+    if ((s = ws_alloc(h, (void**)&h->cl_nd, bytes)) != PDF_OK) return s;
+  }
   a.alpha = h->alpha;
   a.tab = h->adam_tab;
   a.cap = h->adam_cap;
@@ -674,6 +807,8 @@ pdf_status cl_run(pdf_problem* h, const pdf_solve_opts* o, int iters, cudaStream
   a.b2 = (float)o->adam_b2;
   a.eps = (float)o->adam_eps;
   a.nd = h->cl_nd;
+  a.rc = h->cl_nd + 2 * (size_t)d.ni * d.M;
+  a.dsg = (float*)(a.rc + d.M);
   a.bar = h->bar;
   a.err = h->perr;
   PDF_CUDA(cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st));

@@ -167,6 +167,83 @@ template <int P> struct WarpFFT {
   }
 };
 
+// L independent lines per warp, transformed together: the butterflies of WarpFFT applied stage by
+// stage to every line, so the lines' shuffles and multiplies overlap (same results line by line).
+template <int P, int L> struct WarpFFTn {
+  static constexpr int R = P / 32;
+
+  static __device__ __forceinline__ void forward(float2 (&v)[L][R], const float2* __restrict__ tw, int lane) {
+#pragma unroll
+    for (int l = 0; l < L; ++l) SmallDFT<R, false>::run(v[l]);
+#pragma unroll
+    for (int k1 = 1; k1 < R; ++k1) {
+      const float2 w = tw[lane * k1];
+#pragma unroll
+      for (int l = 0; l < L; ++l) v[l][k1] = cmul(v[l][k1], w);
+    }
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+      const bool hi = lane & h;
+      const float s = hi ? -1.f : 1.f;
+      if (h > 1) {
+        const float2 wt = tw[(lane & (h - 1)) * (16 / h) * R];
+        const float2 w = hi ? wt : make_float2(1.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+          for (int l = 0; l < L; ++l) {
+            const float2 p = shfl_xor2(v[l][k], h);
+            v[l][k] = cmul(make_float2(fmaf(s, v[l][k].x, p.x), fmaf(s, v[l][k].y, p.y)), w);
+          }
+      } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+          for (int l = 0; l < L; ++l) {
+            const float2 p = shfl_xor2(v[l][k], h);
+            v[l][k] = make_float2(fmaf(s, v[l][k].x, p.x), fmaf(s, v[l][k].y, p.y));
+          }
+      }
+    }
+  }
+
+  static __device__ __forceinline__ void inverse(float2 (&v)[L][R], const float2* __restrict__ tw, int lane) {
+#pragma unroll
+    for (int h = 1; h <= 16; h <<= 1) {
+      const bool hi = lane & h;
+      const float s = hi ? -1.f : 1.f;
+      if (h > 1) {
+        const float2 wt = cconj(tw[(lane & (h - 1)) * (16 / h) * R]);
+        const float2 w = hi ? wt : make_float2(1.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+          for (int l = 0; l < L; ++l) {
+            const float2 t = cmul(v[l][k], w);
+            const float2 p = shfl_xor2(t, h);
+            v[l][k] = make_float2(fmaf(s, t.x, p.x), fmaf(s, t.y, p.y));
+          }
+      } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+          for (int l = 0; l < L; ++l) {
+            const float2 p = shfl_xor2(v[l][k], h);
+            v[l][k] = make_float2(fmaf(s, v[l][k].x, p.x), fmaf(s, v[l][k].y, p.y));
+          }
+      }
+    }
+#pragma unroll
+    for (int k1 = 1; k1 < R; ++k1) {
+      const float2 w = cconj(tw[lane * k1]);
+#pragma unroll
+      for (int l = 0; l < L; ++l) v[l][k1] = cmul(v[l][k1], w);
+    }
+#pragma unroll
+    for (int l = 0; l < L; ++l) SmallDFT<R, true>::run(v[l]);
+  }
+};
+
 // digit-reversal of the lane index (5 bits)
 __host__ __device__ __forceinline__ int brev5(int l) {
   return ((l & 1) << 4) | ((l & 2) << 2) | (l & 4) | ((l & 8) >> 2) | ((l & 16) >> 4);

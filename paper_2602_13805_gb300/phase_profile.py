@@ -22,7 +22,7 @@ PHASES = [
     "column convolution with the G_D spectrum -> row owners + cluster barrier",
     "inverse row DFT (G_D J)",
     "s and the per-incidence sums + grid barrier",
-    "R-hat, chi-hat from the sums over incidences (Eq. 6, 7)",
+    "R-hat, chi-hat from the sums over incidences (Eq. 6, 7; split over the grid: + grid barrier)",
     "TV / bridge pieces (Eq. 18, 19)",
     "residual, cotangent on chi, adjoint inputs u, v",
     "row DFT of u -> column owners + cluster barrier",

@@ -13,11 +13,13 @@
 //      incidences (when those sums are large, each CTA of the grid sums one slice of pixels and
 //      writes R-hat, chi-hat there, and the CTAs read their rows after a second GRID barrier);
 //      the TV / bridge pieces of Eq. 18-19 once per pixel; state residual (Eq. 15),
-//      regulariser cotangent -> w; adjoint inputs u, v; row DFT of u -> column owners    | cluster barrier
-//   5. column convolution with the conjugated spectrum (G_D^H), result kept at the column owner
-//   6. analysis (Phi^H) of dL/dJ = v + G_D^H u: the G_D^H u part as the column data times
-//      conj(what) (the x-analysis of an inverse row DFT) over its columns and all rows, v over
-//      its rows, then the y-analysis -> partial dL/d alpha_p to every CTA of the cluster | cluster barrier
+//      regulariser cotangent -> w; adjoint inputs u, v; row DFTs of u and v / Px -> column owners
+//                                                                                     | cluster barrier
+//   5. column convolution of u's data with the conjugated spectrum (G_D^H), plus v's data: the row
+//      spectrum of dL/dJ = v + G_D^H u, kept at the column owner
+//   6. analysis (Phi^H) of dL/dJ: the column data times conj(what) (the x-analysis of an inverse
+//      row DFT) over its columns and all rows, then the y-analysis -> partial dL/d alpha_p to
+//      every CTA of the cluster                                                        | cluster barrier
 //   7. dL/d alpha_p = sum of the partials (same order in every CTA), Adam step on each CTA's copy
 //      of alpha_p (identical in all CTAs of the cluster)
 // The data term goes through the folded operator G_S Phi, its receivers split over the cluster:
@@ -136,7 +138,7 @@ __device__ __noinline__ Line<P> line_conv(Line<P> x, Line<P> g, const float2* __
   return x;
 }
 
-// two columns convolved together (interleaved butterflies; used where a warp owns two columns)
+// two columns convolved together, or two lines transformed together (interleaved butterflies)
 template <int P> struct Line2 {
   float2 v[2][P / 32];
 };
@@ -149,6 +151,65 @@ __device__ __noinline__ Line2<P> line_conv2(Line2<P> x, Line2<P> g, const float2
     for (int k = 0; k < P / 32; ++k) x.v[l][k] = cmul(x.v[l][k], g.v[l][k]);
   WarpFFTn<P, 2>::inverse(x.v, tw, lane);
   return x;
+}
+template <int P>
+__device__ __noinline__ Line2<P> line_fwd2(Line2<P> x, const float2* __restrict__ tw, int lane) {
+  WarpFFTn<P, 2>::forward(x.v, tw, lane);
+  return x;
+}
+
+// Small complex product on shared-memory operands, C(m, n) = sum_k a(m, k) b(k, n), with
+// a(m, k) = A[m sam + k sak] and b(k, n) = B[k sbk + n sbn] (conjugated when CA / CB).  Each output
+// tile is held by KS adjacent lanes, lane s summing k = s, s + KS, ... in increasing k, and the KS
+// partial sums are added across the lanes.  A tile is TM x TN outputs in registers: rows
+// m = m0 + i tm, columns n = n0 + j tn (tm = ceil(M/TM), tn = ceil(N/TN)) for tile index
+// m0 tn + n0, so a warp reads few distinct m and consecutive n, and every loaded a(m, k) or b(k, n)
+// feeds TN or TM multiply-adds.  epi(m, n, value) receives each output once.
+template <int TM, int TN, int KS, bool CA, bool CB, class Epi>
+__device__ __forceinline__ void cl_cgemm(int M, int N, int K, const float2* __restrict__ A, int sam, int sak,
+                                         const float2* __restrict__ B, int sbk, int sbn, Epi epi) {
+  const int tm = (M + TM - 1) / TM, tn = (N + TN - 1) / TN, total = tm * tn * KS;
+#pragma unroll 1
+  for (int t0 = 0; t0 < total; t0 += CL_NT) {                         // same trip count in every warp
+    if (t0 + (int)(threadIdx.x & ~31u) >= total) break;                 // whole warp past the end
+    const int t = t0 + threadIdx.x, s = t % KS, tile = min(t / KS, tm * tn - 1);
+    const int m0 = tile / tn, n0 = tile - m0 * tn;
+    const float2* a[TM];
+    const float2* b[TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i) a[i] = A + min(m0 + i * tm, M - 1) * sam;   // clamped: computed, not kept
+#pragma unroll
+    for (int j = 0; j < TN; ++j) b[j] = B + min(n0 + j * tn, N - 1) * sbn;
+    float2 acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc[i][j] = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (int k = s; k < K; k += KS) {
+      float2 av[TM], bv[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) av[i] = CA ? cconj(a[i][k * sak]) : a[i][k * sak];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) bv[j] = CB ? cconj(b[j][k * sbk]) : b[j][k * sbk];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = acc[i][j] + cmul(av[i], bv[j]);
+    }
+#pragma unroll
+    for (int o = 1; o < KS; o <<= 1)
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = acc[i][j] + shfl_xor2(acc[i][j], o);
+    if (t < total && s == 0)
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j)
+          if (m0 + i * tm < M && n0 + j * tn < N) epi(m0 + i * tm, n0 + j * tn, acc[i][j]);
+  }
 }
 
 // Sums over the ni incidences of one pixel's contributions N = beta J conj(s), D = |s|^2 (stride
@@ -195,9 +256,17 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
   // ---- shared memory carve-up ----
   extern __shared__ float2 sm[];
   float2* tw = sm;                           // [P]
-  float2* rowb = tw + P;                     // [RB][P]
-  float2* colb = rowb + RB * P;              // [CB][LS]
-  float2* Js = colb + CB * LS;               // [GP]
+  // The two exchanges write into buffers laid out as the sender's warp holds the data, so that
+  // each warp's remote stores are contiguous: a column owner's warp holds one column (lanes along
+  // y) and writes into the row owners' rowT[c][yl]; a row owner's warp holds one row (lanes along
+  // c) and writes into the column owners' colT[y][lc].  Odd strides keep local reads of the other
+  // direction on distinct banks.
+  const int RS = RB + 1, SC = CB + 1;
+  float2* rowT = tw + P;                     // [P][RS] row spectra of own rows, column by column
+  float2* colb = rowT + P * RS;              // [CB][LS] row DFT of J at own columns (phases 1-2)
+  float2* colT = colb + CB * LS;             // [ny][SC] row DFT of u at own columns, then of dL/dJ (4-6)
+  float2* colV = colT + ny * SC;             // [ny][SC] row DFT of v / Px at own columns (4-5)
+  float2* Js = colV + ny * SC;               // [GP]
   float2* ss = Js + GP;                      // [GP] s
   float2* Es = ss + GP;                      // [GP]
   float2* vs = Es + GP;                      // [GP] v + G_S^H term
@@ -215,10 +284,9 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
   const int NRK = (nr - k + C - 1) / C;      // receivers r = k + C t owned by this CTA
   float2* rd = gpart + NU;                   // [NRK] data residual r_d,p at own receivers
   float2* es = rd + nr;                      // [NRK]
-  float2* T2 = es + nr;                      // [RB][kx] x-analysis of v on own rows
-  float2* Tall = T2 + RB * kx;               // [ny][kx] T' of all rows (phase 1), column-side x-analysis (phase 6)
+  float2* Tall = es + nr;                    // [ny][kx] T' of all rows (phase 1), x-analysis (phase 6)
   float2* wyf = Tall + ny * kx;              // [ky][ny] y basis
-  float2* whs = wyf + ky * ny;               // [kx][CB] row DFT of the x basis at this CTA's columns
+  float2* whs = wyf + ky * ny;               // [CB][kx] row DFT of the x basis at this CTA's columns
   float2* ghs = whs + kx * CB;               // [CB][P] this CTA's columns of the G_D spectrum
   float2* wxs = ghs + CB * P;                // [kx][nx] x basis
   float* am = (float*)(wxs + kx * nx);       // [2 NA]
@@ -242,7 +310,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
   for (int i = threadIdx.x; i < ky * ny; i += CL_NT) wyf[i] = d.wy[i];
 #pragma unroll 1
   for (int i = threadIdx.x; i < kx * CB; i += CL_NT) {
-    const int jx = i / CB, lc = i - jx * CB;
+    const int lc = i / kx, jx = i - lc * kx;
     whs[i] = d.what[(size_t)jx * P + c0 + lc];
   }
 #pragma unroll 1
@@ -263,16 +331,11 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     CL_STAMP(0);
     float4* nd = a.nd + (size_t)(it & 1) * ni * M;
     // ===== 1. synthesis (Eq. 9): T' of all rows, J on own rows, the padded row DFT of J on own columns =====
+    // T'[y][jx] = sum_jy Wy[jy][y] al[jy][jx] (low threads) while the top warps form r_d
+    cl_cgemm<2, 2, 1, false, false>(ny, kx, ky, wyf, 1, ny, al, kx, 1,
+                                 [&](int y, int jx, float2 v) { Tall[y * kx + jx] = v; });
 #pragma unroll 1
-    for (int i = threadIdx.x; i < ny * kx; i += CL_NT) {               // T'[y][jx] = sum_jy Wy[jy][y] al[jy][jx]
-      const int y = i / kx, jx = i - y * kx;
-      float2 acc = make_float2(0.f, 0.f);
-#pragma unroll 4
-      for (int jy = 0; jy < ky; ++jy) acc = acc + cmul(wyf[jy * ny + y], al[jy * kx + jx]);
-      Tall[i] = acc;
-    }
-#pragma unroll 1
-    for (int t = warp; t < NRK; t += CL_NW) {                            // r_d,p = (G_S Phi) alpha_p - E_sca,p, own receivers
+    for (int t = CL_NW - 1 - warp; t < NRK; t += CL_NW) {               // r_d,p = (G_S Phi) alpha_p - E_sca,p, own receivers
       float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 4
       for (int j = lane; j < NA; j += 32) acc = acc + cmul(gsf[t * NA + j], al[j]);
@@ -282,25 +345,11 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     }
     __syncthreads();
     CL_STAMP(1);
-#pragma unroll 1
-    for (int i = threadIdx.x; i < GP; i += CL_NT) {                    // J = T' Wx on own pixels
-      const int yl = i / nx, x = i - yl * nx;
-      const float2* tr = Tall + (y0 + yl) * kx;
-      float2 s = make_float2(0.f, 0.f);
-#pragma unroll 4
-      for (int jx = 0; jx < kx; ++jx) s = s + cmul(tr[jx], wxs[jx * nx + x]);
-      Js[i] = s;
-    }
+    cl_cgemm<2, 2, 1, false, false>(RB, nx, kx, Tall + y0 * kx, kx, 1, wxs, nx, 1,   // J = T' Wx on own pixels
+                                 [&](int yl, int x, float2 v) { Js[yl * nx + x] = v; });
     CL_STAMP(2);
-#pragma unroll 1
-    for (int i = threadIdx.x; i < CB * ny; i += CL_NT) {               // row DFT of J at own columns: T' what
-      const int lc = i / ny, y = i - lc * ny;
-      const float2* tr = Tall + y * kx;
-      float2 s = make_float2(0.f, 0.f);
-#pragma unroll 4
-      for (int jx = 0; jx < kx; ++jx) s = s + cmul(tr[jx], whs[jx * CB + lc]);
-      colb[lc * LS + y] = s;
-    }
+    cl_cgemm<2, 2, 1, false, false>(ny, CB, kx, Tall, kx, 1, whs, 1, kx,              // row DFT of J at own columns: T' what
+                                 [&](int y, int lc, float2 v) { colb[lc * LS + y] = v; });
     __syncthreads();
     CL_STAMP(3);
     // ===== 2. column convolution, results back to row owners =====
@@ -322,12 +371,12 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
         }
         L = line_conv2<P>(L, G, tw, lane);
 #pragma unroll
-        for (int m = 0; m < R; ++m) {
+        for (int m = 0; m < R; ++m) {                                    // to the row owners
           const int y = lane + 32 * m;
           if (y < ny) {
-            float2* dst = cl.map_shared_rank(rowb, y / RB) + (y % RB) * P + c0;
-            dst[lc] = L.v[0][m];
-            dst[lc2] = L.v[1][m];
+            float2* dst = cl.map_shared_rank(rowT, y / RB) + y % RB;
+            dst[(c0 + lc) * RS] = L.v[0][m];
+            dst[(c0 + lc2) * RS] = L.v[1][m];
           }
         }
       } else {
@@ -344,10 +393,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
 #pragma unroll
         for (int m = 0; m < R; ++m) {
           const int y = lane + 32 * m;
-          if (y < ny) {
-            float2* dst = cl.map_shared_rank(rowb, y / RB);
-            dst[(y % RB) * P + c0 + lc] = L.v[m];
-          }
+          if (y < ny) cl.map_shared_rank(rowT, y / RB)[(c0 + lc) * RS + y % RB] = L.v[m];
         }
       }
     }
@@ -358,12 +404,12 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     for (int yl = warp; yl < RB; yl += CL_NW) {
       Line<P> L;
 #pragma unroll
-      for (int kk = 0; kk < R; ++kk) L.v[kk] = rowb[yl * P + kk * 32 + lane];
+      for (int kk = 0; kk < R; ++kk) L.v[kk] = rowT[(kk * 32 + lane) * RS + yl];
       L = line_inv<P>(L, tw, lane);
 #pragma unroll
       for (int m = 0; m < R; ++m) {                                      // G_D J back in place (x < nx)
         const int x = lane + 32 * m;
-        if (x < nx) rowb[yl * P + x] = L.v[m];
+        if (x < nx) rowT[x * RS + yl] = L.v[m];
       }
     }
     __syncthreads();
@@ -372,7 +418,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     for (int i = threadIdx.x; i < GP; i += CL_NT) {
       const int yl = i / nx, x = i - yl * nx;
       const float2 J = Js[i];
-      const float2 s = cmul(beta, J) + Es[i] + rowb[yl * P + x];
+      const float2 s = cmul(beta, J) + Es[i] + rowT[x * RS + yl];
       ss[i] = s;
       const float2 n = cmul(beta, cmulc(J, s));
       __stcg(&nd[(size_t)p * M + y0 * nx + i], make_float4(n.x, n.y, cabs2(s), 0.f));
@@ -463,7 +509,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     }
     __syncthreads();
     CL_STAMP(8);
-    // state residual, cotangent on chi -> w, u (into rowb) and v + G_S^H r_d (into vs)
+    // state residual, cotangent on chi -> w, u (into rowT) and v (into vs)
 #pragma unroll 1
     for (int li = threadIdx.x; li < GP; li += CL_NT) {
       const int yl = li / nx, x = li - yl * nx, y = y0 + yl;
@@ -500,26 +546,28 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
       }
       const float2 wc = cconj(w);
       const float2 cs = cmul(cmul(wc, beta), J) - (2.f * cmul(wc, Rv).x) * s;
-      rowb[yl * P + x] = ke * cmulc(r, Rv) + cs;                         // u
+      rowT[x * RS + yl] = ke * cmulc(r, Rv) + cs;                        // u
       const float2 omr = make_float2(1.f - Rv.x, Rv.y);
       vs[li] = ke * cmul(cmul(make_float2(-bc.x, -bc.y), omr), r) + cmul(bc, cmul(w, s) + cs);   // v
     }
     __syncthreads();
     CL_STAMP(9);
 #pragma unroll 1
-    for (int yl = warp; yl < RB; yl += CL_NW) {                          // row DFT of u -> column owners
-      Line<P> L;
+    for (int yl = warp; yl < RB; yl += CL_NW) {                          // row DFTs of u and v / Px -> column owners
+      Line2<P> L;
+      const float sP = 1.f / (float)P;                                   // exact: P is a power of two
 #pragma unroll
       for (int m = 0; m < R; ++m) {
         const int x = lane + 32 * m;
-        L.v[m] = x < nx ? rowb[yl * P + x] : make_float2(0.f, 0.f);
+        L.v[0][m] = x < nx ? rowT[x * RS + yl] : make_float2(0.f, 0.f);
+        L.v[1][m] = x < nx ? sP * vs[yl * nx + x] : make_float2(0.f, 0.f);
       }
-      L = line_fwd<P>(L, tw, lane);
+      L = line_fwd2<P>(L, tw, lane);
 #pragma unroll
-      for (int kk = 0; kk < R; ++kk) {
-        const int c = kk * 32 + lane;
-        float2* dst = cl.map_shared_rank(colb, c / CB);
-        dst[(c % CB) * LS + y0 + yl] = L.v[kk];
+      for (int kk = 0; kk < R; ++kk) {                                   // to the column owners
+        const int c = kk * 32 + lane, o = (y0 + yl) * SC + c % CB;
+        cl.map_shared_rank(colT, c / CB)[o] = L.v[0][kk];
+        cl.map_shared_rank(colV, c / CB)[o] = L.v[1][kk];
       }
     }
     cl.sync();
@@ -538,16 +586,16 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
 #pragma unroll
           for (int m = 0; m < R; ++m) {
             const int y = lane + 32 * m;
-            L.v[l][m] = y < ny ? colb[c * LS + y] : make_float2(0.f, 0.f);
+            L.v[l][m] = y < ny ? colT[y * SC + c] : make_float2(0.f, 0.f);
           }
         }
         L = line_conv2<P>(L, G, tw, lane);
 #pragma unroll
         for (int m = 0; m < R; ++m) {
           const int y = lane + 32 * m;
-          if (y < ny) {
-            colb[lc * LS + y] = L.v[0][m];                                // B = row-spectral G_D^H u, own columns
-            colb[lc2 * LS + y] = L.v[1][m];
+          if (y < ny) {                                                   // row-spectral v + G_D^H u, own columns
+            colT[y * SC + lc] = L.v[0][m] + colV[y * SC + lc];
+            colT[y * SC + lc2] = L.v[1][m] + colV[y * SC + lc2];
           }
         }
       } else {
@@ -558,78 +606,38 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
 #pragma unroll
         for (int m = 0; m < R; ++m) {
           const int y = lane + 32 * m;
-          L.v[m] = y < ny ? colb[lc * LS + y] : make_float2(0.f, 0.f);
+          L.v[m] = y < ny ? colT[y * SC + lc] : make_float2(0.f, 0.f);
         }
         L = line_conv<P>(L, G, tw, lane);
 #pragma unroll
         for (int m = 0; m < R; ++m) {
           const int y = lane + 32 * m;
-          if (y < ny) colb[lc * LS + y] = L.v[m];
+          if (y < ny) colT[y * SC + lc] = L.v[m] + colV[y * SC + lc];
         }
       }
     }
     __syncthreads();
     CL_STAMP(11);
-    // ===== 6. analysis (Phi^H) of dL/dJ = v + G_D^H u, partial over this CTA's share =====
-    // G_D^H u = inverse row DFT of B, so its x-analysis is B conj(what) summed over the columns
-    // (each CTA: all rows, its columns); v is analysed over this CTA's rows.
-#pragma unroll 1
-    for (int i = threadIdx.x; i < ny * kx; i += CL_NT) {
-      const int jx = i / ny, y = i - jx * ny;                             // lanes along y: column reads contiguous
-      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-      int lc = 0;
-#pragma unroll 4
-      for (; lc + 1 < CB; lc += 2) {
-        a0 = a0 + cmulc(colb[lc * LS + y], whs[jx * CB + lc]);
-        a1 = a1 + cmulc(colb[(lc + 1) * LS + y], whs[jx * CB + lc + 1]);
-      }
-      if (lc < CB) a0 = a0 + cmulc(colb[lc * LS + y], whs[jx * CB + lc]);
-      Tall[y * kx + jx] = a0 + a1;
-    }
-#pragma unroll 1
-    for (int yl = warp; yl < RB; yl += CL_NW) {                          // x-analysis of v: warp per row
-      for (int j0 = 0; j0 < kx; j0 += 16) {
-        float2 acc[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) acc[j] = make_float2(0.f, 0.f);
-#pragma unroll 1
-        for (int x = lane; x < nx; x += 32) {
-          const float2 vv = vs[yl * nx + x];
-#pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (j0 + j < kx) acc[j] = acc[j] + cmulc(vv, wxs[(j0 + j) * nx + x]);
-        }
-        warp_reduce_scatter16(acc, lane);
-        const int jx = j0 + (lane >> 1);
-        if ((lane & 1) == 0 && jx < kx) T2[yl * kx + jx] = acc[0];
-      }
-    }
+    // ===== 6. analysis (Phi^H) of dL/dJ = v + G_D^H u, partial over this CTA's columns =====
+    // dL/dJ = inverse row DFT of B (B = the row-spectral v + G_D^H u at the column owners), so its
+    // x-analysis is B conj(what) summed over the columns (each CTA: all rows, its columns).
+    cl_cgemm<2, 2, 1, false, true>(ny, kx, CB, colT, SC, 1, whs, kx, 1,
+                                [&](int y, int jx, float2 v) { Tall[y * kx + jx] = v; });
     __syncthreads();
     CL_STAMP(12);
-#pragma unroll 1
-    for (int i = threadIdx.x; i < NA; i += CL_NT) {                     // analysis along y
-      const int jy = i / kx, jx = i - jy * kx;
-      const float2* wr = wyf + jy * ny;
-      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-      int y = 0;
-#pragma unroll 4
-      for (; y + 1 < ny; y += 2) {
-        a0 = a0 + cmulc(Tall[y * kx + jx], wr[y]);
-        a1 = a1 + cmulc(Tall[(y + 1) * kx + jx], wr[y + 1]);
-      }
-      if (y < ny) a0 = a0 + cmulc(Tall[y * kx + jx], wr[y]);
-#pragma unroll 4
-      for (int yl = 0; yl < RB; ++yl) a1 = a1 + cmulc(T2[yl * kx + jx], wr[y0 + yl]);
-      float2 gd = make_float2(0.f, 0.f);                                 // data term (Eq. 16), own receivers
+    // analysis along y, plus the data term (Eq. 16) at own receivers; to every CTA
+    cl_cgemm<1, 2, 1, true, false>(ky, kx, ny, wyf, ny, 1, Tall, kx, 1, [&](int jy, int jx, float2 v) {
+      const int i = jy * kx + jx;
+      float2 gd = make_float2(0.f, 0.f);
 #pragma unroll 4
       for (int t = 0; t < NRK; ++t) gd = gd + cmulc(rd[t], gsf[t * NA + i]);
-      const float2 acc = (a0 + a1) + ks * gd;
+      const float2 acc = v + ks * gd;
 #pragma unroll 1
       for (int q = 0; q < C; ++q) {
         float2* dst = cl.map_shared_rank(gpart, q);
         dst[k * NA + i] = acc;
       }
-    }
+    });
     cl.sync();
     CL_STAMP(13);
     // ===== 7. gradient and Adam step on this CTA's copy of alpha_p =====
@@ -660,8 +668,9 @@ static size_t cluster_smem(const Dev& d, int C, int RB, int CB, int P) {
                TP = (size_t)(RB + 1) * d.nx;
   const size_t nscr = 2 * GP + HP + 2 * TP;
   const size_t NU = std::max((size_t)C * NA, (nscr + 1) / 2);
-  const size_t f2 = P + (size_t)RB * P + (size_t)CB * (d.ny + 1) + 4 * GP + 2 * HP + NA + NU + 2 * (size_t)d.nr +
-                    (size_t)RB * d.kx + (size_t)d.ny * d.kx + (size_t)d.ky * d.ny + (size_t)d.kx * CB +
+  const size_t f2 = P + (size_t)P * (RB + 1) + (size_t)CB * (d.ny + 1) + 2 * (size_t)d.ny * (CB + 1) + 4 * GP + 2 * HP +
+                    NA + NU + 2 * (size_t)d.nr +
+                    (size_t)d.ny * d.kx + (size_t)d.ky * d.ny + (size_t)d.kx * CB +
                     (size_t)CB * P + (size_t)d.kx * d.nx + (size_t)((d.nr + C - 1) / C) * NA;
   return f2 * sizeof(float2) + 4 * NA * sizeof(float);
 }

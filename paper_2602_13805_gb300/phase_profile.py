@@ -25,9 +25,9 @@ PHASES = [
     "R-hat, chi-hat from the sums over incidences (Eq. 6, 7; split over the grid: + grid barrier)",
     "TV / bridge pieces (Eq. 18, 19)",
     "residual, cotangent on chi, adjoint inputs u, v",
-    "row DFT of u -> column owners + cluster barrier",
-    "column convolution with the conjugated spectrum (kept local)",
-    "x-analysis: column data x conj(what), v on own rows",
+    "row DFTs of u and v -> column owners + cluster barrier",
+    "column convolution with the conjugated spectrum, + v (kept local)",
+    "x-analysis: column data x conj(what)",
     "y-analysis partials -> all CTAs + cluster barrier",
     "gradient sum + (G_S Phi)^H r_d + Adam step",
 ]

@@ -52,7 +52,7 @@ struct ClusterArgs {
   float4* nd;             // [2][ni][M] per-incidence (Re N, Im N, D, unused)
   float4* rc;             // [M] (R-hat, chi-hat) when the sums are split over the grid
   float* dsg;             // [M] D, sign = clamp flag, likewise
-  int sl;                 // pixels per CTA slice (0: every CTA sums its own rows)
+  int sl, sg;             // pixels per CTA slice (0: every CTA sums its own rows), lanes per pixel
   unsigned* bar;
   int* err;               // 1: a grid barrier timed out; 2: launched with the wrong cluster shape
 };
@@ -428,19 +428,38 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     CL_STAMP(6);
     // ===== 4. R-hat, chi-hat (own rows + halo), residuals, regulariser cotangent, adjoint inputs =====
     if (a.sl > 0) {
-      // Sums over incidences split over the grid: CTA b sums pixels [b sl, (b+1) sl) (a thread per
-      // pixel, as below) and writes R-hat, chi-hat and the signed D there; after a second grid
-      // barrier every CTA reads its rows + halo.  Same arithmetic as the per-CTA form.
-      const int pix1 = min((int)blockIdx.x * a.sl + a.sl, M);
+      // Sums over incidences split over the grid: CTA b sums pixels [b sl, (b+1) sl), each pixel
+      // over sg adjacent lanes (lane g: incidences 8g .. 8g+7, all loads in flight at once, pairwise
+      // sum) whose partial sums are added in float-float across the lanes, and writes R-hat,
+      // chi-hat and the signed D there; after a second grid barrier every CTA reads its rows + halo.
+      const int G = a.sg, gl = threadIdx.x & (G - 1), pix0 = blockIdx.x * a.sl;
+      const int pix1 = min(pix0 + a.sl, M);
 #pragma unroll 1
-      for (int j = blockIdx.x * a.sl + threadIdx.x; j < pix1; j += CL_NT) {
-        const float4 sm4 = cl_pixel_sums(nd + j, ni, M);
-        const float Df = sm4.z;
-        const float2 Rv = make_float2(sm4.x / Df, sm4.y / Df);
-        bool clamped;
-        const float2 chi = chi_of_R_f(Rv, beta, d.q_min, &clamped);
-        __stcg(a.rc + j, make_float4(Rv.x, Rv.y, chi.x, chi.y));
-        __stcg(a.dsg + j, clamped ? -Df : Df);
+      for (int j0 = pix0; j0 < pix1; j0 += CL_NT / G) {
+        if (j0 + (int)(threadIdx.x & ~31u) / G >= pix1) break;           // whole warp past the end
+        const int j = j0 + (int)threadIdx.x / G;
+        const bool on = j < pix1;
+        float4 b[8];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          const int q = gl * 8 + jj;
+          b[jj] = on && q < ni ? __ldcg(nd + (size_t)q * M + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        FF f[3] = {ff_make(((b[0].x + b[1].x) + (b[2].x + b[3].x)) + ((b[4].x + b[5].x) + (b[6].x + b[7].x))),
+                   ff_make(((b[0].y + b[1].y) + (b[2].y + b[3].y)) + ((b[4].y + b[5].y) + (b[6].y + b[7].y))),
+                   ff_make(((b[0].z + b[1].z) + (b[2].z + b[3].z)) + ((b[4].z + b[5].z) + (b[6].z + b[7].z)))};
+#pragma unroll 1
+        for (int o = 1; o < G; o <<= 1)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) f[c] = ff_add(f[c], ff_shfl_xor(f[c], o));
+        if (on && gl == 0) {
+          const float Df = f[2].hi + f[2].lo;
+          const float2 Rv = make_float2((f[0].hi + f[0].lo) / Df, (f[1].hi + f[1].lo) / Df);
+          bool clamped;
+          const float2 chi = chi_of_R_f(Rv, beta, d.q_min, &clamped);
+          __stcg(a.rc + j, make_float4(Rv.x, Rv.y, chi.x, chi.y));
+          __stcg(a.dsg + j, clamped ? -Df : Df);
+        }
       }
       cl_grid_barrier(a.bar, ((unsigned)it * 2u + 2u) * nblocks, a.err);
       const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -803,6 +822,8 @@ pdf_status cl_run(pdf_problem* h, const pdf_solve_opts* o, int iters, cudaStream
   const int nb = d.ni * a.C;
   const size_t rep_bytes = (size_t)d.ni * (a.RB + 2) * d.nx * sizeof(float4);
   a.sl = rep_bytes > 128 * 1024 ? (d.M + nb - 1) / nb : 0;
+  for (a.sg = 1; 8 * a.sg < d.ni; a.sg *= 2) {
+  }
   if ((uint64_t)iters * 2 * nb >= 0xffffffffull) return PDF_OK;  // barrier counter range
   if (!h->cl_nd) {
     pdf_status s;

@@ -331,6 +331,8 @@ def run_ours(args, rank, world, local):
             "gpu_launches": int(launches),
             "roofline": roofline,
             "loop_mode": rep.loop_mode,
+            "cluster_size": next((r[0] for r in pdf.pdf_cluster_plan(prob.h) if r[3]), None)
+            if rep.loop_mode == 3 else None,
             "kernels_ms": {n: round(t, 5) for n, t in prof},
             "loss_grad_ms": per_iter_ms,
             "kernels_note": "kernels_ms / loss_grad_ms: one loss-and-gradient evaluation by the stand-alone "

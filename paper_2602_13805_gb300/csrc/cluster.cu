@@ -69,10 +69,13 @@ __device__ __forceinline__ int cl_ld_relaxed(const int* p) {
 }
 
 // Grid-wide barrier on a monotonic counter: thread 0 adds one with release semantics and polls
-// with acquire loads; bar.sync on both sides extends the ordering to the whole CTA.  Bounded:
+// with acquire loads; bar.sync on both sides extends the ordering to the whole CTA.  Warps 1.. run
+// idle_work (work that needs nothing from other CTAs) meanwhile.  Bounded:
 // after ~2^31 cycles, or once any CTA has flagged a timeout, it stops waiting.
-__device__ __forceinline__ void cl_grid_barrier(unsigned* bar, unsigned target, int* err) {
+template <class F>
+__device__ __forceinline__ void cl_grid_barrier(unsigned* bar, unsigned target, int* err, F&& idle_work) {
   __syncthreads();
+  if (threadIdx.x >= 32) idle_work();                                  // warps 1.. while thread 0 waits
   if (threadIdx.x == 0) {
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" : : "l"(bar) : "memory");
     if (cl_ld_relaxed(err) == 0) {
@@ -118,23 +121,31 @@ __device__ unsigned long long g_cl_stamps[4][16];
 template <int P> struct Line {
   float2 v[P / 32];
 };
+// Every padded length here satisfies P >= 2n, so register slots m >= R/2 (points P/2 .. P-1) are
+// zero on input and unused on output; stating that as constants lets the compiler drop that part
+// of the first and last small DFTs.
 template <int P>
-__device__ __noinline__ Line<P> line_fwd(Line<P> x, const float2* __restrict__ tw, int lane) {
-  WarpFFT<P>::forward(x.v, tw, lane);
-  return x;
+__device__ __forceinline__ void zero_upper(float2 (&v)[P / 32]) {
+#pragma unroll
+  for (int m = P / 64; m < P / 32; ++m) v[m] = make_float2(0.f, 0.f);
 }
+// inverse transform of a line whose outputs are used for n <= P/2 points only
 template <int P>
 __device__ __noinline__ Line<P> line_inv(Line<P> x, const float2* __restrict__ tw, int lane) {
   WarpFFT<P>::inverse(x.v, tw, lane);
+  zero_upper<P>(x.v);
   return x;
 }
-// circular convolution of the line with the spectrum g (stored in the forward transform's order)
+// circular convolution of a padded line (n <= P/2 points in and out) with the spectrum g (stored in
+// the forward transform's order)
 template <int P>
 __device__ __noinline__ Line<P> line_conv(Line<P> x, Line<P> g, const float2* __restrict__ tw, int lane) {
+  zero_upper<P>(x.v);
   WarpFFT<P>::forward(x.v, tw, lane);
 #pragma unroll
   for (int k = 0; k < P / 32; ++k) x.v[k] = cmul(x.v[k], g.v[k]);
   WarpFFT<P>::inverse(x.v, tw, lane);
+  zero_upper<P>(x.v);
   return x;
 }
 
@@ -144,16 +155,23 @@ template <int P> struct Line2 {
 };
 template <int P>
 __device__ __noinline__ Line2<P> line_conv2(Line2<P> x, Line2<P> g, const float2* __restrict__ tw, int lane) {
+  zero_upper<P>(x.v[0]);
+  zero_upper<P>(x.v[1]);
   WarpFFTn<P, 2>::forward(x.v, tw, lane);
 #pragma unroll
   for (int l = 0; l < 2; ++l)
 #pragma unroll
     for (int k = 0; k < P / 32; ++k) x.v[l][k] = cmul(x.v[l][k], g.v[l][k]);
   WarpFFTn<P, 2>::inverse(x.v, tw, lane);
+  zero_upper<P>(x.v[0]);
+  zero_upper<P>(x.v[1]);
   return x;
 }
+// forward transforms of two padded lines (n <= P/2 points in)
 template <int P>
 __device__ __noinline__ Line2<P> line_fwd2(Line2<P> x, const float2* __restrict__ tw, int lane) {
+  zero_upper<P>(x.v[0]);
+  zero_upper<P>(x.v[1]);
   WarpFFTn<P, 2>::forward(x.v, tw, lane);
   return x;
 }
@@ -289,7 +307,8 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
   float2* whs = wyf + ky * ny;               // [CB][kx] row DFT of the x basis at this CTA's columns
   float2* ghs = whs + kx * CB;               // [CB][P] this CTA's columns of the G_D spectrum
   float2* wxs = ghs + CB * P;                // [kx][nx] x basis
-  float* am = (float*)(wxs + kx * nx);       // [2 NA]
+  float2* gdv = wxs + kx * nx;               // [NA] (G_S Phi)^H r_d at own receivers
+  float* am = (float*)(gdv + NA);            // [2 NA]
   float* av = am + 2 * NA;                   // [2 NA]
   float2* gsf = (float2*)(av + 2 * NA);      // [NRK][NA] folded receiver operator, own receivers
 
@@ -424,7 +443,15 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
       __stcg(&nd[(size_t)p * M + y0 * nx + i], make_float4(n.x, n.y, cabs2(s), 0.f));
     }
     const unsigned nbar = a.sl > 0 ? 2u : 1u;                           // grid barriers per iteration
-    cl_grid_barrier(a.bar, ((unsigned)it * nbar + 1u) * nblocks, a.err);
+    cl_grid_barrier(a.bar, ((unsigned)it * nbar + 1u) * nblocks, a.err, [&] {
+#pragma unroll 1
+      for (int i = threadIdx.x - 32; i < NA; i += CL_NT - 32) {            // (G_S Phi)^H r_d, own receivers (Eq. 16)
+        float2 g = make_float2(0.f, 0.f);
+#pragma unroll 4
+        for (int t = 0; t < NRK; ++t) g = g + cmulc(rd[t], gsf[t * NA + i]);
+        gdv[i] = g;
+      }
+    });
     CL_STAMP(6);
     // ===== 4. R-hat, chi-hat (own rows + halo), residuals, regulariser cotangent, adjoint inputs =====
     if (a.sl > 0) {
@@ -461,7 +488,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
           __stcg(a.dsg + j, clamped ? -Df : Df);
         }
       }
-      cl_grid_barrier(a.bar, ((unsigned)it * 2u + 2u) * nblocks, a.err);
+      cl_grid_barrier(a.bar, ((unsigned)it * 2u + 2u) * nblocks, a.err, [] {});
       const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 1
       for (int i0 = threadIdx.x; i0 < HP; i0 += 4 * CL_NT) {             // own rows + halo, four loads in flight
@@ -644,13 +671,11 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
                                 [&](int y, int jx, float2 v) { Tall[y * kx + jx] = v; });
     __syncthreads();
     CL_STAMP(12);
-    // analysis along y, plus the data term (Eq. 16) at own receivers; to every CTA
+    // analysis along y, plus the data term (Eq. 16) at own receivers (formed during the grid
+    // barrier); to every CTA
     cl_cgemm<1, 2, 1, true, false>(ky, kx, ny, wyf, ny, 1, Tall, kx, 1, [&](int jy, int jx, float2 v) {
       const int i = jy * kx + jx;
-      float2 gd = make_float2(0.f, 0.f);
-#pragma unroll 4
-      for (int t = 0; t < NRK; ++t) gd = gd + cmulc(rd[t], gsf[t * NA + i]);
-      const float2 acc = v + ks * gd;
+      const float2 acc = v + ks * gdv[i];
 #pragma unroll 1
       for (int q = 0; q < C; ++q) {
         float2* dst = cl.map_shared_rank(gpart, q);
@@ -690,7 +715,7 @@ static size_t cluster_smem(const Dev& d, int C, int RB, int CB, int P) {
   const size_t f2 = P + (size_t)P * (RB + 1) + (size_t)CB * (d.ny + 1) + 2 * (size_t)d.ny * (CB + 1) + 4 * GP + 2 * HP +
                     NA + NU + 2 * (size_t)d.nr +
                     (size_t)d.ny * d.kx + (size_t)d.ky * d.ny + (size_t)d.kx * CB +
-                    (size_t)CB * P + (size_t)d.kx * d.nx + (size_t)((d.nr + C - 1) / C) * NA;
+                    (size_t)CB * P + (size_t)d.kx * d.nx + NA + (size_t)((d.nr + C - 1) / C) * NA;
   return f2 * sizeof(float2) + 4 * NA * sizeof(float);
 }
 

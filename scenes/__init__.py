@@ -217,6 +217,20 @@ def snr_db_to_nu(snr_db: float) -> float:
     return 10.0 ** (-snr_db / 20.0)
 
 
+def fcnn_params(ky: int, kx: int, hidden: int, seed: int) -> np.ndarray:
+    """Initial weights of the coefficient-correcting network, float32, flat in the order
+    W1 [H][D], b1 [H], W2 [H][H], b2 [H], W3 [D][H], b3 [D] with D = 2 ky kx: the hidden layers
+    uniform in +-1/sqrt(fan_in) (the common default for linear layers), the output layer zero so the
+    first iterate is alpha_(0) itself.  Seeded input data for both implementations."""
+    D, H = 2 * ky * kx, hidden
+    rng = np.random.default_rng(seed)
+    b_in, b_h = 1.0 / np.sqrt(D), 1.0 / np.sqrt(H)
+    parts = [rng.uniform(-b_in, b_in, H * D), rng.uniform(-b_in, b_in, H),
+             rng.uniform(-b_h, b_h, H * H), rng.uniform(-b_h, b_h, H),
+             np.zeros(D * H), np.zeros(D)]
+    return np.concatenate(parts).astype(np.float32)
+
+
 def random_coeffs(ni: int, ky: int, kx: int, scale: float, rng: np.random.Generator) -> np.ndarray:
     """i.i.d. complex Gaussian coefficient array [ni][ky][kx] complex128."""
     return scale * (rng.standard_normal((ni, ky, kx)) + 1j * rng.standard_normal((ni, ky, kx)))

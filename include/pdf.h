@@ -138,6 +138,18 @@ typedef struct pdf_solve_opts {
                                 6 loss terms, RelErr of chi-hat and of its CCO image (NaN-free
                                 only with chi_true; the loop then runs without a CUDA graph)    */
   double* history;           /* device [ceil(iters / history_every)][8] when history_every > 0 */
+  /* Coefficient-correcting network (Sec. 3, network architecture; training settings): with
+   * fcnn_hidden = H > 0 the solve optimises the weights theta of a fully connected network that maps
+   * each incidence's initial coefficients to a correction, alpha = alpha_(0) + Delta alpha(theta),
+   * with Adam (lr, betas, eps above) on theta instead of on alpha.  Per incidence p the input is
+   * x_p = s [Re alpha_(0),p, Im alpha_(0),p] (D = 2 ky kx reals, s = 1 / RMS of alpha_(0)'s real
+   * components), two hidden layers of width H with ReLU, a linear output y_p of D reals, and
+   * Delta alpha_p = (y_p[0 .. ky kx) + i y_p[ky kx .. D)) / s; one network for all incidences.
+   * fcnn_params0: device float32, caller-owned, read at the start of the solve: W1 [H][D], b1 [H],
+   * W2 [H][H], b2 [H], W3 [D][H], b3 [D], row-major, concatenated.  1 <= H <= 4096.  The loop runs
+   * as the CUDA graph (use_graph 1..3) or one launch per kernel (0); alpha_out receives alpha-hat. */
+  int32_t fcnn_hidden;       /* 0 = off (Adam on alpha) */
+  const void* fcnn_params0;
 } pdf_solve_opts;
 
 typedef struct pdf_solve_report {

@@ -683,6 +683,8 @@ extern "C" pdf_status pdf_solve(pdf_problem* h, const pdf_solve_opts* o, void* c
   if (o->init < 0 || o->init > 3) return set_err(PDF_EINVAL, "init must be 0, 1, 2 or 3");
   if (o->init == 3 && !o->alpha0) return set_err(PDF_EINVAL, "init == 3 needs alpha0");
   if (o->history_every > 0 && !o->history) return set_err(PDF_EINVAL, "history_every > 0 needs history");
+  if (o->fcnn_hidden < 0 || o->fcnn_hidden > 4096) return set_err(PDF_EINVAL, "fcnn_hidden must be in [0, 4096]");
+  if (o->fcnn_hidden > 0 && !o->fcnn_params0) return set_err(PDF_EINVAL, "fcnn_hidden > 0 needs fcnn_params0");
   if (o->apply_cco && (o->cco_radius < 0 || o->cco_radius > 16 || o->cco_eps <= 0))
     return set_err(PDF_EINVAL, "cco_radius must be in [0, 16] and cco_eps > 0");
   return sv_solve(h, o, (float2*)chi_out, (float2*)chi_raw_out, (float2*)alpha_out, rep, (cudaStream_t)stream);

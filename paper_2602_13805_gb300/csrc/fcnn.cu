@@ -1,0 +1,228 @@
+// Coefficient-correcting network of the solve (Sec. 3, network architecture; training settings).
+//
+// The solver's variable is the weight vector theta of a fully connected network that maps each
+// incidence's initial Fourier coefficients (real and imaginary parts as two channels) to a
+// correction: alpha-hat = alpha_(0) + Delta alpha(theta); Adam acts on theta.  The paper does not
+// print the architecture; the form built here (also in include/pdf.h): one network for all
+// incidences, input x_p = s [Re alpha_(0),p, Im alpha_(0),p] (D = 2 ky kx, s = 1 / RMS of
+// alpha_(0)'s real components), two hidden layers of width H with ReLU, a linear output y_p of D
+// reals, Delta alpha_p = (y_p[:ky kx] + i y_p[ky kx:]) / s.  The chain rule to theta takes the
+// loss gradient g = dL/dRe alpha + i dL/dIm alpha as dL/dy_p = [Re g_p, Im g_p] / s.
+//
+// All products are FP32 with FP32 accumulation in increasing k order, on a 32 x 32 output tile per
+// 256-thread block staged through shared memory (the batch is ni <= 64 rows, so these are small,
+// latency-bound products next to the loss gradient's FFTs).
+#include "problem.cuh"
+
+constexpr int FCT = 32;   // output tile side and k chunk
+
+// C(m, n) = sum_k A(m, k) B(k, n) for m < M, n < N, with A(m, k) = TA ? A[k lda + m] : A[m lda + k]
+// and B(k, n) = TB ? B[n ldb + k] : B[k ldb + n].  Epilogue EPI: 0 store; 1 add bias[n], ReLU;
+// 2 add bias[n]; 3 multiply by (mask[m ldc + n] > 0), the ReLU derivative of a stored activation.
+template <bool TA, bool TB, int EPI>
+__global__ void __launch_bounds__(256) k_fc_gemm(const float* __restrict__ A, int lda, const float* __restrict__ B,
+                                                 int ldb, float* __restrict__ C, int ldc, int M, int N, int K,
+                                                 const float* __restrict__ bias, const float* __restrict__ mask) {
+  __shared__ float As[FCT][FCT + 1];   // [m][k]
+  __shared__ float Bs[FCT][FCT + 1];   // [k][n]
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m0 = blockIdx.y * FCT, n0 = blockIdx.x * FCT;
+  float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  for (int k0 = 0; k0 < K; k0 += FCT) {
+    for (int e = threadIdx.x; e < FCT * FCT; e += blockDim.x) {
+      const int a = e / FCT, b = e - a * FCT;                            // b runs along the contiguous index
+      if (TA) {
+        const int m = m0 + b, k = k0 + a;
+        As[b][a] = (m < M && k < K) ? A[(size_t)k * lda + m] : 0.f;
+      } else {
+        const int m = m0 + a, k = k0 + b;
+        As[a][b] = (m < M && k < K) ? A[(size_t)m * lda + k] : 0.f;
+      }
+      if (TB) {
+        const int k = k0 + b, n = n0 + a;
+        Bs[b][a] = (k < K && n < N) ? B[(size_t)n * ldb + k] : 0.f;
+      } else {
+        const int k = k0 + a, n = n0 + b;
+        Bs[a][b] = (k < K && n < N) ? B[(size_t)k * ldb + n] : 0.f;
+      }
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < FCT; ++kk) {
+      const float a0 = As[ty][kk], a1 = As[ty + 16][kk];
+      const float b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+      acc[0][0] = fmaf(a0, b0, acc[0][0]);
+      acc[0][1] = fmaf(a0, b1, acc[0][1]);
+      acc[1][0] = fmaf(a1, b0, acc[1][0]);
+      acc[1][1] = fmaf(a1, b1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+      if (m >= M || n >= N) continue;
+      float v = acc[i][j];
+      if (EPI == 1) v = fmaxf(v + bias[n], 0.f);
+      if (EPI == 2) v = v + bias[n];
+      if (EPI == 3) v = mask[(size_t)m * ldc + n] > 0.f ? v : 0.f;
+      C[(size_t)m * ldc + n] = v;
+    }
+}
+
+// out[c] = sum over r (increasing) of A[r cols + c]: bias gradients
+__global__ void k_fc_colsum(const float* __restrict__ A, int rows, int cols, float* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  float s = 0.f;
+  for (int r = 0; r < rows; ++r) s += A[(size_t)r * cols + c];
+  out[c] = s;
+}
+
+// X = s [Re alpha0, Im alpha0] per incidence, s = 1 / RMS of the real components (one block)
+__global__ void k_fc_input(const float2* __restrict__ a0, int ni, int k2, float* __restrict__ X,
+                           float* __restrict__ s_out) {
+  __shared__ double red[32];
+  __shared__ float s_sh;
+  double acc = 0.0;
+  const int n = ni * k2;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float2 v = a0[i];
+    acc += (double)v.x * v.x + (double)v.y * v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) tot += red[w];
+    const double ms = tot / (2.0 * n);
+    s_sh = ms > 0.0 ? (float)(1.0 / sqrt(ms)) : 1.f;                   // all-zero start: unscaled
+    s_out[0] = s_sh;
+  }
+  __syncthreads();
+  const float s = s_sh;
+  const int D = 2 * k2;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int b = i / k2, j = i - b * k2;
+    const float2 v = a0[i];
+    X[(size_t)b * D + j] = s * v.x;
+    X[(size_t)b * D + k2 + j] = s * v.y;
+  }
+}
+
+// alpha = alpha0 + (y[:k2] + i y[k2:]) / s
+__global__ void k_fc_alpha(const float2* __restrict__ a0, const float* __restrict__ y, const float* __restrict__ s,
+                           int ni, int k2, float2* __restrict__ alpha) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ni * k2) return;
+  const int b = i / k2, j = i - b * k2, D = 2 * k2;
+  const float sc = s[0];
+  const float2 v = a0[i];
+  alpha[i] = make_float2(v.x + y[(size_t)b * D + j] / sc, v.y + y[(size_t)b * D + k2 + j] / sc);
+}
+
+// dL/dy = [Re g, Im g] / s
+__global__ void k_fc_dy(const float2* __restrict__ g, const float* __restrict__ s, int ni, int k2,
+                        float* __restrict__ dY) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ni * k2) return;
+  const int b = i / k2, j = i - b * k2, D = 2 * k2;
+  const float sc = s[0];
+  const float2 v = g[i];
+  dY[(size_t)b * D + j] = v.x / sc;
+  dY[(size_t)b * D + k2 + j] = v.y / sc;
+}
+
+template <bool TA, bool TB, int EPI>
+static void gemm(const float* A, int lda, const float* B, int ldb, float* C, int ldc, int M, int N, int K,
+                 const float* bias, const float* mask, cudaStream_t st) {
+  const dim3 grid((N + FCT - 1) / FCT, (M + FCT - 1) / FCT);
+  k_fc_gemm<TA, TB, EPI><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, M, N, K, bias, mask);
+}
+
+// parameter offsets in the flat vector
+struct FcOff {
+  size_t W1, b1, W2, b2, W3, b3;
+};
+static FcOff fc_off(int D, int H) {
+  FcOff o;
+  o.W1 = 0;
+  o.b1 = (size_t)H * D;
+  o.W2 = o.b1 + H;
+  o.b2 = o.W2 + (size_t)H * H;
+  o.W3 = o.b2 + H;
+  o.b3 = o.W3 + (size_t)D * H;
+  return o;
+}
+
+pdf_status fc_prepare(pdf_problem* h, int hidden, const void* params0, cudaStream_t st) {
+  FcState& f = h->fc;
+  const Dev& d = h->d;
+  const int D = 2 * d.ky * d.kx, B = d.ni, H = hidden;
+  const size_t np = (size_t)H * D + H + (size_t)H * H + H + (size_t)D * H + D;
+  if (f.H != H || f.D != D || f.B != B) {                              // (re)allocate; old blocks stay owned
+    pdf_status s;
+    void** bufs[] = {(void**)&f.theta, (void**)&f.gtheta, (void**)&f.m, (void**)&f.v};
+    for (void** b : bufs)
+      if ((s = ws_alloc(h, b, sizeof(float) * np)) != PDF_OK) return s;
+    if ((s = ws_alloc(h, (void**)&f.X, sizeof(float) * B * D)) != PDF_OK) return s;
+    if ((s = ws_alloc(h, (void**)&f.y, sizeof(float) * B * D)) != PDF_OK) return s;
+    if ((s = ws_alloc(h, (void**)&f.s, sizeof(float))) != PDF_OK) return s;
+    float** hb[] = {&f.h1, &f.h2, &f.dz1, &f.dz2};
+    for (float** b : hb)
+      if ((s = ws_alloc(h, (void**)b, sizeof(float) * B * H)) != PDF_OK) return s;
+    if ((s = ws_alloc(h, (void**)&f.alpha0, sizeof(float2) * d.ni * d.ky * d.kx)) != PDF_OK) return s;
+    f.H = H;
+    f.D = D;
+    f.B = B;
+    f.np = np;
+  }
+  PDF_CUDA(cudaMemcpyAsync(f.theta, params0, sizeof(float) * np, cudaMemcpyDeviceToDevice, st));
+  PDF_CUDA(cudaMemsetAsync(f.m, 0, sizeof(float) * np, st));
+  PDF_CUDA(cudaMemsetAsync(f.v, 0, sizeof(float) * np, st));
+  PDF_CUDA(cudaMemcpyAsync(f.alpha0, h->alpha, sizeof(float2) * d.ni * d.ky * d.kx, cudaMemcpyDeviceToDevice, st));
+  k_fc_input<<<1, 1024, 0, st>>>(f.alpha0, d.ni, d.ky * d.kx, f.X, f.s);
+  pdf_count_launch(1);
+  PDF_LAUNCHED("network input");
+  return PDF_OK;
+}
+
+pdf_status fc_forward(pdf_problem* h, cudaStream_t st) {
+  FcState& f = h->fc;
+  const Dev& d = h->d;
+  const int D = f.D, B = f.B, H = f.H, k2 = d.ky * d.kx;
+  const FcOff o = fc_off(D, H);
+  const float* th = f.theta;
+  gemm<false, true, 1>(f.X, D, th + o.W1, D, f.h1, H, B, H, D, th + o.b1, nullptr, st);    // h1 = relu(X W1^T + b1)
+  gemm<false, true, 1>(f.h1, H, th + o.W2, H, f.h2, H, B, H, H, th + o.b2, nullptr, st);   // h2 = relu(h1 W2^T + b2)
+  gemm<false, true, 2>(f.h2, H, th + o.W3, H, f.y, D, B, D, H, th + o.b3, nullptr, st);    // y = h2 W3^T + b3
+  k_fc_alpha<<<(B * k2 + 255) / 256, 256, 0, st>>>(f.alpha0, f.y, f.s, d.ni, k2, h->alpha);
+  pdf_count_launch(4);
+  PDF_LAUNCHED("network forward");
+  return PDF_OK;
+}
+
+pdf_status fc_backward(pdf_problem* h, cudaStream_t st) {
+  FcState& f = h->fc;
+  const Dev& d = h->d;
+  const int D = f.D, B = f.B, H = f.H, k2 = d.ky * d.kx;
+  const FcOff o = fc_off(D, H);
+  const float* th = f.theta;
+  float* g = f.gtheta;
+  float* dY = f.y;                                                       // y is not needed any more
+  k_fc_dy<<<(B * k2 + 255) / 256, 256, 0, st>>>(h->grad, f.s, d.ni, k2, dY);
+  gemm<true, false, 0>(dY, D, f.h2, H, g + o.W3, H, D, H, B, nullptr, nullptr, st);       // dW3 = dY^T h2
+  k_fc_colsum<<<(D + 255) / 256, 256, 0, st>>>(dY, B, D, g + o.b3);                       // db3
+  gemm<false, false, 3>(dY, D, th + o.W3, H, f.dz2, H, B, H, D, nullptr, f.h2, st);       // dz2 = (dY W3) * 1[h2 > 0]
+  gemm<true, false, 0>(f.dz2, H, f.h1, H, g + o.W2, H, H, H, B, nullptr, nullptr, st);    // dW2 = dz2^T h1
+  k_fc_colsum<<<(H + 255) / 256, 256, 0, st>>>(f.dz2, B, H, g + o.b2);                    // db2
+  gemm<false, false, 3>(f.dz2, H, th + o.W2, H, f.dz1, H, B, H, H, nullptr, f.h1, st);    // dz1 = (dz2 W2) * 1[h1 > 0]
+  gemm<true, false, 0>(f.dz1, H, f.X, D, g + o.W1, D, H, D, B, nullptr, nullptr, st);     // dW1 = dz1^T X
+  k_fc_colsum<<<(H + 255) / 256, 256, 0, st>>>(f.dz1, B, H, g + o.b1);                    // db1
+  pdf_count_launch(9);
+  PDF_LAUNCHED("network backward");
+  return PDF_OK;
+}

@@ -68,8 +68,27 @@ struct Dev {
 
 struct TC;
 
+// State of the coefficient-correcting network (fcnn.cu), allocated on the first solve that uses it.
+struct FcState {
+  int H, D, B;           // hidden width, 2 ky kx, ni
+  size_t np;             // parameter count
+  float* theta;          // [np] W1 [H][D], b1 [H], W2 [H][H], b2 [H], W3 [D][H], b3 [D]
+  float* gtheta;         // [np]
+  float* m;              // [np] Adam moments
+  float* v;
+  float* X;              // [B][D] scaled input
+  float* s;              // [1] input scale
+  float* h1;             // [B][H]
+  float* h2;             // [B][H]
+  float* y;              // [B][D] output, then dL/dy
+  float* dz1;            // [B][H]
+  float* dz2;            // [B][H]
+  float2* alpha0;        // [ni][ky][kx] the network's input coefficients
+};
+
 struct pdf_problem {
   pdf_config cfg;
+  FcState fc;
   TC* tc;                // split-BF16 tensor-core state (precision = 1), else NULL
   std::vector<double> tx, rx;
   Dev d;
@@ -103,12 +122,18 @@ struct pdf_problem {
   cudaGraphExec_t graph_exec;
   int graph_iters;       // iterations per graph launch (0 = none)
   int graph_kernels;     // kernel nodes in the graph
-  double graph_key[4];   // lr, b1, b2, eps used when captured
+  double graph_key[5];   // lr, b1, b2, eps, network width used when captured
+  int fc_active;         // the current solve optimises the network's weights (fcnn.cu)
   float2* adam_tab;      // device table (see Dev::adam_tab)
   int adam_cap;
   double adam_key[3];    // lr, b1, b2 of the table
   float* invn;
 };
+
+// coefficient-correcting network (fcnn.cu)
+pdf_status fc_prepare(pdf_problem* h, int hidden, const void* params0, cudaStream_t st);
+pdf_status fc_forward(pdf_problem* h, cudaStream_t st);    // h->alpha = alpha0 + Delta alpha(theta)
+pdf_status fc_backward(pdf_problem* h, cudaStream_t st);   // fc.gtheta from h->grad
 
 // error helpers (api.cu)
 pdf_status set_err(pdf_status st, const std::string& msg);

@@ -344,6 +344,19 @@ static pdf_status adam_step(pdf_problem* h, const pdf_solve_opts* o, cudaStream_
 }
 
 static pdf_status iteration(pdf_problem* h, const pdf_solve_opts* o, cudaStream_t st) {
+  if (h->fc_active) {
+    // alpha = alpha0 + Delta alpha(theta); loss gradient; chain rule to theta; Adam on theta
+    pdf_status s = fc_forward(h, st);
+    if (s != PDF_OK) return s;
+    if ((s = hp_loss_grad(h, h->alpha, h->grad, h->terms, st, h->adam_t)) != PDF_OK) return s;
+    if ((s = fc_backward(h, st)) != PDF_OK) return s;
+    const int n = (int)h->fc.np;
+    k_adam<<<(n + 255) / 256, 256, 0, st>>>(h->fc.theta, h->fc.gtheta, h->fc.m, h->fc.v, n, h->adam_t, h->adam_tab,
+                                            h->adam_cap, (float)o->adam_b1, (float)o->adam_b2, (float)o->adam_eps);
+    pdf_count_launch(1);
+    PDF_LAUNCHED("Adam on the network weights");
+    return PDF_OK;
+  }
   pdf_status s = hp_loss_grad(h, h->alpha, h->grad, h->terms, st, h->adam_t);
   if (s != PDF_OK) return s;
   return adam_step(h, o, st);
@@ -352,8 +365,9 @@ static pdf_status iteration(pdf_problem* h, const pdf_solve_opts* o, cudaStream_
 #define GRAPH_UNROLL 10
 
 static pdf_status build_graph(pdf_problem* h, const pdf_solve_opts* o) {
+  const double width = h->fc_active ? (double)h->fc.H : 0.0;
   if (h->graph_exec && h->graph_key[0] == o->lr && h->graph_key[1] == o->adam_b1 && h->graph_key[2] == o->adam_b2 &&
-      h->graph_key[3] == o->adam_eps)
+      h->graph_key[3] == o->adam_eps && h->graph_key[4] == width)
     return PDF_OK;
   if (h->graph_exec) {
     cudaGraphExecDestroy(h->graph_exec);
@@ -382,6 +396,7 @@ static pdf_status build_graph(pdf_problem* h, const pdf_solve_opts* o) {
   h->graph_key[1] = o->adam_b1;
   h->graph_key[2] = o->adam_b2;
   h->graph_key[3] = o->adam_eps;
+  h->graph_key[4] = width;
   return PDF_OK;
 }
 
@@ -412,6 +427,15 @@ pdf_status sv_solve(pdf_problem* h, const pdf_solve_opts* o, float2* chi_out, fl
   PDF_CUDA(cudaMemsetAsync(h->adam_m, 0, sizeof(float) * 2 * NA, st));
   PDF_CUDA(cudaMemsetAsync(h->adam_v, 0, sizeof(float) * 2 * NA, st));
   PDF_CUDA(cudaMemsetAsync(h->adam_t, 0, sizeof(int), st));
+  h->fc_active = 0;
+  if (o->fcnn_hidden > 0) {                                           // the network's input is this alpha
+    if (h->fc.H != o->fcnn_hidden && h->graph_exec) {                  // the graph holds the old buffers
+      cudaGraphExecDestroy(h->graph_exec);
+      h->graph_exec = nullptr;
+    }
+    if ((s = fc_prepare(h, o->fcnn_hidden, o->fcnn_params0, st)) != PDF_OK) return s;
+    h->fc_active = 1;
+  }
   int it = 0;
   int loop_mode = 0;                  // which loop form ran (reported)
   if (o->history_every > 0) {
@@ -437,14 +461,14 @@ pdf_status sv_solve(pdf_problem* h, const pdf_solve_opts* o, float2* chi_out, fl
     }
   } else {
     bool persisted = false;
-    if (o->use_graph == 3) {
+    if (o->use_graph == 3 && !h->fc_active) {
       if ((s = cl_run(h, o, o->iters, st, &persisted)) != PDF_OK) return s;
       if (persisted) {
         it = o->iters;
         loop_mode = 3;
       }
     }
-    if (!persisted && o->use_graph == 2) {
+    if (!persisted && o->use_graph == 2 && !h->fc_active) {
       if ((s = ps_run(h, o, o->iters, h->bar, h->perr, st, &persisted)) != PDF_OK) return s;
       if (persisted) {
         it = o->iters;
@@ -461,6 +485,9 @@ pdf_status sv_solve(pdf_problem* h, const pdf_solve_opts* o, float2* chi_out, fl
     }
     for (; it < o->iters; ++it)
       if ((s = iteration(h, o, st)) != PDF_OK) return s;
+  }
+  if (h->fc_active) {                                                  // alpha-hat at the final weights
+    if ((s = fc_forward(h, st)) != PDF_OK) return s;
   }
   // final chi-hat (and loss terms when a report is requested)
   if (rep) {

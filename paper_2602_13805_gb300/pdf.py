@@ -62,6 +62,7 @@ class pdf_solve_opts(ctypes.Structure):
         ("cco_delta", ctypes.c_double),
         ("use_graph", ctypes.c_int32), ("history_every", ctypes.c_int32),
         ("history", ctypes.c_void_p),
+        ("fcnn_hidden", ctypes.c_int32), ("fcnn_params0", ctypes.c_void_p),
     ]
 
 
@@ -280,7 +281,7 @@ def solve_opts(**kw) -> pdf_solve_opts:
     o = pdf_solve_opts()
     load().pdf_solve_opts_default(ctypes.byref(o))
     for k, v in kw.items():
-        if k in ("alpha0", "chi_true", "history"):
+        if k in ("alpha0", "chi_true", "history", "fcnn_params0"):
             v = _ptr(v)
         setattr(o, k, v)
     return o

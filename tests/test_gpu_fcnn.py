@@ -1,0 +1,114 @@
+"""GPU parity of the coefficient-correcting network (Sec. 3, network architecture; training
+settings): the library's FP32 network kernels inside pdf_solve against the FP64 oracle
+(oracle/fcnn.py), on the same alpha_(0), measured data and initial weights.
+
+Tolerances.  One Adam step from the zero output layer moves only that layer, each weight by
+-lr g / (|g| + eps): the step hardly depends on the size of g, so FP32 rounding of g changes
+alpha_(1) by ~1e-4 relative (eps / |g| terms and the FP32 products), far inside 1e-3.  Over many
+steps Adam's sign-like updates amplify rounding, so FP32 and FP64 weight trajectories separate;
+as for the plain solve the contract of a whole reconstruction is the RelErr, within 1e-3.
+"""
+import numpy as np
+import pytest
+
+import scenes
+from oracle import fcnn, solve
+from tests.gpu_common import Case, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+H = 64
+
+
+def _dev(a):
+    return torch.tensor(a, device="cuda")
+
+
+def _case(name="c1", **kw):
+    w = scenes.workload(name, **kw)
+    c = Case(w)
+    a0 = c.alpha(scale=0.2, seed=4)
+    th0 = scenes.fcnn_params(w.ky, w.kx, H, seed=7)
+    return w, c, a0, th0
+
+
+@pytest.mark.parametrize("name,kw", [("c1", {}), ("g24x20", dict(nx=24, ny=20, ni=5, nr=7, kx=7, ky=5))])
+def test_one_step_matches_oracle(name, kw):
+    w, c, a0, th0 = _case("c1", **kw)
+    prob = c.problem()
+    out = prob.solve(iters=1, init=1, alpha0=_dev(a0), apply_cco=False, use_graph=0,
+                     fcnn_hidden=H, fcnn_params0=_dev(th0))
+    ref = fcnn.reparam_solve(c.ops, c.esca, 1, th0, H, lr=1e-2, alpha0=a0.astype(np.complex128), apply_cco=False)
+    d_gpu = out["alpha"].cpu().numpy() - a0
+    d_ref = ref["alpha"] - a0
+    print(name, "one-step Delta alpha rel", rel(d_gpu, d_ref))
+    assert np.abs(d_ref).max() > 0
+    assert rel(d_gpu, d_ref) < 1e-3
+    prob.close()
+
+
+def test_zero_iterations_give_alpha0_and_the_plain_loss():
+    w, c, a0, th0 = _case()
+    prob = c.problem()
+    out = prob.solve(iters=0, init=1, alpha0=_dev(a0), apply_cco=False, fcnn_hidden=H, fcnn_params0=_dev(th0))
+    assert torch.equal(out["alpha"], _dev(a0))                      # the output layer starts at zero
+    plain = prob.solve(iters=0, init=1, alpha0=_dev(a0), apply_cco=False)
+    np.testing.assert_array_equal(out["terms"], plain["terms"])
+    prob.close()
+
+
+def test_loss_history_tracks_oracle():
+    w, c, a0, th0 = _case()
+    prob = c.problem()
+    n = 10
+    out = prob.solve(iters=n, init=1, alpha0=_dev(a0), apply_cco=False, history_every=1,
+                     fcnn_hidden=H, fcnn_params0=_dev(th0))
+    ref = fcnn.reparam_solve(c.ops, c.esca, n, th0, H, lr=1e-2, alpha0=a0.astype(np.complex128), apply_cco=False,
+                             history=True)
+    L_gpu = out["history"].cpu().numpy()[:, 0]
+    L_ref = ref["losses"][:, 0]
+    print("loss gpu", L_gpu, "\nloss ref", L_ref)
+    assert abs(L_gpu[0] - L_ref[0]) < 1e-5 * L_ref[0]               # at alpha_(0): the plain loss
+    np.testing.assert_allclose(L_gpu, L_ref, rtol=1e-3)
+    prob.close()
+
+
+def test_graph_and_eager_loops_agree_and_cluster_falls_back():
+    w, c, a0, th0 = _case()
+    prob = c.problem()
+    kw = dict(iters=30, init=1, alpha0=_dev(a0), apply_cco=False, fcnn_hidden=H, fcnn_params0=_dev(th0))
+    e = prob.solve(use_graph=0, **kw)
+    g = prob.solve(use_graph=1, **kw)
+    k = prob.solve(use_graph=3, **kw)
+    assert torch.equal(e["alpha"], g["alpha"])                       # same kernels, same order
+    assert torch.equal(g["alpha"], k["alpha"])
+    assert g["loop_mode"] == 1 and k["loop_mode"] == 1              # the cluster loop optimises alpha only
+    plain = prob.solve(use_graph=1, iters=30, init=1, alpha0=_dev(a0), apply_cco=False)
+    assert not torch.equal(plain["alpha"], g["alpha"])               # the graph was rebuilt for the plain form
+    prob.close()
+
+
+def test_whole_solve_relerr_matches_oracle():
+    w = scenes.workload("c1", iters=100)
+    c = Case(w)
+    th0 = scenes.fcnn_params(w.ky, w.kx, H, seed=7)
+    prob = c.problem()
+    chi_t = _dev(c.chi.astype(np.complex64))
+    out = prob.solve(iters=w.iters, chi_true=chi_t, fcnn_hidden=H, fcnn_params0=_dev(th0))
+    ref = fcnn.reparam_solve(c.ops, c.esca, w.iters, th0, H, lr=1e-2, chi_true=c.chi)
+    plain = solve.pdf_solve(c.ops, c.esca, w.iters, chi_true=c.chi)
+    print("relerr_cco gpu", out["relerr_cco"], "oracle", ref["relerr_cco"], "plain oracle", plain["relerr_cco"])
+    assert abs(out["relerr"] - ref["relerr"]) < 1e-3
+    assert abs(out["relerr_cco"] - ref["relerr_cco"]) < 1e-3
+    prob.close()
+
+
+def test_bad_network_options_are_rejected():
+    from paper_2602_13805_gb300 import pdf
+    w, c, a0, th0 = _case()
+    prob = c.problem()
+    for kw in (dict(fcnn_hidden=-1, fcnn_params0=_dev(th0)), dict(fcnn_hidden=8), dict(fcnn_hidden=5000, fcnn_params0=_dev(th0))):
+        with pytest.raises(pdf.PDFError):
+            prob.solve(iters=1, init=1, alpha0=_dev(a0), **kw)
+    prob.close()

@@ -182,9 +182,12 @@ def fp32_peak_tflops(peaks):
 
 def bench_config(w, args, world):
     """The workload description shared by both arms of the benchmark."""
+    net = (f", Adam on the weights of the coefficient-correcting network (two hidden layers of {args.fcnn})"
+           if args.fcnn > 0 else "")
     return {"workload": f"{w.name}: {w.nx}x{w.ny} grid, {w.side} lambda DOI, Ni={w.ni}, Nr={w.nr}, "
-                        f"K={w.kx}x{w.ky}, {w.iters} Adam iterations, BP+CSI init, CCO",
+                        f"K={w.kx}x{w.ky}, {w.iters} Adam iterations, BP+CSI init, CCO{net}",
             "iters": w.iters, "lr": args.lr, "precision": args.precision, "loop": args.loop,
+            "fcnn_hidden": args.fcnn,
             "fold_gs": args.fold, "parallelism": "replicas" if world > 1 else "single",
             "l2": "flushed between reconstructions (512 MB write); working set L2-resident within one"}
 
@@ -210,7 +213,11 @@ def run_ours(args, rank, world, local):
     esca_d = torch.from_numpy(esca).cuda()
     prob.set_data(esca_d)
     stream = torch.cuda.current_stream()
-    opts = pdf.solve_opts(iters=w.iters, lr=args.lr, init=0, chi_true=chi_d, apply_cco=1, use_graph=args.loop)
+    net = {}
+    if args.fcnn > 0:                                   # the network's seeded initial weights
+        net = dict(fcnn_hidden=args.fcnn,
+                   fcnn_params0=torch.from_numpy(scenes.fcnn_params(w.ky, w.kx, args.fcnn, seed=0)).cuda())
+    opts = pdf.solve_opts(iters=w.iters, lr=args.lr, init=0, chi_true=chi_d, apply_cco=1, use_graph=args.loop, **net)
     chi_out = torch.empty((w.ny, w.nx), dtype=torch.complex64, device="cuda")
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -266,7 +273,7 @@ def run_ours(args, rank, world, local):
     # --- the fused loop alone: the same solve with 0 iterations, subtracted ------------------
     loop_ms = None
     if rep.loop_mode == 3:
-        opts0 = pdf.solve_opts(iters=0, lr=args.lr, init=0, chi_true=chi_d, apply_cco=1, use_graph=args.loop)
+        opts0 = pdf.solve_opts(iters=0, lr=args.lr, init=0, chi_true=chi_d, apply_cco=1, use_graph=args.loop, **net)
         ev0 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         torch.cuda.synchronize()
         for k in range(args.steps):
@@ -342,7 +349,7 @@ def run_ours(args, rank, world, local):
             "forward_solver_iters": fwd_iters,
         }
         if not args.no_cpu:
-            out["cpu_baseline"] = cpu_baseline(w, args.cpu_iters)
+            out["cpu_baseline"] = cpu_baseline(w, args.cpu_iters, args.fcnn)
     prob.close()
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -361,19 +368,28 @@ def _oracle_case(w, seed=0):
     return ops, esca, chi
 
 
-def cpu_baseline(w, iters):
-    """FP64 oracle on the host: init + `iters` Adam iterations, scaled to a full reconstruction."""
+def cpu_baseline(w, iters, fcnn=0):
+    """FP64 oracle on the host: init + `iters` Adam iterations (on alpha, or on the network's
+    weights when fcnn > 0), scaled to a full reconstruction."""
+    from oracle import fcnn as onet
     from oracle import loss, solve
     ops, esca, chi = _oracle_case(w)
     t0 = time.perf_counter()
     _, R0, _ = solve.bp_init(ops, esca)
     a = solve.csi_step(ops, esca, R0)
     t_init = time.perf_counter() - t0
-    opt = solve.Adam(lr=1e-2)
     t0 = time.perf_counter()
-    for _ in range(iters):
-        _, g = loss.loss_grad(ops, esca, a)
-        a = opt.step(a, g)
+    if fcnn > 0:
+        th = scenes.fcnn_params(w.ky, w.kx, fcnn, seed=0).astype(np.float64)
+        opt = onet.AdamReal(lr=1e-2)
+        for _ in range(iters):
+            _, g = onet.loss_grad_theta(ops, esca, a, th, fcnn)
+            th = opt.step(th, g)
+    else:
+        opt = solve.Adam(lr=1e-2)
+        for _ in range(iters):
+            _, g = loss.loss_grad(ops, esca, a)
+            a = opt.step(a, g)
     t_it = (time.perf_counter() - t0) / iters
     ms = (t_init + t_it * w.iters) * 1e3
     return {"value": ms, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
@@ -471,7 +487,7 @@ def run_reference(args, rank, world):
     iters = args.cpu_iters
     times = []
     for k in range(args.warmup + args.steps):
-        r = cpu_baseline(w, iters)
+        r = cpu_baseline(w, iters, args.fcnn)
         if k >= args.warmup:
             times.append(r["value"])
     v = sum(times) / len(times)
@@ -488,6 +504,9 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--fcnn", type=int, default=0,
+                    help="hidden width of the coefficient-correcting network whose weights Adam optimises "
+                         "(0: Adam on the coefficients)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])

@@ -9,9 +9,11 @@
 // reals, Delta alpha_p = (y_p[:ky kx] + i y_p[ky kx:]) / s.  The chain rule to theta takes the
 // loss gradient g = dL/dRe alpha + i dL/dIm alpha as dL/dy_p = [Re g_p, Im g_p] / s.
 //
-// All products are FP32 with FP32 accumulation in increasing k order, on a 32 x 32 output tile per
-// 256-thread block staged through shared memory (the batch is ni <= 64 rows, so these are small,
-// latency-bound products next to the loss gradient's FFTs).
+// All products are FP32 with FP32 accumulation, on a 32 x 32 output tile per 256-thread block
+// staged through shared memory; the ones with a long k and only ni <= 64 rows split k into chunks
+// of 64 over blocks and add the partial sums in a fixed order (deterministic).
+#include <algorithm>
+
 #include "problem.cuh"
 
 constexpr int FCT = 32;   // output tile side and k chunk
@@ -19,31 +21,35 @@ constexpr int FCT = 32;   // output tile side and k chunk
 // C(m, n) = sum_k A(m, k) B(k, n) for m < M, n < N, with A(m, k) = TA ? A[k lda + m] : A[m lda + k]
 // and B(k, n) = TB ? B[n ldb + k] : B[k ldb + n].  Epilogue EPI: 0 store; 1 add bias[n], ReLU;
 // 2 add bias[n]; 3 multiply by (mask[m ldc + n] > 0), the ReLU derivative of a stored activation.
+// With gridDim.z = S > 1 block z covers k in [z kc, (z+1) kc) and stores its partial sums to
+// C + z M N (row-major [M][N], no epilogue); k_fc_reduce adds the S partials in order.
 template <bool TA, bool TB, int EPI>
 __global__ void __launch_bounds__(256) k_fc_gemm(const float* __restrict__ A, int lda, const float* __restrict__ B,
                                                  int ldb, float* __restrict__ C, int ldc, int M, int N, int K,
-                                                 const float* __restrict__ bias, const float* __restrict__ mask) {
+                                                 int kc, const float* __restrict__ bias, const float* __restrict__ mask) {
   __shared__ float As[FCT][FCT + 1];   // [m][k]
   __shared__ float Bs[FCT][FCT + 1];   // [k][n]
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int m0 = blockIdx.y * FCT, n0 = blockIdx.x * FCT;
+  const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
+  const bool partial = gridDim.z > 1;
   float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-  for (int k0 = 0; k0 < K; k0 += FCT) {
+  for (int k0 = kb; k0 < ke; k0 += FCT) {
     for (int e = threadIdx.x; e < FCT * FCT; e += blockDim.x) {
       const int a = e / FCT, b = e - a * FCT;                            // b runs along the contiguous index
       if (TA) {
         const int m = m0 + b, k = k0 + a;
-        As[b][a] = (m < M && k < K) ? A[(size_t)k * lda + m] : 0.f;
+        As[b][a] = (m < M && k < ke) ? A[(size_t)k * lda + m] : 0.f;
       } else {
         const int m = m0 + a, k = k0 + b;
-        As[a][b] = (m < M && k < K) ? A[(size_t)m * lda + k] : 0.f;
+        As[a][b] = (m < M && k < ke) ? A[(size_t)m * lda + k] : 0.f;
       }
       if (TB) {
         const int k = k0 + b, n = n0 + a;
-        Bs[b][a] = (k < K && n < N) ? B[(size_t)n * ldb + k] : 0.f;
+        Bs[b][a] = (k < ke && n < N) ? B[(size_t)n * ldb + k] : 0.f;
       } else {
         const int k = k0 + a, n = n0 + b;
-        Bs[a][b] = (k < K && n < N) ? B[(size_t)k * ldb + n] : 0.f;
+        Bs[a][b] = (k < ke && n < N) ? B[(size_t)k * ldb + n] : 0.f;
       }
     }
     __syncthreads();
@@ -65,11 +71,30 @@ __global__ void __launch_bounds__(256) k_fc_gemm(const float* __restrict__ A, in
       const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
       if (m >= M || n >= N) continue;
       float v = acc[i][j];
+      if (partial) {
+        C[((size_t)blockIdx.z * M + m) * N + n] = v;
+        continue;
+      }
       if (EPI == 1) v = fmaxf(v + bias[n], 0.f);
       if (EPI == 2) v = v + bias[n];
       if (EPI == 3) v = mask[(size_t)m * ldc + n] > 0.f ? v : 0.f;
       C[(size_t)m * ldc + n] = v;
     }
+}
+
+// C[m][n] = epilogue(sum over z (increasing) of part[z][m][n]) for the split-k form
+template <int EPI>
+__global__ void k_fc_reduce(const float* __restrict__ part, int S, float* __restrict__ C, int ldc, int M, int N,
+                            const float* __restrict__ bias, const float* __restrict__ mask) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M * N) return;
+  const int m = i / N, n = i - m * N;
+  float v = 0.f;
+  for (int z = 0; z < S; ++z) v += part[(size_t)z * M * N + i];
+  if (EPI == 1) v = fmaxf(v + bias[n], 0.f);
+  if (EPI == 2) v = v + bias[n];
+  if (EPI == 3) v = mask[(size_t)m * ldc + n] > 0.f ? v : 0.f;
+  C[(size_t)m * ldc + n] = v;
 }
 
 // out[c] = sum over r (increasing) of A[r cols + c]: bias gradients
@@ -136,11 +161,24 @@ __global__ void k_fc_dy(const float2* __restrict__ g, const float* __restrict__ 
   dY[(size_t)b * D + k2 + j] = v.y / sc;
 }
 
+// k chunk per split (two 32-wide steps): the batch is small, so a long k runs as many blocks of two
+// steps each instead of one block walking k with a round trip to L2 per step
+constexpr int FC_KC = 2 * FCT;
+constexpr int FC_SMAX = 32;
+static int fc_splits(int K) { return std::min(FC_SMAX, (K + FC_KC - 1) / FC_KC); }
+
 template <bool TA, bool TB, int EPI>
-static void gemm(const float* A, int lda, const float* B, int ldb, float* C, int ldc, int M, int N, int K,
-                 const float* bias, const float* mask, cudaStream_t st) {
-  const dim3 grid((N + FCT - 1) / FCT, (M + FCT - 1) / FCT);
-  k_fc_gemm<TA, TB, EPI><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, M, N, K, bias, mask);
+static int gemm(const float* A, int lda, const float* B, int ldb, float* C, int ldc, int M, int N, int K,
+                const float* bias, const float* mask, float* work, cudaStream_t st) {
+  const int S = fc_splits(K), kc = (K + S - 1) / S;
+  const dim3 grid((N + FCT - 1) / FCT, (M + FCT - 1) / FCT, S);
+  if (S == 1) {
+    k_fc_gemm<TA, TB, EPI><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, M, N, K, K, bias, mask);
+    return 1;
+  }
+  k_fc_gemm<TA, TB, EPI><<<grid, 256, 0, st>>>(A, lda, B, ldb, work, N, M, N, K, kc, nullptr, nullptr);
+  k_fc_reduce<EPI><<<(M * N + 255) / 256, 256, 0, st>>>(work, S, C, ldc, M, N, bias, mask);
+  return 2;
 }
 
 // parameter offsets in the flat vector
@@ -175,6 +213,9 @@ pdf_status fc_prepare(pdf_problem* h, int hidden, const void* params0, cudaStrea
     for (float** b : hb)
       if ((s = ws_alloc(h, (void**)b, sizeof(float) * B * H)) != PDF_OK) return s;
     if ((s = ws_alloc(h, (void**)&f.alpha0, sizeof(float2) * d.ni * d.ky * d.kx)) != PDF_OK) return s;
+    // split-k partials: the products with M = B rows and a long k (D or H)
+    const size_t wn = (size_t)std::max(fc_splits(D) * std::max(H, D), fc_splits(H) * std::max(H, D)) * B;
+    if ((s = ws_alloc(h, (void**)&f.work, sizeof(float) * wn)) != PDF_OK) return s;
     f.H = H;
     f.D = D;
     f.B = B;
@@ -196,11 +237,12 @@ pdf_status fc_forward(pdf_problem* h, cudaStream_t st) {
   const int D = f.D, B = f.B, H = f.H, k2 = d.ky * d.kx;
   const FcOff o = fc_off(D, H);
   const float* th = f.theta;
-  gemm<false, true, 1>(f.X, D, th + o.W1, D, f.h1, H, B, H, D, th + o.b1, nullptr, st);    // h1 = relu(X W1^T + b1)
-  gemm<false, true, 1>(f.h1, H, th + o.W2, H, f.h2, H, B, H, H, th + o.b2, nullptr, st);   // h2 = relu(h1 W2^T + b2)
-  gemm<false, true, 2>(f.h2, H, th + o.W3, H, f.y, D, B, D, H, th + o.b3, nullptr, st);    // y = h2 W3^T + b3
+  int n = 1;
+  n += gemm<false, true, 1>(f.X, D, th + o.W1, D, f.h1, H, B, H, D, th + o.b1, nullptr, f.work, st);   // h1 = relu(X W1^T + b1)
+  n += gemm<false, true, 1>(f.h1, H, th + o.W2, H, f.h2, H, B, H, H, th + o.b2, nullptr, f.work, st);  // h2 = relu(h1 W2^T + b2)
+  n += gemm<false, true, 2>(f.h2, H, th + o.W3, H, f.y, D, B, D, H, th + o.b3, nullptr, f.work, st);   // y = h2 W3^T + b3
   k_fc_alpha<<<(B * k2 + 255) / 256, 256, 0, st>>>(f.alpha0, f.y, f.s, d.ni, k2, h->alpha);
-  pdf_count_launch(4);
+  pdf_count_launch(n);
   PDF_LAUNCHED("network forward");
   return PDF_OK;
 }
@@ -214,15 +256,16 @@ pdf_status fc_backward(pdf_problem* h, cudaStream_t st) {
   float* g = f.gtheta;
   float* dY = f.y;                                                       // y is not needed any more
   k_fc_dy<<<(B * k2 + 255) / 256, 256, 0, st>>>(h->grad, f.s, d.ni, k2, dY);
-  gemm<true, false, 0>(dY, D, f.h2, H, g + o.W3, H, D, H, B, nullptr, nullptr, st);       // dW3 = dY^T h2
-  k_fc_colsum<<<(D + 255) / 256, 256, 0, st>>>(dY, B, D, g + o.b3);                       // db3
-  gemm<false, false, 3>(dY, D, th + o.W3, H, f.dz2, H, B, H, D, nullptr, f.h2, st);       // dz2 = (dY W3) * 1[h2 > 0]
-  gemm<true, false, 0>(f.dz2, H, f.h1, H, g + o.W2, H, H, H, B, nullptr, nullptr, st);    // dW2 = dz2^T h1
-  k_fc_colsum<<<(H + 255) / 256, 256, 0, st>>>(f.dz2, B, H, g + o.b2);                    // db2
-  gemm<false, false, 3>(f.dz2, H, th + o.W2, H, f.dz1, H, B, H, H, nullptr, f.h1, st);    // dz1 = (dz2 W2) * 1[h1 > 0]
-  gemm<true, false, 0>(f.dz1, H, f.X, D, g + o.W1, D, H, D, B, nullptr, nullptr, st);     // dW1 = dz1^T X
-  k_fc_colsum<<<(H + 255) / 256, 256, 0, st>>>(f.dz1, B, H, g + o.b1);                    // db1
-  pdf_count_launch(9);
+  int n = 4;
+  n += gemm<true, false, 0>(dY, D, f.h2, H, g + o.W3, H, D, H, B, nullptr, nullptr, f.work, st);      // dW3 = dY^T h2
+  k_fc_colsum<<<(D + 255) / 256, 256, 0, st>>>(dY, B, D, g + o.b3);                                  // db3
+  n += gemm<false, false, 3>(dY, D, th + o.W3, H, f.dz2, H, B, H, D, nullptr, f.h2, f.work, st);      // dz2 = (dY W3) 1[h2 > 0]
+  n += gemm<true, false, 0>(f.dz2, H, f.h1, H, g + o.W2, H, H, H, B, nullptr, nullptr, f.work, st);   // dW2 = dz2^T h1
+  k_fc_colsum<<<(H + 255) / 256, 256, 0, st>>>(f.dz2, B, H, g + o.b2);                               // db2
+  n += gemm<false, false, 3>(f.dz2, H, th + o.W2, H, f.dz1, H, B, H, H, nullptr, f.h1, f.work, st);   // dz1 = (dz2 W2) 1[h1 > 0]
+  n += gemm<true, false, 0>(f.dz1, H, f.X, D, g + o.W1, D, H, D, B, nullptr, nullptr, f.work, st);    // dW1 = dz1^T X
+  k_fc_colsum<<<(H + 255) / 256, 256, 0, st>>>(f.dz1, B, H, g + o.b1);                               // db1
+  pdf_count_launch(n);
   PDF_LAUNCHED("network backward");
   return PDF_OK;
 }

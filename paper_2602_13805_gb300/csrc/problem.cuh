@@ -84,6 +84,7 @@ struct FcState {
   float* dz1;            // [B][H]
   float* dz2;            // [B][H]
   float2* alpha0;        // [ni][ky][kx] the network's input coefficients
+  float* work;           // split-k partial sums
 };
 
 struct pdf_problem {

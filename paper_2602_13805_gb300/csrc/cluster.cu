@@ -364,8 +364,6 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     }
     __syncthreads();
     CL_STAMP(1);
-    cl_cgemm<2, 2, 1, false, false>(RB, nx, kx, Tall + y0 * kx, kx, 1, wxs, nx, 1,   // J = T' Wx on own pixels
-                                 [&](int yl, int x, float2 v) { Js[yl * nx + x] = v; });
     CL_STAMP(2);
     cl_cgemm<2, 2, 1, false, false>(ny, CB, kx, Tall, kx, 1, whs, 1, kx,              // row DFT of J at own columns: T' what
                                  [&](int y, int lc, float2 v) { colb[lc * LS + y] = v; });
@@ -416,7 +414,12 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
         }
       }
     }
-    cl.sync();
+    // J on own pixels is needed only after the exchange: it runs between this CTA's arrival at the
+    // cluster barrier and its wait
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    cl_cgemm<2, 2, 1, false, false>(RB, nx, kx, Tall + y0 * kx, kx, 1, wxs, nx, 1,   // J = T' Wx on own pixels
+                                    [&](int yl, int x, float2 v) { Js[yl * nx + x] = v; });
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
     CL_STAMP(4);
     // ===== 3. inverse row DFT, s, per-incidence contributions, partial G_S J_p =====
 #pragma unroll 1

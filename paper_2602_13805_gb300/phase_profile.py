@@ -17,9 +17,9 @@ import numpy as np
 
 PHASES = [
     "synthesis T' = Wy^T alpha, all rows (Eq. 9); r_d = (G_S Phi) alpha - E_sca (Eq. 16)",
-    "J on own rows",
+    "(no work: J on own rows runs inside the exchange barrier below)",
     "row DFT of J at own columns (T' what)",
-    "column convolution with the G_D spectrum -> row owners + cluster barrier",
+    "column convolution with the G_D spectrum -> row owners; J on own rows between arrive and wait of the cluster barrier",
     "inverse row DFT (G_D J)",
     "s and the per-incidence sums + grid barrier",
     "R-hat, chi-hat from the sums over incidences (Eq. 6, 7; split over the grid: + grid barrier)",

@@ -112,3 +112,19 @@ def test_bad_network_options_are_rejected():
         with pytest.raises(pdf.PDFError):
             prob.solve(iters=1, init=1, alpha0=_dev(a0), **kw)
     prob.close()
+
+
+def test_network_form_with_split_bf16_contractions():
+    # the network's weights optimised through the tensor-core loss gradient (precision 1): same
+    # iterates as the FP32 form within the split-BF16 contract
+    w, c, a0, th0 = _case()
+    kw = dict(iters=20, init=1, alpha0=_dev(a0), apply_cco=False, use_graph=1, fcnn_hidden=H,
+              fcnn_params0=_dev(th0))
+    p32, p16 = c.problem(), c.problem(precision=1)
+    a = p32.solve(**kw)
+    b = p16.solve(**kw)
+    err = rel(b["alpha"].cpu().numpy(), a["alpha"].cpu().numpy())
+    print("network form, split-BF16 vs FP32 alpha rel", err)
+    assert err < 1e-2
+    p32.close()
+    p16.close()

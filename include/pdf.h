@@ -201,8 +201,9 @@ const char* pdf_stage_name(pdf_problem* h, int32_t k);
  * in ordinary builds, whose kernels carry no marks. */
 pdf_status pdf_phase_stamps(uint64_t* out);
 
-/* The cluster sizes the cluster loop (use_graph = 3) would consider for this handle, in order of
- * preference: for each, out[4 i + 0..3] = cluster size C, shared-memory bytes per CTA, how many
+/* The cluster sizes the cluster loop (use_graph = 3) would consider for this handle (16, 8, 6, 4, 2:
+ * at most 5 rows; C need not divide the grid, the last CTA then owns fewer rows or columns), in
+ * order of preference: for each, out[4 i + 0..3] = cluster size C, shared-memory bytes per CTA, how many
  * such clusters the device can hold at once (-1 when the plan exceeds the shared-memory limit or
  * the query failed), and 1 when all ni clusters fit (the solve takes the first such row).
  * Returns the number of rows (0: the problem does not qualify; the graph loop runs) or a

@@ -266,11 +266,15 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nx = d.nx, ny = d.ny, kx = d.kx, ky = d.ky, nr = d.nr, M = d.M, ni = d.ni;
   const int y0 = k * RB, c0 = k * CB;
+  // RB, CB: rows and padded columns per CTA (array strides; the last CTA may own fewer when C does
+  // not divide ny or P): this CTA owns nrow rows and ncol columns
+  const int nrow = min(RB, ny - y0), ncol = min(CB, P - c0);
   const int LS = ny + 1;
   const int NA = ky * kx;
-  const int GP = RB * nx;                    // pixels owned by this CTA
+  const int GP = RB * nx;                    // pixel capacity per CTA
   const int HP = (RB + 2) * nx;              // with one halo row above and below
   const int TP = (RB + 1) * nx;              // rows y0-1 .. y0+RB-1
+  const int GPk = nrow * nx, HPk = (nrow + 2) * nx, TPk = (nrow + 1) * nx;   // this CTA's counts
   // ---- shared memory carve-up ----
   extern __shared__ float2 sm[];
   float2* tw = sm;                           // [P]
@@ -279,7 +283,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
   // y) and writes into the row owners' rowT[c][yl]; a row owner's warp holds one row (lanes along
   // c) and writes into the column owners' colT[y][lc].  Odd strides keep local reads of the other
   // direction on distinct banks.
-  const int RS = RB + 1, SC = CB + 1;
+  const int RS = (RB + 1) | 1, SC = CB | 1;   // odd strides (RB + 1 or RB + 2, CB or CB + 1)
   float2* rowT = tw + P;                     // [P][RS] row spectra of own rows, column by column
   float2* colb = rowT + P * RS;              // [CB][LS] row DFT of J at own columns (phases 1-2)
   float2* colT = colb + CB * LS;             // [ny][SC] row DFT of u at own columns, then of dL/dJ (4-6)
@@ -322,7 +326,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     av[2 * i] = av[2 * i + 1] = 0.f;
   }
 #pragma unroll 1
-  for (int i = threadIdx.x; i < GP; i += CL_NT) Es[i] = d.einc[(size_t)p * M + y0 * nx + i];
+  for (int i = threadIdx.x; i < GPk; i += CL_NT) Es[i] = d.einc[(size_t)p * M + y0 * nx + i];
 #pragma unroll 1
   for (int t = threadIdx.x; t < NRK; t += CL_NT) es[t] = d.esca[(size_t)p * nr + k + C * t];
 #pragma unroll 1
@@ -330,10 +334,10 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
 #pragma unroll 1
   for (int i = threadIdx.x; i < kx * CB; i += CL_NT) {
     const int lc = i / kx, jx = i - lc * kx;
-    whs[i] = d.what[(size_t)jx * P + c0 + lc];
+    whs[i] = lc < ncol ? d.what[(size_t)jx * P + c0 + lc] : make_float2(0.f, 0.f);
   }
 #pragma unroll 1
-  for (int i = threadIdx.x; i < CB * P; i += CL_NT) ghs[i] = d.ghat_perm[(size_t)c0 * P + i];
+  for (int i = threadIdx.x; i < ncol * P; i += CL_NT) ghs[i] = d.ghat_perm[(size_t)c0 * P + i];
 #pragma unroll 1
   for (int i = threadIdx.x; i < kx * nx; i += CL_NT) wxs[i] = d.wx[i];
 #pragma unroll 1
@@ -365,15 +369,15 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     __syncthreads();
     CL_STAMP(1);
     CL_STAMP(2);
-    cl_cgemm<2, 2, 1, false, false>(ny, CB, kx, Tall, kx, 1, whs, 1, kx,              // row DFT of J at own columns: T' what
+    cl_cgemm<2, 2, 1, false, false>(ny, ncol, kx, Tall, kx, 1, whs, 1, kx,            // row DFT of J at own columns: T' what
                                  [&](int y, int lc, float2 v) { colb[lc * LS + y] = v; });
     __syncthreads();
     CL_STAMP(3);
     // ===== 2. column convolution, results back to row owners =====
 #pragma unroll 1
-    for (int lc = warp; lc < CB; lc += 2 * CL_NW) {                    // columns lc and lc + NW together
+    for (int lc = warp; lc < ncol; lc += 2 * CL_NW) {                  // columns lc and lc + NW together
       const int lc2 = lc + CL_NW;
-      if (lc2 < CB) {
+      if (lc2 < ncol) {
         Line2<P> G, L;
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
@@ -417,13 +421,13 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     // J on own pixels is needed only after the exchange: it runs between this CTA's arrival at the
     // cluster barrier and its wait
     asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-    cl_cgemm<2, 2, 1, false, false>(RB, nx, kx, Tall + y0 * kx, kx, 1, wxs, nx, 1,   // J = T' Wx on own pixels
+    cl_cgemm<2, 2, 1, false, false>(nrow, nx, kx, Tall + y0 * kx, kx, 1, wxs, nx, 1, // J = T' Wx on own pixels
                                     [&](int yl, int x, float2 v) { Js[yl * nx + x] = v; });
     asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
     CL_STAMP(4);
     // ===== 3. inverse row DFT, s, per-incidence contributions, partial G_S J_p =====
 #pragma unroll 1
-    for (int yl = warp; yl < RB; yl += CL_NW) {
+    for (int yl = warp; yl < nrow; yl += CL_NW) {
       Line<P> L;
 #pragma unroll
       for (int kk = 0; kk < R; ++kk) L.v[kk] = rowT[(kk * 32 + lane) * RS + yl];
@@ -437,7 +441,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     __syncthreads();
     CL_STAMP(5);
 #pragma unroll 1
-    for (int i = threadIdx.x; i < GP; i += CL_NT) {
+    for (int i = threadIdx.x; i < GPk; i += CL_NT) {
       const int yl = i / nx, x = i - yl * nx;
       const float2 J = Js[i];
       const float2 s = cmul(beta, J) + Es[i] + rowT[x * RS + yl];
@@ -494,7 +498,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
       cl_grid_barrier(a.bar, ((unsigned)it * 2u + 2u) * nblocks, a.err, [] {});
       const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 1
-      for (int i0 = threadIdx.x; i0 < HP; i0 += 4 * CL_NT) {             // own rows + halo, four loads in flight
+      for (int i0 = threadIdx.x; i0 < HPk; i0 += 4 * CL_NT) {            // own rows + halo, four loads in flight
         float4 v[4];
         float dv[4];
         bool ok[4], own[4];
@@ -502,8 +506,8 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int i = i0 + u * CL_NT, hy = i / nx, x = i - hy * nx, y = y0 + hy - 1;
-          ok[u] = i < HP && y >= 0 && y < ny;
-          own[u] = ok[u] && hy >= 1 && hy <= RB;
+          ok[u] = i < HPk && y >= 0 && y < ny;
+          own[u] = ok[u] && hy >= 1 && hy <= nrow;
           ix[u] = y * nx + x;
           v[u] = ok[u] ? __ldcg(a.rc + ix[u]) : z4;
           dv[u] = own[u] ? __ldcg(a.dsg + ix[u]) : 0.f;
@@ -521,7 +525,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
       }
     } else {
 #pragma unroll 1
-      for (int i = threadIdx.x; i < HP; i += CL_NT) {
+      for (int i = threadIdx.x; i < HPk; i += CL_NT) {
         const int hy = i / nx, x = i - hy * nx, y = y0 + hy - 1;
         if (y < 0 || y >= ny) continue;
         const float4 sm4 = cl_pixel_sums(nd + (size_t)y * nx + x, ni, M);
@@ -532,14 +536,14 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
         Rh[i] = Rv;
         Ch[i] = chi;
         mgs[i] = sqrtf(cabs2(chi) + d.eps_abs);
-        if (hy >= 1 && hy <= RB) Dl[(hy - 1) * nx + x] = clamped ? -Df : Df;
+        if (hy >= 1 && hy <= nrow) Dl[(hy - 1) * nx + x] = clamped ? -Df : Df;
       }
     }
     __syncthreads();
     CL_STAMP(7);
     // TV and bridge pieces at (y, x) for rows y0-1 .. y0+RB-1, each computed once (Eq. 18, 19)
 #pragma unroll 1
-    for (int i = threadIdx.x; i < TP; i += CL_NT) {
+    for (int i = threadIdx.x; i < TPk; i += CL_NT) {
       const int hy = i / nx, x = i - hy * nx, y = y0 + hy - 1;
       if (y < 0) continue;
       const float2 c = Ch[i];
@@ -560,7 +564,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     CL_STAMP(8);
     // state residual, cotangent on chi -> w, u (into rowT) and v (into vs)
 #pragma unroll 1
-    for (int li = threadIdx.x; li < GP; li += CL_NT) {
+    for (int li = threadIdx.x; li < GPk; li += CL_NT) {
       const int yl = li / nx, x = li - yl * nx, y = y0 + yl;
       const int hc = li + nx;                                            // index in the halo-row arrays
       const float2 Rv = Rh[hc], c = Ch[hc];
@@ -602,7 +606,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     __syncthreads();
     CL_STAMP(9);
 #pragma unroll 1
-    for (int yl = warp; yl < RB; yl += CL_NW) {                          // row DFTs of u and v / Px -> column owners
+    for (int yl = warp; yl < nrow; yl += CL_NW) {                        // row DFTs of u and v / Px -> column owners
       Line2<P> L;
       const float sP = 1.f / (float)P;                                   // exact: P is a power of two
 #pragma unroll
@@ -623,9 +627,9 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     CL_STAMP(10);
     // ===== 5. column convolution with the conjugated spectrum, kept at the column owner =====
 #pragma unroll 1
-    for (int lc = warp; lc < CB; lc += 2 * CL_NW) {                    // columns lc and lc + NW together
+    for (int lc = warp; lc < ncol; lc += 2 * CL_NW) {                  // columns lc and lc + NW together
       const int lc2 = lc + CL_NW;
-      if (lc2 < CB) {
+      if (lc2 < ncol) {
         Line2<P> G, L;
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
@@ -670,7 +674,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     // ===== 6. analysis (Phi^H) of dL/dJ = v + G_D^H u, partial over this CTA's columns =====
     // dL/dJ = inverse row DFT of B (B = the row-spectral v + G_D^H u at the column owners), so its
     // x-analysis is B conj(what) summed over the columns (each CTA: all rows, its columns).
-    cl_cgemm<2, 2, 1, false, true>(ny, kx, CB, colT, SC, 1, whs, kx, 1,
+    cl_cgemm<2, 2, 1, false, true>(ny, kx, ncol, colT, SC, 1, whs, kx, 1,
                                 [&](int y, int jx, float2 v) { Tall[y * kx + jx] = v; });
     __syncthreads();
     CL_STAMP(12);
@@ -715,7 +719,8 @@ static size_t cluster_smem(const Dev& d, int C, int RB, int CB, int P) {
                TP = (size_t)(RB + 1) * d.nx;
   const size_t nscr = 2 * GP + HP + 2 * TP;
   const size_t NU = std::max((size_t)C * NA, (nscr + 1) / 2);
-  const size_t f2 = P + (size_t)P * (RB + 1) + (size_t)CB * (d.ny + 1) + 2 * (size_t)d.ny * (CB + 1) + 4 * GP + 2 * HP +
+  const size_t RS = (size_t)((RB + 1) | 1), SC = (size_t)(CB | 1);
+  const size_t f2 = P + (size_t)P * RS + (size_t)CB * (d.ny + 1) + 2 * (size_t)d.ny * SC + 4 * GP + 2 * HP +
                     NA + NU + 2 * (size_t)d.nr +
                     (size_t)d.ny * d.kx + (size_t)d.ky * d.ny + (size_t)d.kx * CB +
                     (size_t)CB * P + (size_t)d.kx * d.nx + NA + (size_t)((d.nr + C - 1) / C) * NA;
@@ -725,9 +730,15 @@ static size_t cluster_smem(const Dev& d, int C, int RB, int CB, int P) {
 // dynamic shared memory limit of the cluster kernel (227 KB per block; no static use)
 static const size_t CL_SMEM_MAX = 226 * 1024;
 
-// Whether cluster size c splits rows and padded columns evenly with ni * c CTAs resident.
+// Rows and padded columns per CTA for cluster size c (the last CTA may own fewer).
+static int cl_rb(const Dev& d, int c) { return (d.ny + c - 1) / c; }
+static int cl_cb(const Dev& d, int c) { return (d.Px + c - 1) / c; }
+
+// Whether cluster size c gives every CTA at least one row and one padded column, with ni * c CTAs
+// resident.
 static bool cluster_ok(const Dev& d, int sms, int c) {
-  return d.ni * c <= sms && d.ny % c == 0 && d.Px % c == 0 && d.ny / c <= 64 && d.nr <= 1024;
+  const int rb = cl_rb(d, c), cb = cl_cb(d, c);
+  return d.ni * c <= sms && (c - 1) * rb < d.ny && (c - 1) * cb < d.Px && rb <= 64 && d.nr <= 1024;
 }
 
 template <int P>
@@ -784,10 +795,12 @@ static int cl_plan(const pdf_problem* h, ClPlanRow* rows, int nmax) {
     cudaGetLastError();
     return 0;
   }
+  static const int sizes[] = {16, 8, 6, 4, 2};
   int n = 0;
-  for (int c = 16; c >= 2 && n < nmax; c >>= 1) {
+  for (int c : sizes) {
+    if (n >= nmax) break;
     if (!cluster_ok(d, sms, c)) continue;
-    const size_t smem = cluster_smem(d, c, d.ny / c, d.Px / c, d.Px);
+    const size_t smem = cluster_smem(d, c, cl_rb(d, c), cl_cb(d, c), d.Px);
     ClPlanRow r = {c, (int)smem, -1, 0};
     if (smem <= CL_SMEM_MAX) {
       r.clusters = d.Px == 64 ? max_active_clusters<64>(d.ni, c, smem) : max_active_clusters<128>(d.ni, c, smem);
@@ -803,8 +816,8 @@ extern "C" int32_t pdf_cluster_plan(pdf_problem* h, int32_t* out, int32_t nmax) 
     set_err(PDF_EINVAL, "pdf_cluster_plan: bad arguments");
     return PDF_EINVAL;
   }
-  ClPlanRow rows[4];
-  const int n = cl_plan(h, rows, std::min(4, (int)nmax));
+  ClPlanRow rows[5];
+  const int n = cl_plan(h, rows, std::min(5, (int)nmax));
   for (int i = 0; i < n; ++i) {
     out[4 * i + 0] = rows[i].C;
     out[4 * i + 1] = rows[i].smem;
@@ -831,8 +844,8 @@ pdf_status cl_run(pdf_problem* h, const pdf_solve_opts* o, int iters, cudaStream
   *done = false;
   const Dev& d = h->d;
   if (iters < 1) return PDF_OK;
-  ClPlanRow rows[4];
-  const int n = cl_plan(h, rows, 4);
+  ClPlanRow rows[5];
+  const int n = cl_plan(h, rows, 5);
   int pick = -1;
   for (int i = 0; i < n && pick < 0; ++i)
     if (rows[i].usable) pick = i;
@@ -840,8 +853,8 @@ pdf_status cl_run(pdf_problem* h, const pdf_solve_opts* o, int iters, cudaStream
   ClusterArgs a;
   a.iters = iters;
   a.C = rows[pick].C;
-  a.RB = d.ny / a.C;
-  a.CB = d.Px / a.C;
+  a.RB = cl_rb(d, a.C);
+  a.CB = cl_cb(d, a.C);
   // Sums over incidences: each CTA reads ni x (RB + 2) x nx float4 when it forms R-hat on its own
   // rows, all CTAs at once, and the phase is bound by L2 bandwidth; the split form costs a second
   // grid barrier and two more L2 round trips instead.  Measured on GB300 (per iteration): 32x32,

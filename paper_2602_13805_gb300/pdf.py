@@ -229,8 +229,8 @@ def pdf_apply_op(h: int, op: int, x, out, stream=None):
 
 def pdf_cluster_plan(h: int):
     """[(C, smem bytes, co-resident clusters, usable)] the cluster loop would consider for handle h."""
-    buf = (ctypes.c_int32 * 16)()
-    n = load().pdf_cluster_plan(h, buf, 4)
+    buf = (ctypes.c_int32 * 20)()
+    n = load().pdf_cluster_plan(h, buf, 5)
     if n < 0:
         _check(n)
     return [tuple(buf[4 * i: 4 * i + 4]) for i in range(n)]

@@ -200,9 +200,7 @@ def run_ours(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    w = scenes.workload(args.workload)
-    if args.iters is not None:
-        w = scenes.workload(args.workload, iters=args.iters)
+    w = bench_workload(args)
     seed = rank
     chi_true = scenes.make_scene(w, seed)
     torch.cuda.synchronize()
@@ -383,9 +381,17 @@ def _oracle_case(w, seed=0):
     return ops, esca, chi
 
 
+def bench_workload(args):
+    """The named workload, with --iters overriding its iteration count (both arms)."""
+    if args.iters is not None:
+        return scenes.workload(args.workload, iters=args.iters)
+    return scenes.workload(args.workload)
+
+
 def cpu_baseline(w, iters, fcnn=0):
     """FP64 oracle on the host: init + `iters` Adam iterations (on alpha, or on the network's
-    weights when fcnn > 0), scaled to a full reconstruction."""
+    weights when fcnn > 0; at most the workload's own count), scaled to a full reconstruction."""
+    iters = min(iters, w.iters)
     from oracle import fcnn as onet
     from oracle import loss, solve
     ops, esca, chi = _oracle_case(w)
@@ -405,7 +411,7 @@ def cpu_baseline(w, iters, fcnn=0):
         for _ in range(iters):
             _, g = loss.loss_grad(ops, esca, a)
             a = opt.step(a, g)
-    t_it = (time.perf_counter() - t0) / iters
+    t_it = (time.perf_counter() - t0) / max(iters, 1)
     ms = (t_init + t_it * w.iters) * 1e3
     return {"value": ms, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"BP+CSI init + {iters} of {w.iters} Adam iterations (FP64 NumPy/SciPy), "
@@ -434,7 +440,7 @@ def run_warm(args):
     import torch
     from paper_2602_13805_gb300 import pdf
     from paper_2602_13805_gb300.warmstart import WarmStartMLP, generate, predict_alpha, train
-    w = scenes.workload(args.workload)
+    w = bench_workload(args)
     prob = pdf.Problem.from_workload(w, fold_gs=args.fold)
     chosen = pdf.Problem.from_workload(w, precision=args.precision, fold_gs=args.fold)
     t0 = time.perf_counter()
@@ -498,8 +504,8 @@ def run_warm(args):
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    w = scenes.workload(args.workload)
-    iters = args.cpu_iters
+    w = bench_workload(args)
+    iters = min(args.cpu_iters, w.iters)
     times = []
     for k in range(args.warmup + args.steps):
         r = cpu_baseline(w, iters, args.fcnn)

@@ -338,8 +338,10 @@ def run_ours(args, rank, world, local):
             "metric": METRIC, "value": ms_per_recon, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "c64 (fp32 complex), fp64 reductions" if args.precision == 0 else
-                     "c64 FFT path + split-BF16 tensor-core contractions (fp32 accumulate), fp64 reductions",
+            "dtype": "f32" if args.precision == 0 else "f32+bf16",
+            "dtype_note": "complex64 (fp32 pairs) throughout, fp64 sums over incidences" if args.precision == 0 else
+                          "complex64 FFT path, split-BF16 tensor-core contractions with fp32 accumulation, "
+                          "fp64 sums over incidences",
             "data": "synthetic (seeded scene, GPU forward solver, AWGN)",
             "config": bench_config(w, args, world),
             "iters_per_s": w.iters * args.steps * world / (total_ms * 1e-3),

@@ -18,7 +18,11 @@ Readings (the paper cites but does not print them):
 
 Pinned by: Adam against torch.optim.Adam, line-search optimality, guided-filter limits
 (eps -> 0 gives the identity, eps -> inf the double box mean, constants pass through).
-The reconstruction error of a whole solve has no printed value in the paper: parity unpinned.
+pdf_solve is pinned as a composition: its first Adam step lowers L at the rate ||g||_1 (Re and
+Im parts) as lr -> 0, which a conjugated gradient or a reversed step breaks; started from the
+exact coefficients of the true currents (K = M, no noise, no regularisers) it returns the true
+contrast after a step bounded by lr max|g| / eps.  The RelErr a whole solve reaches on a given
+workload has no printed value in the paper to compare with.
 """
 from __future__ import annotations
 

@@ -60,3 +60,33 @@ def test_adjoint_without_conjugate_breaks_finite_differences(monkeypatch):
     orig = ops.gd
     monkeypatch.setattr(ops, "gd", lambda J, adjoint=False: orig(J, False))
     assert mismatch() > 1e-3
+
+
+def _first_step_rate():
+    """(L(alpha_0) - L(alpha_1)) / lr of the oracle solve at small lr, and ||g||_1 at alpha_0."""
+    from oracle import solve
+    p = from_workload(scenes.workload("c1", nx=12, ny=12, ni=3, nr=6, kx=5, ky=5))
+    ops = Operators(p, dense_gd=True)
+    chi = scenes.rasterise([scenes.Shape("disk", 0.0, 0.0, 0.4, eps_r=2.0)], 12, 12, 2.0)
+    _, _, esca = forward_solve(ops, chi)
+    rng = np.random.default_rng(1)
+    a0 = 0.2 * (rng.standard_normal((3, 5, 5)) + 1j * rng.standard_normal((3, 5, 5)))
+    _, g = loss.loss_grad(ops, esca, a0)
+    lr = 1e-6
+    out = solve.pdf_solve(ops, esca, 2, lr=lr, alpha0=a0, apply_cco=False, history=True)
+    return (out["losses"][0, 0] - out["losses"][1, 0]) / lr, np.abs(g.real).sum() + np.abs(g.imag).sum()
+
+
+@pytest.mark.parametrize("mistake", ["conjugated_gradient", "ascent"])
+def test_solve_mistakes_break_first_step_descent(monkeypatch, mistake):
+    from oracle import solve
+    rate, l1 = _first_step_rate()
+    assert abs(rate - l1) < 2e-2 * l1
+    if mistake == "conjugated_gradient":
+        good = solve.loss_grad
+        monkeypatch.setattr(solve, "loss_grad", lambda o, e, a: (lambda t, g: (t, np.conj(g)))(*good(o, e, a)))
+    else:
+        good_step = solve.Adam.step
+        monkeypatch.setattr(solve.Adam, "step", lambda self, x, g: 2 * x - good_step(self, x, g))
+    rate, l1 = _first_step_rate()
+    assert abs(rate - l1) > 0.1 * l1

@@ -107,3 +107,42 @@ def test_small_solve_reduces_loss_and_error(c1_small):
     assert L[-1] < 0.7 * L[0]
     chi_init = loss.forward(ops, esca, out["alpha0"]).chi
     assert out["relerr"] < solve.relerr(chi_init, chi)
+
+
+def test_solve_from_the_exact_coefficients():
+    # With no truncation (K = M), noise-free data and no regularisers, alpha = F_T(J_true) makes
+    # both residuals vanish (Eq. 6, 15, 16): the gradient is at rounding level, so the first Adam
+    # step, lr g / (|g| + eps) per real component, moves alpha by at most lr max|g| / eps, and
+    # chi-hat read back from the solve's final alpha is the true contrast.  (Later steps do not
+    # stay put: once |g| exceeds eps, Adam's normalised step is ~lr whatever the gradient's size,
+    # so the exact minimiser is not a fixed point of the loop beyond the first step.)
+    w = scenes.workload("c1", nx=12, ny=12, ni=4, nr=8, kx=12, ky=12)
+    p = from_workload(w, lam_bound=0.0, lam_tv=0.0, lam_bridge=0.0)
+    ops = Operators(p, dense_gd=True)
+    chi = scenes.rasterise([scenes.Shape("disk", 0.1, -0.05, 0.45, eps_r=2.5, tan_d=0.2)], 12, 12, 2.0)
+    J, _, esca = forward_solve(ops, chi)
+    a_star = fbe.analysis(J, 12, 12)
+    terms, g = loss.loss_grad(ops, esca, a_star)
+    gmax = max(np.abs(g.real).max(), np.abs(g.imag).max())
+    assert terms[0] < 1e-24 and gmax < 1e-10
+    out = solve.pdf_solve(ops, esca, 1, alpha0=a_star, chi_true=chi, apply_cco=False)
+    step = out["alpha"] - a_star
+    ulp = np.spacing(np.abs(a_star).max())                 # rounding of alpha + step
+    assert max(np.abs(step.real).max(), np.abs(step.imag).max()) <= 1e-2 * gmax / 1e-8 + 2 * ulp
+    assert out["relerr"] < 1e-6
+
+
+def test_first_adam_step_descends_by_the_l1_norm(c1_small):
+    # At t = 1 Adam moves each real component by -lr g / (|g| + eps), so for small lr
+    # L(alpha_1) = L(alpha_0) - lr ||g||_1 + O(lr^2), with ||g||_1 summed over Re and Im parts in
+    # the gradient convention g = dL/dRe + i dL/dIm.  A conjugated gradient (the sign of the
+    # imaginary part flipped) or a wrong sign in the update breaks the first-order term.
+    p, ops, chi, esca = c1_small
+    _, R0, _ = solve.bp_init(ops, esca)
+    a0 = solve.csi_step(ops, esca, R0)
+    _, g = loss.loss_grad(ops, esca, a0)
+    l1 = np.abs(g.real).sum() + np.abs(g.imag).sum()
+    for lr in (1e-5, 1e-6):
+        out = solve.pdf_solve(ops, esca, 2, lr=lr, alpha0=a0, apply_cco=False, history=True)
+        L0, L1 = out["losses"][0, 0], out["losses"][1, 0]
+        assert abs((L0 - L1) / lr - l1) < 2e-2 * l1, (lr, (L0 - L1) / lr, l1)

@@ -186,6 +186,13 @@ pdf_status pdf_forward(pdf_problem* h, const void* chi, void* esca_out, void* j_
 int32_t pdf_profile_loss_grad(pdf_problem* h, const void* alpha, int32_t reps, float* ms, int32_t n,
                               void* stream);
 
+/* Measured FP32 FMA throughput of the current device, the denominator of the "alu" roofline of
+ * the cluster loop: a kernel of independent fmaf chains filling every SM (occupancy-sized grid,
+ * ~1 ms a launch) runs once to warm up and then `reps` times between two CUDA events on
+ * `stream`; *tflops = 2 x FMAs / elapsed time, in TFLOP/s.  Synchronises `stream`.  Errors:
+ * PDF_EINVAL (reps < 1 or tflops NULL), PDF_ECUDA. */
+pdf_status pdf_fp32_fma_peak(int32_t reps, double* tflops, void* stream);
+
 /* Name of kernel k of pdf_loss_grad in launch order ("" when out of range), FP32 path with the
  * default folded data term (fold_gs = 1). */
 const char* pdf_kernel_name(int32_t k);

@@ -734,6 +734,59 @@ extern "C" int32_t pdf_profile_loss_grad(pdf_problem* h, const void* alpha, int3
   return K;
 }
 
+// FP32 FMA throughput: every thread runs FMA_CHAINS independent multiply-add chains for
+// `steps` rounds (16 rounds unrolled per loop trip, so loop overhead is ~1% of the issue
+// slots); the sum is stored only if it equals `sentinel`, which it never does, so the chains
+// cannot be removed.  m < 1 and c > 0 keep every value finite and normal.
+constexpr int FMA_CHAINS = 8;
+__global__ void __launch_bounds__(256) k_fma_peak(float* out, int steps, float m, float c, float sentinel) {
+  float a[FMA_CHAINS];
+#pragma unroll
+  for (int i = 0; i < FMA_CHAINS; ++i) a[i] = (float)(threadIdx.x + i) * 1e-3f;
+  for (int k = 0; k < steps; k += 16) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+#pragma unroll
+      for (int i = 0; i < FMA_CHAINS; ++i) a[i] = fmaf(a[i], m, c);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < FMA_CHAINS; ++i) s += a[i];
+  if (s == sentinel) out[0] = s;
+}
+
+extern "C" pdf_status pdf_fp32_fma_peak(int32_t reps, double* tflops, void* stream) {
+  if (reps < 1 || !tflops) return set_err(PDF_EINVAL, "pdf_fp32_fma_peak: reps must be >= 1 and tflops non-NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fma_peak, 256, 0);
+  if (e != cudaSuccess) return cuda_err(e, "pdf_fp32_fma_peak: device query");
+  const int blocks = sms * std::max(per_sm, 1), steps = 16384;
+  float* out = nullptr;
+  e = cudaMalloc(&out, sizeof(float));
+  if (e != cudaSuccess) return cuda_err(e, "pdf_fp32_fma_peak: cudaMalloc");
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  k_fma_peak<<<blocks, 256, 0, s>>>(out, steps, 0.9999999f, 1e-7f, -1.2345e30f);   // warm-up
+  cudaEventRecord(a, s);
+  for (int r = 0; r < reps; ++r) k_fma_peak<<<blocks, 256, 0, s>>>(out, steps, 0.9999999f, 1e-7f, -1.2345e30f);
+  cudaEventRecord(b, s);
+  e = cudaEventSynchronize(b);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(out);
+  if (e != cudaSuccess) return cuda_err(e, "pdf_fp32_fma_peak");
+  pdf_count_launch(reps + 1);
+  const double flops = 2.0 * FMA_CHAINS * steps * 256.0 * blocks * reps;
+  *tflops = flops / (ms * 1e-3) / 1e12;
+  return PDF_OK;
+}
+
 extern "C" const char* pdf_kernel_name(int32_t k) { return hp_kernel_name(k, 0, 1); }
 
 extern "C" const char* pdf_stage_name(pdf_problem* h, int32_t k) {

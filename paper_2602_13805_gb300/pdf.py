@@ -82,7 +82,7 @@ EXPORTS = ("pdf_config_default", "pdf_setup", "pdf_set_data", "pdf_loss_grad", "
            "pdf_last_error", "pdf_profile_loss_grad", "pdf_kernel_name", "pdf_gs_apply_static",
            "pdf_stage_name", "pdf_mlp_create", "pdf_mlp_destroy", "pdf_mlp_set_params", "pdf_mlp_get_params",
            "pdf_mlp_forward", "pdf_mlp_loss_grad", "pdf_mlp_train_step", "pdf_mlp_error_flag",
-           "pdf_phase_stamps", "pdf_cluster_plan")
+           "pdf_phase_stamps", "pdf_cluster_plan", "pdf_fp32_fma_peak")
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -118,6 +118,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pdf_profile_loss_grad.restype = i32
     lib.pdf_phase_stamps.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
     lib.pdf_phase_stamps.restype = ctypes.c_int
+    lib.pdf_fp32_fma_peak.argtypes = [i32, ctypes.POINTER(dbl), vp]
+    lib.pdf_fp32_fma_peak.restype = ctypes.c_int
     lib.pdf_cluster_plan.argtypes = [vp, ctypes.POINTER(i32), i32]
     lib.pdf_cluster_plan.restype = i32
     lib.pdf_kernel_name.argtypes = [i32]
@@ -265,6 +267,13 @@ def pdf_destroy(h: int):
 
 def pdf_launch_count() -> int:
     return int(load().pdf_launch_count())
+
+
+def pdf_fp32_fma_peak(reps: int = 10, stream=None) -> float:
+    """Measured FP32 FMA throughput of the current device, TFLOP/s."""
+    out = ctypes.c_double(0.0)
+    _check(load().pdf_fp32_fma_peak(reps, ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 def pdf_profile_loss_grad(h: int, alpha, reps: int = 20, stream=None):

@@ -86,3 +86,9 @@ def _load_fresh(pdf, path):
         pdf.load(path)
     finally:
         pdf._lib = saved
+
+
+def test_fma_peak_rejects_bad_arguments_without_gpu(lib):
+    out = ctypes.c_double(0.0)
+    assert lib.pdf_fp32_fma_peak(0, ctypes.byref(out), None) == -1
+    assert lib.pdf_fp32_fma_peak(3, None, None) == -1

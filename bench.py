@@ -366,6 +366,8 @@ def run_ours(args, rank, world, local):
                           "fp64 sums over incidences",
             "data": "synthetic (seeded scene, GPU forward solver, AWGN)",
             "config": bench_config(w, args, world),
+            "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms),
+                        "note": "rank 0's timed steps; value is their mean (max over ranks)"},
             "iters_per_s": (w.iters * world / (loop_ms * 1e-3)) if loop_ms else None,
             "iters_per_s_note": "iterations / loop time (the solve minus the same solve with 0 "
                                 "iterations), all ranks",

@@ -20,9 +20,10 @@ def _w(name, over):
     return scenes.workload(base, **over)
 
 
-# register-FFT path (default) on every geometry, the generic shared-memory FFT on two, and the
-# unfolded data term (G_S applied to J every evaluation) on two
+# register-FFT path (default) on every geometry up to the largest accepted grid (256 x 256), the
+# generic shared-memory FFT on two, and the unfolded data term (G_S applied to J every evaluation) on two
 PARITY_CASES = [(n, o, {}) for n, o in SMALL_CASES] + [("c2", dict(), {})] + [
+    ("g256", dict(nx=256, ny=256, ni=2, nr=8, kx=9, ky=9), {}),     # largest grid: 512-point lines (R = 16)
     ("g24x20-smemfft", dict(nx=24, ny=20, ni=5, nr=7, kx=7, ky=5), dict(fft_path=1)),
     ("c1-smemfft", dict(), dict(fft_path=1)),
     ("c1-unfolded", dict(), dict(fold_gs=0)),
@@ -116,6 +117,11 @@ def test_gradient_heavy_regularisers():
     prob.close()
 
 
+def terms_of(prob, a):
+    t, _ = prob.loss_grad(a.detach().contiguous())
+    return abs(t[0].item())
+
+
 def test_autograd_function_and_central_differences(case):
     from paper_2602_13805_gb300 import pdf
     prob = case.prob
@@ -124,18 +130,22 @@ def test_autograd_function_and_central_differences(case):
     L.backward()
     _, g = prob.loss_grad(a.detach())
     assert torch.equal(a.grad, g)
-    # central differences of the FP64-reduced loss along a random direction (h = 1e-4 relative)
+    # central differences of the FP64-reduced loss along a random direction (h = 1e-3 relative)
     rng = np.random.default_rng(9)
     d = torch.tensor(scenes.random_coeffs(*a.shape, 1.0, rng).astype(np.complex64), device="cuda")
-    h = 1e-4 * a.detach().abs().max().item() / d.abs().max().item()
+    h = 1e-3 * a.detach().abs().max().item() / d.abs().max().item()
     tp, _ = prob.loss_grad((a.detach() + h * d).contiguous())
     tm, _ = prob.loss_grad((a.detach() - h * d).contiguous())
     fd = (tp[0] - tm[0]).item() / (2 * h)
     an = torch.sum(torch.real(torch.conj(g) * d)).item()
-    # the loss is evaluated from FP32 fields (relative rounding ~1e-7), so a central difference with
-    # h = 1e-4 resolves the directional derivative to ~1e-3; the 1e-5 gradient contract is checked
-    # against the FP64 oracle in test_loss_and_gradient
-    assert abs(fd - an) < 5e-3 * abs(an) + 1e-6
+    # The loss is evaluated from FP32 fields, so each evaluation carries a rounding error of about
+    # one FP32 unit roundoff u = 2^-24 of L (measured 1.0 u L at 256 x 256): the difference quotient
+    # has a noise floor of ~u L / h, allowed four times over, on top of 5e-3 of the derivative for
+    # the O(h^2) truncation.  The 1e-5 gradient contract is checked against the FP64 oracle in
+    # test_loss_and_gradient.
+    u = 2.0 ** -24
+    L0 = terms_of(prob, a)
+    assert abs(fd - an) < 5e-3 * abs(an) + 4 * u * L0 / h, (fd, an, u * L0 / h)
 
 
 def test_forward_solver_matches_oracle(case):

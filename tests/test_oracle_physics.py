@@ -113,3 +113,28 @@ def test_iterative_matches_dense():
     J1, _, e1 = forward_solve(ops, chi, dense_max=4096)
     J2, _, e2 = forward_solve(Operators(p), chi, dense_max=0)
     assert np.linalg.norm(e1 - e2) / np.linalg.norm(e1) < 1e-8
+
+
+@pytest.mark.parametrize("eps_r", [1.5, 2.0, 3.5, 5.0])
+@pytest.mark.parametrize("k0a", [0.3, 1.5, 4.0])
+def test_mie_partial_waves_conserve_energy(eps_r, k0a):
+    # Outside the cylinder partial wave n is J_n + a_n H_n = (H_n^(2) + (1 + 2 a_n) H_n^(1)) / 2:
+    # incoming amplitude 1/2, outgoing (1 + 2 a_n) / 2.  A lossless cylinder returns all incoming
+    # power, so |S_n| = |1 + 2 a_n| = 1 for every n.  This checks the matching algebra
+    # independently (a sign error in a_n breaks it).  It cannot see a conjugated a_n (H^(2) for
+    # H^(1), the other time convention), which the absorption test below catches.
+    from oracle.mie import mie_coeffs
+    k0 = 2 * np.pi
+    an = mie_coeffs(k0, k0a / k0, eps_r, 30)
+    assert np.abs(np.abs(1 + 2 * an) - 1).max() < 1e-10
+
+
+def test_mie_lossy_cylinder_absorbs():
+    # With the e^{-i w t} convention a medium with Im eps_r > 0 absorbs: every |S_n| <= 1, and the
+    # low orders, which carry the power into the cylinder, lose a visible part of it.
+    from oracle.mie import mie_coeffs
+    k0 = 2 * np.pi
+    an = mie_coeffs(k0, 0.4, 2.5 * (1 + 0.3j), 30)
+    s = np.abs(1 + 2 * an)
+    assert s.max() <= 1 + 1e-12
+    assert s[30] < 0.99 and s[31] < 0.99 and s[29] < 0.99            # n = 0, +1, -1

@@ -90,3 +90,25 @@ def test_solve_mistakes_break_first_step_descent(monkeypatch, mistake):
         monkeypatch.setattr(solve.Adam, "step", lambda self, x, g: 2 * x - good_step(self, x, g))
     rate, l1 = _first_step_rate()
     assert abs(rate - l1) > 0.1 * l1
+
+
+def test_mie_mistakes_break_energy_pins(monkeypatch):
+    # H^(2) in place of H^(1) (the e^{+i w t} convention) turns the lossy cylinder into a gain
+    # medium; a sign error in a_n breaks lossless unitarity.
+    from scipy import special
+    from oracle import mie
+    good = mie.mie_coeffs
+
+    def lossless_err():
+        return np.abs(np.abs(1 + 2 * mie.mie_coeffs(2 * np.pi, 0.4, 3.5, 30)) - 1).max()
+
+    def lossy_gain():
+        return np.abs(1 + 2 * mie.mie_coeffs(2 * np.pi, 0.4, 2.5 * (1 + 0.3j), 30)).max()
+    assert lossless_err() < 1e-10 and lossy_gain() <= 1 + 1e-12
+    fake = type("special", (), {"jv": special.jv, "jvp": special.jvp,
+                                "hankel1": special.hankel2, "h1vp": special.h2vp})
+    monkeypatch.setattr(mie, "special", fake)
+    assert lossy_gain() > 1.01
+    monkeypatch.setattr(mie, "special", special)
+    monkeypatch.setattr(mie, "mie_coeffs", lambda *a: -good(*a))
+    assert lossless_err() > 1e-2

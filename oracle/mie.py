@@ -14,6 +14,9 @@ and, by Graf's addition theorem H0(k0|r - r_s|) = sum_n J_n(k0 rho) H_n(k0 rho_s
 (rho < rho_s), the scattered field at rho > a
 
     E_sca(rho, phi) = sum_n a_n H_n(k0 rho_s) H_n(k0 rho) e^{in(phi - phi_s)} / |H0(k0 rho_s)|.
+
+Pinned by energy conservation (tests/test_oracle_physics.py): every partial wave of a lossless
+cylinder has |1 + 2 a_n| = 1, and a lossy one (Im eps_r > 0) absorbs, |1 + 2 a_n| < 1.
 """
 from __future__ import annotations
 

@@ -3,6 +3,10 @@
 The DOI is an M1 x M2 grid of square-ish pulse cells centred on the origin
 (Sec. 2, "discretized into an M1 x M2 uniform grid").  Lengths are in
 wavelengths when k0 = 2*pi.  Arrays over the grid are [y][x] with x fastest.
+
+Pinned by tests/test_oracle_physics.py::test_grid_geometry: centres symmetric about the origin
+with spacing side / n, half a cell clear of the edges, the equal-area Richmond radius, and the
+same centres as the scene rasteriser.
 """
 from __future__ import annotations
 

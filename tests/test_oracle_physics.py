@@ -138,3 +138,19 @@ def test_mie_lossy_cylinder_absorbs():
     s = np.abs(1 + 2 * an)
     assert s.max() <= 1 + 1e-12
     assert s[30] < 0.99 and s[31] < 0.99 and s[29] < 0.99            # n = 0, +1, -1
+
+
+def test_grid_geometry():
+    # Sec. 2: an M1 x M2 uniform grid over a DOI centred on the origin.  Cell centres are
+    # symmetric about 0 with spacing side / n and half a cell clear of the edges; the Richmond
+    # disk has the cell's area; the scene rasteriser samples the same centres.
+    p = Problem(nx=24, ny=20, side_x=2.0, side_y=1.5, k0=2 * np.pi, tx=np.zeros((1, 2)), rx=np.zeros((1, 2)),
+                kx=5, ky=5)
+    X, Y = p.centres()
+    assert X.shape == (20, 24) and Y.shape == (20, 24)
+    assert np.allclose(X[0], -X[0, ::-1]) and np.allclose(Y[:, 0], -Y[::-1, 0])
+    assert np.allclose(np.diff(X[0]), 2.0 / 24) and np.allclose(np.diff(Y[:, 0]), 1.5 / 20)
+    assert np.isclose(X[0, 0], -1.0 + 1.0 / 24) and np.isclose(Y[-1, 0], 0.75 - 0.75 / 20)
+    assert np.isclose(np.pi * p.a_eq ** 2, (2.0 / 24) * (1.5 / 20))
+    Xs, Ys = scenes.pixel_centres(24, 20, 2.0, 1.5)
+    assert np.array_equal(X, Xs) and np.array_equal(Y, Ys)

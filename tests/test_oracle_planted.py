@@ -112,3 +112,33 @@ def test_mie_mistakes_break_energy_pins(monkeypatch):
     monkeypatch.setattr(mie, "special", special)
     monkeypatch.setattr(mie, "mie_coeffs", lambda *a: -good(*a))
     assert lossless_err() > 1e-2
+
+
+def _periodic_fdiff(a):
+    return np.roll(a, -1, axis=1) - a, np.roll(a, -1, axis=0) - a
+
+
+def _adjoint_without_outflow(cx, cy):
+    out = np.zeros_like(cx)
+    out[:, 1:] += cx[:, :-1]
+    out[1:, :] += cy[:-1, :]
+    return out
+
+
+@pytest.mark.parametrize("mistake", ["periodic_differences", "flipped_sigmoid", "half_adjoint"])
+def test_regulariser_mistakes_break_their_pins(monkeypatch, mistake):
+    # Eq. 17-19: each plant must fail the pin that guards it: the closed forms of the regularisers
+    # on constant, step and ramp images (boundary and sigmoid direction), or the central
+    # differences of the loss with heavy regulariser weights (the adjoint of the differences).
+    from tests import test_oracle_loss as pins
+    if mistake == "periodic_differences":
+        monkeypatch.setattr(loss, "_fdiff", _periodic_fdiff)
+        check = pins.test_regulariser_closed_forms
+    elif mistake == "flipped_sigmoid":
+        monkeypatch.setattr(loss, "_sigmoid", lambda x: 1.0 / (1.0 + np.exp(x)))
+        check = pins.test_regulariser_closed_forms
+    else:
+        monkeypatch.setattr(loss, "_fdiff_adjoint", _adjoint_without_outflow)
+        check = lambda: pins.test_gradient_central_differences((1.0, 0.3, 0.5))   # noqa: E731
+    with pytest.raises(AssertionError):
+        check()

@@ -142,3 +142,32 @@ def test_regulariser_mistakes_break_their_pins(monkeypatch, mistake):
         check = lambda: pins.test_gradient_central_differences((1.0, 0.3, 0.5))   # noqa: E731
     with pytest.raises(AssertionError):
         check()
+
+
+@pytest.mark.parametrize("mistake", ["floor_half_set", "unnormalised_synthesis", "analysis_with_inverse_dft"])
+def test_fbe_mistakes_break_their_pins(monkeypatch, mistake):
+    # Eq. 9: a mode set shifted by one for odd K, a synthesis without the unitary 1/sqrt(M), and an
+    # analysis that uses the inverse DFT (the conjugate basis) each fail the brute-force basis sums
+    # or the adjoint / left-inverse identities.
+    from oracle import fbe
+    from tests import test_oracle_fbe as pins
+    good_synth = fbe.synth
+    if mistake == "floor_half_set":
+        monkeypatch.setattr(fbe, "mode_indices",
+                            lambda K, M: np.array([j if j < K // 2 else M - K + j for j in range(K)]))
+    elif mistake == "unnormalised_synthesis":
+        monkeypatch.setattr(fbe, "synth", lambda a, ny, nx: good_synth(a, ny, nx) * np.sqrt(ny * nx))
+    else:
+        def bad_analysis(J, ky, kx):
+            ny, nx = J.shape[-2:]
+            iy, ix = fbe.mode_indices(ky, ny), fbe.mode_indices(kx, nx)
+            return np.fft.ifft2(J, norm="ortho")[..., iy[:, None], ix[None, :]]
+        monkeypatch.setattr(fbe, "analysis", bad_analysis)
+    failed = 0
+    for check in (lambda: pins.test_synth_is_sum_of_basis_functions(6, 8, 3, 5),
+                  pins.test_analysis_is_adjoint_and_left_inverse):
+        try:
+            check()
+        except AssertionError:
+            failed += 1
+    assert failed >= 1

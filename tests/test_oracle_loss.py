@@ -142,3 +142,18 @@ def test_gradient_of_each_component_by_differences():
             e[idx] = unit
             fd = (loss.loss(ops, esca, a + h * e)[0] - loss.loss(ops, esca, a - h * e)[0]) / (2 * h)
             assert abs(fd - part(g[idx])) < 1e-7 * max(abs(g).max(), 1e-3)
+
+
+def test_terms_at_zero_coefficients():
+    # alpha = 0: J = 0, so s = E_inc and the least-squares R-hat is 0 (Eq. 6), r = 0 and
+    # L_State = 0 (Eq. 15); r_d = -E_sca, so L_Data = ||E_sca||^2 / ||E_sca||^2 = 1 exactly (Eq. 16);
+    # chi-hat = 0 gives L_Bound = 0, L_TV = M sqrt(eps_TV) and L_Bridge = M sigmoid((sqrt(eps_abs)
+    # - tau_B) / tau_B) (Eq. 17-19, all differences zero); L is their weighted sum (Eq. 13).
+    p, ops, chi, J, esca = _setup()
+    t = loss.forward(ops, esca, np.zeros((p.ni, p.ky, p.kx), complex)).terms
+    m = p.nx * p.ny
+    assert t[1] == 0.0 and abs(t[2] - 1.0) < 1e-15 and t[3] == 0.0
+    assert abs(t[4] - m * np.sqrt(p.eps_tv)) < 1e-15
+    br = m / (1.0 + np.exp(-(np.sqrt(p.eps_abs) - p.tau_b) / p.tau_b))
+    assert abs(t[5] - br) < 1e-12 * br
+    assert abs(t[0] - (1.0 + p.lam_tv * t[4] + p.lam_bridge * t[5])) < 1e-15

@@ -171,3 +171,19 @@ def test_fbe_mistakes_break_their_pins(monkeypatch, mistake):
         except AssertionError:
             failed += 1
     assert failed >= 1
+
+
+@pytest.mark.parametrize("mistake", ["chi_with_1_plus_R", "swapped_norms"])
+def test_cie_and_normalisation_mistakes_break_their_pins(monkeypatch, mistake):
+    # Eq. 7 read as chi = R / (beta (1 + R)) fails the CIE identity at the exact solution; the
+    # incident and measured norms swapped (Eq. 15, 16) fail L_Data = 1 at zero coefficients.
+    from tests import test_oracle_loss as pins
+    if mistake == "chi_with_1_plus_R":
+        monkeypatch.setattr(loss, "chi_from_R", lambda R, beta, q_min: (R / (beta * (1.0 + R)), np.zeros(R.shape, bool)))
+        check = pins.test_cie_identity_at_exact_solution
+    else:
+        good = loss.norms
+        monkeypatch.setattr(loss, "norms", lambda ops, esca: good(ops, esca)[::-1])
+        check = pins.test_terms_at_zero_coefficients
+    with pytest.raises(AssertionError):
+        check()

@@ -62,3 +62,18 @@ def test_two_replicas_take_the_slowest_rank():
 def test_single_rank_needs_no_collective():
     per_recon, e2e, total = bench.combine_ranks(80.0, 90.0, 4, 1, "cpu")
     assert (per_recon, e2e, total) == (20.0, 90.0, 80.0)
+
+
+@pytest.mark.parametrize("name,bmin_mb,bmodel_mb,half_unit", [("c1", 0.33, 0.98, 0.005), ("c2", 2.6, 7.9, 0.05),
+                                                              ("c3", 23.6, 70.8, 0.05), ("c5", 94.4, 283.1, 0.05)])
+def test_byte_models_per_iteration(name, bmin_mb, bmodel_mb, half_unit):
+    # B_min = U + 2|G_S| and B_model = 11 U + 2|G_S| (U = Ni M 8 B, |G_S| = Nr M 8 B) for the
+    # workload sizes; the fractions divide them by the loop time per iteration and the copy peak
+    import scenes
+    w = scenes.workload(name)
+    m = bench.hbm_model(w, loop_ms=w.iters * 1e-3, peaks={"hbm_gbs": 1000.0})   # 1 us per iteration
+    assert abs(m["B_min_MB"] - bmin_mb) <= half_unit            # the figures as printed, rounded
+    assert abs(m["B_model_MB"] - bmodel_mb) <= half_unit
+    assert abs(m["t_iter_us"] - 1.0) < 1e-9
+    assert abs(m["frac_min"] - m["B_min_MB"] * 1e6 / 1e-6 / 1e12) < 1e-9 * m["frac_min"]
+    assert bench.hbm_model(w, None, {}) is None

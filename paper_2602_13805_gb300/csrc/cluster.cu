@@ -859,7 +859,9 @@ pdf_status cl_run(pdf_problem* h, const pdf_solve_opts* o, int iters, cudaStream
   // rows, all CTAs at once, and the phase is bound by L2 bandwidth; the split form costs a second
   // grid barrier and two more L2 round trips instead.  Measured on GB300 (per iteration): 32x32,
   // Ni = 8, 8-CTA clusters (24 KB per CTA) 10.5 us per CTA vs 12.3 us split; 64x64, Ni = 16, 4-CTA
-  // clusters (295 KB) 31.6 vs 29.6 us; 64x64, Ni = 36 (663 KB) 35.6 vs 30.7 us.
+  // clusters (295 KB) 31.6 vs 29.6 us; 64x64, Ni = 36 (663 KB) 35.6 vs 30.7 us.  With 6-CTA
+  // clusters at 64x64, Ni = 16 (213 KB per CTA) a 256 KB threshold, i.e. the unsplit form, timed
+  // the same as the split one, so 128 KB stays.
   const int nb = d.ni * a.C;
   const size_t rep_bytes = (size_t)d.ni * (a.RB + 2) * d.nx * sizeof(float4);
   a.sl = rep_bytes > 128 * 1024 ? (d.M + nb - 1) / nb : 0;

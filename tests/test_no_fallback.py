@@ -40,3 +40,11 @@ def test_package_never_imports_the_oracle():
             if f.endswith(".py"):
                 src = open(os.path.join(dirpath, f)).read()
                 assert not pat.search(src), os.path.join(dirpath, f)
+
+
+def test_oracle_never_imports_the_package():
+    pat = re.compile(r"paper_2602_13805_gb300|libpdf")
+    odir = os.path.join(ROOT, "oracle")
+    for f in os.listdir(odir):
+        if f.endswith(".py"):
+            assert not pat.search(open(os.path.join(odir, f)).read()), f

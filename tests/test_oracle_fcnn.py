@@ -111,3 +111,20 @@ def test_reparam_solve_lowers_the_loss():
     out = fcnn.reparam_solve(ops, esca, 30, th, H, lr=1e-2, alpha0=a0, chi_true=chi, history=True)
     L = out["losses"][:, 0]
     assert L[-1] < 0.5 * L[0]
+
+
+def test_identity_network_closed_form():
+    # H = D, W1 = W2 = W3 = I and zero biases: the network passes the positive part of its input,
+    # y = ReLU(s x), so Delta alpha = (max(Re alpha_0, 0) + i max(Im alpha_0, 0)) s / s: the input
+    # scale, the (Re, Im) packing, the ReLUs and the layer layout of the flat vector, all by hand.
+    k = 3
+    D = 2 * k * k
+    eye = np.eye(D)
+    th = np.concatenate([eye.ravel(), np.zeros(D), eye.ravel(), np.zeros(D), eye.ravel(), np.zeros(D)])
+    rng = np.random.default_rng(3)
+    a0 = rng.standard_normal((2, k, k)) + 1j * rng.standard_normal((2, k, k))
+    a, _, s = fcnn.alpha_of(th, a0, D)
+    ref = a0 + np.maximum(a0.real, 0) + 1j * np.maximum(a0.imag, 0)
+    assert np.abs(a - ref).max() < 1e-14
+    X = np.concatenate([a0.real.reshape(2, -1), a0.imag.reshape(2, -1)], axis=1)
+    assert abs(s * np.sqrt(np.mean(X ** 2)) - 1.0) < 1e-14

@@ -77,3 +77,32 @@ def test_byte_models_per_iteration(name, bmin_mb, bmodel_mb, half_unit):
     assert abs(m["t_iter_us"] - 1.0) < 1e-9
     assert abs(m["frac_min"] - m["B_min_MB"] * 1e6 / 1e-6 / 1e12) < 1e-9 * m["frac_min"]
     assert bench.hbm_model(w, None, {}) is None
+
+
+def test_clock_sampler_parses_reasons(tmp_path, monkeypatch):
+    # a stand-in nvidia-smi printing three samples (one with the power cap active) then idling
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    "echo '0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "echo '0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active'\n"
+                    "echo '0, 2040, 2070, 1200.5, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}:{os.environ['PATH']}")
+    import time
+    c = bench.Clocks(0)
+    c.start()
+    for _ in range(100):
+        if len(c.lines) >= 3:
+            break
+        time.sleep(0.05)
+    out = c.stop()
+    assert out["samples"] == 3 and out["sm_mhz"] == 2040.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_sampler_without_nvidia_smi(monkeypatch, tmp_path):
+    monkeypatch.setenv("PATH", str(tmp_path))
+    c = bench.Clocks(0)
+    c.start()
+    assert c.stop()["reasons"] == ["nvidia-smi unavailable"]

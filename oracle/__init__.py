@@ -14,7 +14,8 @@ Modules
   mie       Bessel-series scattered field of a homogeneous cylinder (independent pin)
   fbe       truncated Fourier basis expansion J = F*_T(alpha), alpha = F_T(J)      (Eq. 9)
   loss      the composite loss L and its hand-derived gradient dL/d alpha      (Eq. 6, 7, 13-19)
-  solve     BP + one-step CSI initialisation (Eq. 12), Adam loop, CCO (Eq. 10, 11), RelErr
+  cco       contrast-compensated operator (Eq. 10, 11) with the self-guided filter, and its adjoint
+  solve     BP + one-step CSI initialisation (Eq. 12), Adam loop, final CCO, RelErr
   mlp       FP64 reference of the warm-start network forward/backward
 
 Parity status of each function is stated in its docstring ("pinned by ..." or

@@ -13,6 +13,9 @@ Forward, for coefficients alpha [ni][ky][kx]:
   L_TV     = sum sqrt(|chi_{i,j+1}-chi_{i,j}|^2 + |chi_{i+1,j}-chi_{i,j}|^2 + eps_tv)   (Eq. 18)
   L_Bridge = sum sigmoid((|chi|-tau_B)/tau_B) exp(-|grad|chi||^2)                    (Eq. 19)
   L = L_State + L_Data + lam1 L_Bound + lam2 L_TV + lam3 L_Bridge                   (Eq. 13, 14)
+With Problem.cco_in_loss the three regularisers act on chi_CCO = (1 + eta) G(chi|chi) + eta chi
+(Eq. 10, 11; oracle/cco.py) instead of chi, and their cotangent returns to chi through the CCO's
+adjoint before it continues to R and J.
 
 Readings: differences are forward differences in pixel units, a difference
 that would leave the grid is zero; |chi| = sqrt(|chi|^2 + eps_abs).
@@ -33,6 +36,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
+from . import cco as ccomod
 from . import fbe
 from .green import Operators
 
@@ -102,6 +106,7 @@ class Forward:
     R: np.ndarray
     chi: np.ndarray
     clamped: np.ndarray
+    chi_reg: np.ndarray         # the image the regularisers act on: chi, or chi_CCO with cco_in_loss
     r: np.ndarray
     rd: np.ndarray
     terms: np.ndarray           # [L, State, Data, Bound, TV, Bridge]
@@ -126,9 +131,11 @@ def forward(ops: Operators, esca: np.ndarray, alpha: np.ndarray) -> Forward:
     ein2, esc2 = norms(ops, esca)
     l_state = float(np.sum(np.abs(r) ** 2)) / ein2
     l_data = float(np.sum(np.abs(rd) ** 2)) / esc2
-    (lb, ltv, lbr), _ = reg_terms(p, chi)
+    chi_reg = ccomod.cco(chi, p.cco_radius, p.cco_eps, p.cco_eta_max, p.cco_tau, p.cco_delta) \
+        if p.cco_in_loss else chi
+    (lb, ltv, lbr), _ = reg_terms(p, chi_reg)
     total = l_state + l_data + p.lam_bound * lb + p.lam_tv * ltv + p.lam_bridge * lbr
-    return Forward(J, GJ, s, N, D, R, chi, clamped, r, rd,
+    return Forward(J, GJ, s, N, D, R, chi, clamped, chi_reg, r, rd,
                    np.array([total, l_state, l_data, lb, ltv, lbr]))
 
 
@@ -146,7 +153,9 @@ def loss_grad(ops: Operators, esca: np.ndarray, alpha: np.ndarray):
 
     # Regulariser cotangent on chi, pulled back to R through chi = R / (beta (1 - R)):
     # d chi / d R = 1 / (beta (1 - R)^2) (holomorphic), zero where the clamp is active.
-    _, c_chi = reg_terms(p, f.chi)
+    _, c_chi = reg_terms(p, f.chi_reg)
+    if p.cco_in_loss:
+        c_chi = ccomod.cco_vjp(f.chi, c_chi, p.cco_radius, p.cco_eps, p.cco_eta_max, p.cco_tau, p.cco_delta)
     dchi_dR = 1.0 / (beta * (1.0 - f.R) ** 2)
     c_R = np.where(f.clamped, 0.0, np.conj(dchi_dR) * c_chi)
     # R = N / D with N = sum beta J conj(s), D = sum |s|^2:  w = c_R / D

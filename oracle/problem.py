@@ -36,6 +36,15 @@ class Problem:
     eps_tv: float = 1e-8        # smoothing inside the TV square root (reading: Eq. 18 is not differentiable at 0)
     eps_abs: float = 1e-12      # smoothing inside |chi| of the bridge loss (reading of Eq. 19)
     q_min: float = 1e-6         # clamp of |1 - R| in chi = R / (beta (1 - R)) (reading of Eq. 7 near R = 1)
+    # CCO of Sec. 2.4 (Eq. 10, 11): guided-filter box radius and regulariser, gain eta_max, tau, delta.
+    # cco_in_loss: the regularisers of Eq. (17)-(19) act on chi_CCO instead of chi-hat (the CCO inside
+    # the loss); otherwise the CCO only post-processes the solve's output.
+    cco_in_loss: bool = False
+    cco_radius: int = 2
+    cco_eps: float = 1e-2
+    cco_eta_max: float = 0.1
+    cco_tau: float = 3.0
+    cco_delta: float = 0.5
 
     @property
     def ni(self) -> int:

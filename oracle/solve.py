@@ -3,7 +3,7 @@
   bp_init     back-propagation contrast chi_(0) and R_(0) = beta chi / (beta chi + 1)   (Sec. 3.1, Eq. 7)
   csi_step    alpha_(0) = one gradient step of L^CSI from alpha = 0 at fixed R_(0)     (Sec. 3.1, Eq. 12)
   adam        torch.optim.Adam semantics on (Re, Im) pairs, lr 1e-2                     (Sec. 3.3)
-  cco         contrast-compensated operator with a self-guided filter                   (Sec. 2.4, Eq. 10, 11)
+  cco         contrast-compensated operator with a self-guided filter (oracle/cco.py)   (Sec. 2.4, Eq. 10, 11)
   relerr      ||chi - chi_true|| / ||chi_true||
   pdf_solve   the whole reconstruction: init, Adam loop on L, final chi, CCO
 
@@ -29,6 +29,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import fbe
+from .cco import box_mean, cco, guided_self  # noqa: F401  (the CCO of the final output)
 from .green import Operators
 from .loss import chi_from_R, loss_grad, forward, norms
 
@@ -101,35 +102,6 @@ class Adam:
         return xr[..., 0] + 1j * xr[..., 1]
 
 
-def box_mean(a: np.ndarray, r: int) -> np.ndarray:
-    """Mean over the (2r+1)^2 window clipped to the grid (divided by the in-bounds count)."""
-    ny, nx = a.shape
-    out = np.zeros_like(a)
-    for i in range(ny):
-        i0, i1 = max(0, i - r), min(ny, i + r + 1)
-        for j in range(nx):
-            j0, j1 = max(0, j - r), min(nx, j + r + 1)
-            out[i, j] = a[i0:i1, j0:j1].mean()
-    return out
-
-
-def guided_self(I: np.ndarray, r: int, eps: float) -> np.ndarray:
-    """Self-guided filter G(I | I) of a real image (He et al., guide = input)."""
-    mu = box_mean(I, r)
-    var = box_mean(I * I, r) - mu * mu
-    a = var / (var + eps)
-    b = mu - a * mu
-    return box_mean(a, r) * I + box_mean(b, r)
-
-
-def cco(chi: np.ndarray, r: int = 2, eps: float = 1e-2, eta_max: float = 0.1, tau: float = 3.0,
-        delta: float = 0.5, unsharp: bool = False) -> np.ndarray:
-    """chi_CCO = (1 + eta) G(chi|chi) + eta chi, eta = eta_max sigmoid((|chi| - tau)/delta)  (Eq. 10, 11)."""
-    g = guided_self(chi.real, r, eps) + 1j * guided_self(chi.imag, r, eps)
-    eta = eta_max / (1.0 + np.exp(-(np.abs(chi) - tau) / delta))
-    return (1.0 + eta) * g + (-eta if unsharp else eta) * chi
-
-
 def relerr(chi: np.ndarray, chi_true: np.ndarray) -> float:
     return float(np.linalg.norm(chi - chi_true) / np.linalg.norm(chi_true))
 
@@ -154,7 +126,8 @@ def pdf_solve(ops: Operators, esca: np.ndarray, iters: int, lr: float = 1e-2, al
         alpha = opt.step(alpha, g)
     chi = final_chi(ops, esca, alpha)
     out = dict(alpha=alpha, alpha0=alpha0, chi=chi, losses=np.array(losses))
-    out["chi_cco"] = cco(chi) if apply_cco else chi
+    p = ops.p
+    out["chi_cco"] = cco(chi, p.cco_radius, p.cco_eps, p.cco_eta_max, p.cco_tau, p.cco_delta) if apply_cco else chi
     if chi_true is not None:
         out["relerr"] = relerr(chi, chi_true)
         out["relerr_cco"] = relerr(out["chi_cco"], chi_true)

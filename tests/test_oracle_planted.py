@@ -187,3 +187,65 @@ def test_cie_and_normalisation_mistakes_break_their_pins(monkeypatch, mistake):
         check = pins.test_terms_at_zero_coefficients
     with pytest.raises(AssertionError):
         check()
+
+
+def _cco_fd_mismatch():
+    from oracle import cco
+    rng = np.random.default_rng(3)
+    chi = rng.uniform(0.0, 5.0, (9, 8)) * np.exp(1j * rng.uniform(-0.4, 1.2, (9, 8)))
+    c = rng.standard_normal(chi.shape) + 1j * rng.standard_normal(chi.shape)
+    d = rng.standard_normal(chi.shape) + 1j * rng.standard_normal(chi.shape)
+    h = 1e-6
+    f = lambda z: np.sum(np.real(np.conj(c) * cco.cco(z, eps=0.05)))
+    fd = (f(chi + h * d) - f(chi - h * d)) / (2 * h)
+    an = np.sum(np.real(np.conj(cco.cco_vjp(chi, c, eps=0.05)) * d))
+    return abs(fd - an) / abs(fd)
+
+
+def test_cco_adjoint_without_gain_derivative_breaks_differences(monkeypatch):
+    from oracle import cco
+    assert _cco_fd_mismatch() < 1e-8
+    good = cco.gain
+    # the forward keeps its gain, the adjoint loses d eta / d|chi|
+    monkeypatch.setattr(cco, "gain", lambda m, e, t, dl: (good(m, e, t, dl)[0], 0.0 * m))
+    assert _cco_fd_mismatch() > 1e-4
+
+
+def test_cco_adjoint_variance_factor_breaks_differences(monkeypatch):
+    from oracle import cco
+
+    def bad_vjp(I, c, r, eps):                 # the var = box(I^2) - mu^2 path without its factor 2
+        mu = cco.box_mean(I, r)
+        var = cco.box_mean(I * I, r) - mu * mu
+        a = var / (var + eps)
+        c_I = cco.box_mean(a, r) * c
+        c_a = cco.box_mean_adjoint(c * I, r)
+        c_b = cco.box_mean_adjoint(c, r)
+        c_mu = c_b * (1.0 - a)
+        c_a = c_a - c_b * mu
+        c_var = c_a * eps / (var + eps) ** 2
+        c_mu = c_mu - mu * c_var
+        return c_I + I * cco.box_mean_adjoint(c_var, r) + cco.box_mean_adjoint(c_mu, r)
+    assert _cco_fd_mismatch() < 1e-8
+    monkeypatch.setattr(cco, "guided_self_vjp", bad_vjp)
+    assert _cco_fd_mismatch() > 1e-4
+
+
+def test_box_adjoint_with_the_receivers_count_breaks_the_transpose(monkeypatch):
+    from oracle import cco
+    from tests.test_oracle_cco import box_matrix
+
+    def bad(c, r):                              # divides by the count of the window around k, not i
+        ny, nx = c.shape
+        out = np.zeros_like(c)
+        for i in range(ny):
+            for j in range(nx):
+                i0, i1 = max(0, i - r), min(ny, i + r + 1)
+                j0, j1 = max(0, j - r), min(nx, j + r + 1)
+                out[i, j] = c[i0:i1, j0:j1].sum() / ((i1 - i0) * (j1 - j0))
+        return out
+    B = box_matrix(6, 7, 2)
+    c = np.random.default_rng(0).standard_normal((6, 7))
+    assert np.abs(cco.box_mean_adjoint(c, 2).ravel() - B.T @ c.ravel()).max() < 1e-14
+    monkeypatch.setattr(cco, "box_mean_adjoint", bad)
+    assert np.abs(cco.box_mean_adjoint(c, 2).ravel() - B.T @ c.ravel()).max() > 1e-3

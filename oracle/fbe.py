@@ -16,6 +16,7 @@ retained set, and adjoint identities (tests/test_oracle_fbe.py).
 from __future__ import annotations
 
 import numpy as np
+from scipy import fft as sfft
 
 
 def mode_indices(K: int, M: int) -> np.ndarray:
@@ -31,12 +32,12 @@ def synth(alpha: np.ndarray, ny: int, nx: int) -> np.ndarray:
     iy, ix = mode_indices(ky, ny), mode_indices(kx, nx)
     full = np.zeros(alpha.shape[:-2] + (ny, nx), dtype=np.complex128)
     full[..., iy[:, None], ix[None, :]] = alpha
-    return np.fft.ifft2(full, norm="ortho")
+    return sfft.ifft2(full, norm="ortho")
 
 
 def analysis(J: np.ndarray, ky: int, kx: int) -> np.ndarray:
     """F_T(J) restricted to the retained modes = Phi^H J: [..., ny, nx] -> [..., ky, kx]."""
     ny, nx = J.shape[-2:]
     iy, ix = mode_indices(ky, ny), mode_indices(kx, nx)
-    full = np.fft.fft2(J, norm="ortho")
+    full = sfft.fft2(J, norm="ortho")
     return full[..., iy[:, None], ix[None, :]]

@@ -18,6 +18,7 @@ of the full-aperture data, dense == FFT application, adjoint identities.
 from __future__ import annotations
 
 import numpy as np
+from scipy import fft as sfft
 from scipy import special
 
 from .problem import Problem
@@ -65,8 +66,8 @@ def gd_circulant_kernel(p: Problem) -> np.ndarray:
 
 
 def gd_spectrum(p: Problem) -> np.ndarray:
-    """2-D DFT of the circulant kernel (numpy FFT as a library primitive)."""
-    return np.fft.fft2(gd_circulant_kernel(p))
+    """2-D DFT of the circulant kernel (scipy's FFT as a library primitive)."""
+    return sfft.fft2(gd_circulant_kernel(p))
 
 
 def gd_apply(p: Problem, J: np.ndarray, adjoint: bool = False, spec: np.ndarray = None) -> np.ndarray:
@@ -82,7 +83,7 @@ def gd_apply(p: Problem, J: np.ndarray, adjoint: bool = False, spec: np.ndarray 
     Py, Px = 2 * p.ny, 2 * p.nx
     pad = np.zeros(J.shape[:-2] + (Py, Px), dtype=np.complex128)
     pad[..., :p.ny, :p.nx] = J
-    out = np.fft.ifft2(spec * np.fft.fft2(pad))
+    out = sfft.ifft2(spec * sfft.fft2(pad))
     return out[..., :p.ny, :p.nx]
 
 

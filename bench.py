@@ -156,43 +156,47 @@ def kernel_bytes(w):
     }
 
 
-def cluster_flops(w):
+def cluster_flops(w, fold=1):
     """Algorithmic FP32 flops of one iteration of the fused loop (linear algebra only).
 
     Per incidence: synthesis T' = Wy^T alpha (ny ky kx complex MACs) and J = T' Wx (ny nx kx), the
     same two contractions again for the analysis (adjoint), G_D and G_D^H as zero-padded FFT
     convolutions (2 ny row + 2 Px column transforms of length P at 5 P log2 P flops, plus Px Py
-    complex products, each), and G_S J and G_S^H r_d (nr M complex MACs each).  A complex MAC is
-    8 flops, a complex product 6.  The pointwise CIE / regulariser work is not counted, so this
-    is a lower bound on the work done.
+    complex products, each), and the data term forward and adjoint: with the folded operator
+    (fold = 1, the only form the fused loop runs) (G_S Phi) alpha and its adjoint, nr ky kx complex
+    MACs each; unfolded (fold = 0) G_S J and G_S^H r_d, nr M each.  A complex MAC is 8 flops, a
+    complex product 6.  The pointwise CIE / regulariser work is not counted, so this is a lower
+    bound on the work done.
     """
     px, py = next_smooth(2 * w.nx), next_smooth(2 * w.ny)
     M = w.nx * w.ny
     syn = 8 * (w.ny * w.ky * w.kx + w.ny * w.nx * w.kx)
     fft = lambda n: 5 * n * np.log2(n)
     gd = (2 * w.ny * fft(px) + 2 * px * fft(py)) + 6 * px * py
-    gs = 8 * w.nr * M
+    gs = 8 * w.nr * (w.ky * w.kx if fold else M)
     return float(w.ni * (2 * syn + 2 * gd + 2 * gs))
 
 
-def hbm_model(w, loop_ms, peaks):
-    """Whole-iteration HBM fractions by the two byte models of the hot path: B_min = U + 2|G_S|
-    (E_inc once, G_S forward and adjoint) and B_model = 11 U + 2|G_S| (plus one HBM round trip of
-    the padded intermediate per 2-D transform and the J / r hand-off), U = Ni M 8 bytes, |G_S| =
-    Nr M 8 bytes; over the loop time per iteration against the measured copy peak."""
+def hbm_model(w, loop_ms, peaks, fold=1):
+    """Whole-iteration HBM fractions by the two byte models of the hot path: B_min = U + 2|G|
+    (E_inc once, the data operator forward and adjoint) and B_model = 11 U + 2|G| (plus one HBM
+    round trip of the padded intermediate per 2-D transform and the J / r hand-off), U = Ni M 8
+    bytes, |G| the data operator the path reads: the folded G_S Phi, Nr ky kx 8 bytes (fold = 1),
+    or G_S, Nr M 8 bytes (fold = 0); over the loop time per iteration against the measured copy
+    peak."""
     if not loop_ms or w.iters <= 0:
         return None
     M = w.nx * w.ny
-    U, GS = 8 * w.ni * M, 8 * w.nr * M
+    U, GS = 8 * w.ni * M, 8 * w.nr * (w.ky * w.kx if fold else M)
     bmin, bmodel = U + 2 * GS, 11 * U + 2 * GS
     t = loop_ms * 1e-3 / w.iters
     hbm = float(peaks.get("hbm_gbs", 6800.0)) * 1e9
     return {"B_min_MB": bmin / 1e6, "B_model_MB": bmodel / 1e6, "t_iter_us": t * 1e6,
             "frac_min": bmin / t / hbm, "frac_model": bmodel / t / hbm,
             "peak_gbs": hbm / 1e9, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-            "note": "the byte models count the unfolded G_S; the default folded data term reads the "
-                    "[nr][ky kx] operator instead, and at c1-c3 the working set is L2-resident, so "
-                    "these are fractions of the HBM roofline by algorithmic bytes, not DRAM traffic"}
+            "data_operator": "folded G_S Phi [nr][ky kx]" if fold else "G_S [nr][M]",
+            "note": "at c1-c3 the working set is L2-resident, so these are fractions of the HBM "
+                    "roofline by algorithmic bytes, not DRAM traffic"}
 
 
 def fp32_peak_tflops(peaks):
@@ -322,14 +326,15 @@ def run_ours(args, rank, world, local):
     achieved = kb[dom_name] / (dom_ms * 1e-3) / 1e9
     fma_tflops = pdf.pdf_fp32_fma_peak(10)             # measured FP32 FMA peak (burst)
     if rep.loop_mode == 3 and loop_ms is not None:
-        fl = cluster_flops(w) * w.iters
+        fl = cluster_flops(w, args.fold) * w.iters
         ach32 = fl / (loop_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "kernel": "k_cluster_solve", "achieved": ach32, "peak": fma_tflops,
                     "unit": "TFLOP/s", "frac": ach32 / fma_tflops, "traffic": None,
                     "flops_per_launch": fl, "launch_ms": loop_ms,
                     "peak_derived": fp32_peak_tflops(peaks),
                     "note": "one launch runs the whole Adam loop; algorithmic FP32 flops (FFT convolutions, "
-                            "Fourier synthesis/analysis, G_S, G_S^H) / the launch's CUDA-event time "
+                            "Fourier synthesis/analysis, the folded data operator G_S Phi and its "
+                            "adjoint) / the launch's CUDA-event time "
                             "(solve minus the same solve with 0 iterations); peak = FP32 FMA throughput "
                             "measured by pdf_fp32_fma_peak on this GPU (peak_derived: 152 SMs x 128 FP32 "
                             "lanes x 2 x max SM clock); the loop is latency- and barrier-bound at this size; "
@@ -371,7 +376,7 @@ def run_ours(args, rank, world, local):
             "iters_per_s": (w.iters * world / (loop_ms * 1e-3)) if loop_ms else None,
             "iters_per_s_note": "iterations / loop time (the solve minus the same solve with 0 "
                                 "iterations), all ranks",
-            "hbm_model": hbm_model(w, loop_ms, peaks),
+            "hbm_model": hbm_model(w, loop_ms, peaks, args.fold),
             "relerr": rep.relerr, "relerr_cco": rep.relerr_cco, "final_loss": rep.terms[0],
             "e2e": {"value": e2e_per_recon, "unit": "ms", "h2d_bytes_per_step": int(esca.nbytes),
                     "d2h_bytes_per_step": int(w.nx * w.ny * 8)},

@@ -68,10 +68,22 @@ typedef struct pdf_config {
                                 Fourier coefficients (Eq. 9 and 16 composed); 0 = G_S applied to
                                 the synthesised currents J every iteration (tensor cores at
                                 precision 1).  Same result up to rounding.                      */
+  /* Contrast-compensated operator (Sec. 2.4, Eq. 10-11): chi_CCO = (1 + eta) G(chi|chi) + eta chi,
+   * G the self-guided filter (box radius cco_radius, windows clipped to the grid, regulariser
+   * cco_eps, Re and Im filtered separately), eta = cco_eta_max sigmoid((|chi| - cco_tau)/cco_delta).
+   * cco_in_loss = 1: L_Bound, L_TV and L_Bridge (Eq. 17-19) act on chi_CCO of the current chi-hat
+   * instead of on chi-hat, and the gradient runs through the CCO's adjoint; pdf_solve's final CCO
+   * then uses these parameters too.  0 (default): the CCO only post-processes a solve's output, as
+   * Sec. 4.3 describes it, with the pdf_solve_opts parameters.  With cco_in_loss = 1 the solve's
+   * loop runs as the CUDA graph (use_graph 2 and 3 fall back to it).  Defaults 0, 2, 1e-2, 0.1, 3,
+   * 0.5; 0 <= cco_radius <= 16, cco_eps > 0, cco_delta > 0. */
+  int32_t cco_in_loss;
+  int32_t cco_radius;
+  double cco_eps, cco_eta_max, cco_tau, cco_delta;
 } pdf_config;
 
-/* Fills the paper's defaults (beta = 6, lambdas 1e-3/1e-5/1e-5, tau_B = 0.5, k0 = 2 pi) and
- * zero sizes/pointers.  Never fails. */
+/* Fills the paper's defaults (beta = 6, lambdas 1e-3/1e-5/1e-5, tau_B = 0.5, k0 = 2 pi, the CCO
+ * parameters of Eq. 11) and zero sizes/pointers.  Never fails. */
 void pdf_config_default(pdf_config* cfg);
 
 /* Assembles the operators of one geometry on the device: the Richmond G_D kernel spectrum
@@ -150,6 +162,11 @@ typedef struct pdf_solve_opts {
    * as the CUDA graph (use_graph 1..3) or one launch per kernel (0); alpha_out receives alpha-hat. */
   int32_t fcnn_hidden;       /* 0 = off (Adam on alpha) */
   const void* fcnn_params0;
+  /* Cap, in SM clock cycles, on each grid-barrier wait of the one-launch loop forms (use_graph 2
+   * and 3); 0 = the default 2^31 (about one second).  A wait that reaches the cap makes the solve
+   * return PDF_ETIMEOUT instead of waiting on.  A small positive value exists for testing that
+   * path: the first CTA to reach a barrier then gives up at once. */
+  int64_t barrier_wait_cycles;
 } pdf_solve_opts;
 
 typedef struct pdf_solve_report {
@@ -166,8 +183,17 @@ void pdf_solve_opts_default(pdf_solve_opts* o);
 
 /* Whole reconstruction on `stream`.  chi_out [ny][nx] (device, may be NULL) receives chi-hat
  * after the CCO when apply_cco, else chi-hat; chi_raw_out the chi-hat before CCO (may be NULL);
- * alpha_out [ni][ky][kx] the final coefficients (may be NULL).  When report != NULL the call
- * synchronises `stream` and fills it (PDF_ENONFINITE if a loss term is not finite). */
+ * alpha_out [ni][ky][kx] the final coefficients (may be NULL); report (host, may be NULL) is
+ * filled when given.  The call synchronises `stream` before it returns, to read the solve's
+ * device-side status:
+ *   PDF_ETIMEOUT      a grid barrier of the one-launch loop (use_graph 2 or 3) ran out of time
+ *                     (see barrier_wait_cycles); the outputs are not meaningful;
+ *   PDF_ENONFINITE    the reconstructed contrast, or with a report a final loss term, is NaN/Inf
+ *                     (for example from a non-finite alpha0); the outputs are written as computed.
+ * When the cluster loop (use_graph 3) is launched but its thread-block clusters do not come up
+ * with the shape it was launched with (a tool that serialises or replays launches can do this),
+ * the kernel returns without touching any state, and the same iterations run again as the CUDA
+ * graph of the stand-alone kernels; report->loop_mode then says 1. */
 pdf_status pdf_solve(pdf_problem* h, const pdf_solve_opts* opts, void* chi_out, void* chi_raw_out,
                      void* alpha_out, pdf_solve_report* report, void* stream);
 

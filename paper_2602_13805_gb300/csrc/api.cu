@@ -264,6 +264,12 @@ extern "C" void pdf_config_default(pdf_config* c) {
   c->eps_abs = 1e-12;
   c->q_min = 1e-6;
   c->fold_gs = 1;
+  c->cco_in_loss = 0;
+  c->cco_radius = 2;
+  c->cco_eps = 1e-2;
+  c->cco_eta_max = 0.1;
+  c->cco_tau = 3.0;
+  c->cco_delta = 0.5;
 }
 
 static void free_all(pdf_problem* h) {
@@ -324,6 +330,9 @@ static pdf_status validate(const pdf_config* c) {
   if (c->fold_gs != 0 && c->fold_gs != 1) return set_err(PDF_EINVAL, "fold_gs must be 0 or 1");
   if (c->tau_b <= 0 || c->eps_tv < 0 || c->eps_abs < 0 || c->q_min < 0)
     return set_err(PDF_EINVAL, "tau_b > 0 and non-negative eps/q_min required");
+  if (c->cco_in_loss != 0 && c->cco_in_loss != 1) return set_err(PDF_EINVAL, "cco_in_loss must be 0 or 1");
+  if (c->cco_in_loss && (c->cco_radius < 0 || c->cco_radius > 16 || !(c->cco_eps > 0) || !(c->cco_delta > 0)))
+    return set_err(PDF_EINVAL, "cco_radius must be in [0, 16], cco_eps > 0 and cco_delta > 0");
   int M = c->nx * c->ny;
 
   return PDF_OK;
@@ -398,6 +407,12 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
   d.eps_tv = (float)cfg->eps_tv;
   d.eps_abs = (float)cfg->eps_abs;
   d.q_min = (float)cfg->q_min;
+  d.cco_loss = cfg->cco_in_loss;
+  d.cco_r = cfg->cco_radius;
+  d.cco_eps = (float)cfg->cco_eps;
+  d.cco_eta_max = (float)cfg->cco_eta_max;
+  d.cco_tau = (float)cfg->cco_tau;
+  d.cco_delta = (float)cfg->cco_delta;
   // SIMT G_S product: about two CTAs per SM, 32..256 pixels each (multiple of 32)
   d.gs_chunk = std::min(256, std::max(32, ((d.M + 303) / 304 + 31) / 32 * 32));
   d.n_gs_chunks = (d.M + d.gs_chunk - 1) / d.gs_chunk;
@@ -476,9 +491,21 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
   TRY(dalloc(h, &h->alpha_alt, NA));
   TRY(dalloc(h, &h->used_warm, 1));
   TRY(dalloc(h, &h->bar, 1));
-  TRY(dalloc(h, &h->perr, 1));
-  cudaMemsetAsync(h->perr, 0, sizeof(int), s);
+  TRY(dalloc(h, &h->perr, 4));
+  cudaMemsetAsync(h->perr, 0, 4 * sizeof(int), s);
+  TRY(dalloc(h, &h->relerr_part, 3 * RELERR_BLOCKS));
   TRY(dalloc(h, &h->small2, NI * NR));
+  d.chic = nullptr;
+  d.cca = d.ccu = d.ccp = nullptr;
+  d.ccc = d.ccd = nullptr;
+  if (d.cco_loss) {
+    TRY(dalloc(h, &d.chic, M));
+    TRY(dalloc(h, &d.cca, M));
+    TRY(dalloc(h, &d.ccc, M));
+    TRY(dalloc(h, &d.ccd, M));
+    TRY(dalloc(h, &d.ccu, M));
+    TRY(dalloc(h, &d.ccp, M));
+  }
   {
     cudaError_t e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {

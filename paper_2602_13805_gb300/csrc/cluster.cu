@@ -33,6 +33,8 @@
 // runs to its end (cluster barriers need no timeout: a cluster is always co-scheduled) and the
 // host reports the flag.  Co-residency of all clusters comes from the cooperative launch.
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 
 #include <cooperative_groups.h>
 
@@ -55,6 +57,7 @@ struct ClusterArgs {
   int sl, sg;             // pixels per CTA slice (0: every CTA sums its own rows), lanes per pixel
   unsigned* bar;
   int* err;               // 1: a grid barrier timed out; 2: launched with the wrong cluster shape
+  long long wait_cap;     // clock cycles a grid-barrier wait may last
 };
 
 __device__ __forceinline__ unsigned cl_ld_acquire(const unsigned* p) {
@@ -70,10 +73,12 @@ __device__ __forceinline__ int cl_ld_relaxed(const int* p) {
 
 // Grid-wide barrier on a monotonic counter: thread 0 adds one with release semantics and polls
 // with acquire loads; bar.sync on both sides extends the ordering to the whole CTA.  Warps 1.. run
-// idle_work (work that needs nothing from other CTAs) meanwhile.  Bounded:
-// after ~2^31 cycles, or once any CTA has flagged a timeout, it stops waiting.
+// idle_work (work that needs nothing from other CTAs) meanwhile.  Bounded: after `cap` clock
+// cycles (checked on the first unsuccessful poll and every 32nd after it), or once any CTA has
+// flagged a timeout, it stops waiting.
 template <class F>
-__device__ __forceinline__ void cl_grid_barrier(unsigned* bar, unsigned target, int* err, F&& idle_work) {
+__device__ __forceinline__ void cl_grid_barrier(unsigned* bar, unsigned target, int* err, long long cap,
+                                                F&& idle_work) {
   __syncthreads();
   if (threadIdx.x >= 32) idle_work();                                  // warps 1.. while thread 0 waits
   if (threadIdx.x == 0) {
@@ -82,9 +87,9 @@ __device__ __forceinline__ void cl_grid_barrier(unsigned* bar, unsigned target, 
       const long long t0 = clock64();
       unsigned spins = 0;
       while (cl_ld_acquire(bar) < target) {
-        if ((++spins & 31u) == 0) {
+        if ((spins++ & 31u) == 0) {
           if (cl_ld_relaxed(err) != 0) break;
-          if (clock64() - t0 > (1ll << 31)) {
+          if (clock64() - t0 >= cap) {
             atomicExch(err, 1);
             break;
           }
@@ -450,7 +455,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
       __stcg(&nd[(size_t)p * M + y0 * nx + i], make_float4(n.x, n.y, cabs2(s), 0.f));
     }
     const unsigned nbar = a.sl > 0 ? 2u : 1u;                           // grid barriers per iteration
-    cl_grid_barrier(a.bar, ((unsigned)it * nbar + 1u) * nblocks, a.err, [&] {
+    cl_grid_barrier(a.bar, ((unsigned)it * nbar + 1u) * nblocks, a.err, a.wait_cap, [&] {
 #pragma unroll 1
       for (int i = threadIdx.x - 32; i < NA; i += CL_NT - 32) {            // (G_S Phi)^H r_d, own receivers (Eq. 16)
         float2 g = make_float2(0.f, 0.f);
@@ -495,7 +500,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
           __stcg(a.dsg + j, clamped ? -Df : Df);
         }
       }
-      cl_grid_barrier(a.bar, ((unsigned)it * 2u + 2u) * nblocks, a.err, [] {});
+      cl_grid_barrier(a.bar, ((unsigned)it * 2u + 2u) * nblocks, a.err, a.wait_cap, [] {});
       const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 1
       for (int i0 = threadIdx.x; i0 < HPk; i0 += 4 * CL_NT) {            // own rows + halo, four loads in flight
@@ -787,7 +792,7 @@ struct ClPlanRow {
 // such clusters the device can hold at once; a row is usable when all ni clusters fit.
 static int cl_plan(const pdf_problem* h, ClPlanRow* rows, int nmax) {
   const Dev& d = h->d;
-  if (!d.fast || h->tc || !d.fold || !d.what || d.Px != d.Py || d.Px > 128 || d.kx > 64) return 0;
+  if (!d.fast || h->tc || !d.fold || !d.what || d.cco_loss || d.Px != d.Py || d.Px > 128 || d.kx > 64) return 0;
   int dev = 0, sms = 0, coop = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -884,15 +889,21 @@ pdf_status cl_run(pdf_problem* h, const pdf_solve_opts* o, int iters, cudaStream
   a.dsg = (float*)(a.rc + d.M);
   a.bar = h->bar;
   a.err = h->perr;
+  a.wait_cap = o->barrier_wait_cycles > 0 ? (long long)o->barrier_wait_cycles : (1ll << 31);
+  // Test hook for the solve's recovery path: with PDF_TEST_CLUSTER_SHAPE=mismatch in the environment
+  // the kernel is told to expect a cluster size no launch has, so every CTA takes the entry check's
+  // early return (error flag 2) exactly as when a tool launches it without its cluster shape.
+  if (const char* t = getenv("PDF_TEST_CLUSTER_SHAPE"))
+    if (strcmp(t, "mismatch") == 0) a.C = 0;
   PDF_CUDA(cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st));
   cudaLaunchAttribute at[2];
   const size_t smem = (size_t)rows[pick].smem;
   cudaError_t e;
   if (d.Px == 64) {
-    cudaLaunchConfig_t cfg = cluster_config<64>(d.ni, a.C, smem, st, at);
+    cudaLaunchConfig_t cfg = cluster_config<64>(d.ni, rows[pick].C, smem, st, at);
     e = cudaLaunchKernelEx(&cfg, k_cluster_solve<64>, h->d, a);
   } else {
-    cudaLaunchConfig_t cfg = cluster_config<128>(d.ni, a.C, smem, st, at);
+    cudaLaunchConfig_t cfg = cluster_config<128>(d.ni, rows[pick].C, smem, st, at);
     e = cudaLaunchKernelEx(&cfg, k_cluster_solve<128>, h->d, a);
   }
   if (e != cudaSuccess) {

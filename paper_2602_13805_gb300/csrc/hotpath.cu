@@ -8,6 +8,7 @@
 //                      (Eq. 7); r = R s - beta J and ||r||^2 (Eq. 15)
 //   k_gs_partial/reduce  G_S J - E_sca and ||.||^2 (Eq. 16)
 //   k_reg              L_Bound, L_TV, L_Bridge (Eq. 17-19) and their cotangent on chi -> on R -> w
+//                      (with the CCO inside the loss: the six kernels of ccoloss.cu instead)
 //   k_adj_rowfft       u = 2/||Einc||^2 conj(R) r + c_s (goes through G_D^H), v = pointwise part
 //   k_colconv(conj)    G_D^H = convolution with the conjugated spectrum (G_D is symmetric)
 //   k_gsh              2/||Esca||^2 G_S^H r_d
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(256) k_gsh(Dev d, const float2* in, float2* ou
 // ---------------------------------------------------------------------------
 // regularisers (Eq. 17-19) and their cotangent pulled back to w = c_R / D
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_reg(Dev d) { ph_reg(d, blockIdx.x); }
+__global__ void __launch_bounds__(256) k_reg(Dev d) { ph_reg(d, blockIdx.x, d.chi, nullptr); }
 
 // ---------------------------------------------------------------------------
 // adjoint: u (through G_D^H) and v (pointwise), then padded row DFT of u
@@ -622,7 +623,12 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
                                                 d.lpart + LP_DATA * PDF_LP_STRIDE);
   }
   mark();
-  k_reg<<<d.n_reg_blocks, 128, 0, st>>>(d);
+  if (d.cco_loss) {
+    if ((s = cc_reg(d, st)) != PDF_OK) return s;
+    pdf_count_launch(CCO_LOSS_KERNELS - 1);
+  } else {
+    k_reg<<<d.n_reg_blocks, 128, 0, st>>>(d);
+  }
   mark();
   // adjoint
   if (d.fast) {

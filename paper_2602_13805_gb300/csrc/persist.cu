@@ -8,8 +8,8 @@
 // register-FFT problems with square padding (Px == Py) on the FP32 path.
 //
 // The barrier is a monotonic arrival counter in global memory (release by the arriving CTA,
-// acquire by the waiting one).  Every wait is bounded by ~2^31 clock cycles; on timeout the CTA
-// raises the error flag and returns, so a launch that cannot complete ends in bounded time and the
+// acquire by the waiting one).  Every wait is bounded (2^31 clock cycles unless the solve options
+// give a shorter cap); on timeout the CTA raises the error flag and returns, so a launch that cannot complete ends in bounded time and the
 // host reports PDF_ETIMEOUT.  Co-residency of all CTAs is guaranteed by the cooperative launch.
 #include "phases.cuh"
 
@@ -26,6 +26,7 @@ struct PersistArgs {
   double* terms;
   unsigned* bar;
   int* err;
+  long long wait_cap;          // clock cycles a grid-barrier wait may last
   int n_data_blocks;
 };
 
@@ -35,7 +36,15 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int* err) {
+__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Returns false (and the CTA leaves the loop) when the wait lasted `cap` clock cycles or another CTA
+// has already flagged a timeout.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int* err, long long cap) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -44,8 +53,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int
     atomicAdd(bar, 1u);
     if (ld_acquire_u32(bar) < target) {
       const long long t0 = clock64();
+      unsigned spins = 0;
       while (ld_acquire_u32(bar) < target) {
-        if (clock64() - t0 > (1ll << 31)) {
+        if ((spins++ & 31u) == 0 && (ld_relaxed_s32(err) != 0 || clock64() - t0 >= cap)) {
           atomicExch(err, 1);
           ok = 0;
           break;
@@ -73,7 +83,7 @@ __global__ void __launch_bounds__(FT) k_persist(Dev d, PersistArgs a) {
 #define PDF_BARRIER()                                                  \
   do {                                                                 \
     ++gen;                                                             \
-    if (!grid_barrier(a.bar, gen * (unsigned)G, a.err)) return;        \
+    if (!grid_barrier(a.bar, gen * (unsigned)G, a.err, a.wait_cap)) return;        \
   } while (0)
   for (int it = 0; it < a.iters; ++it) {
     // forward: synthesis + row DFT, column convolution, row IDFT + CIE update + state residual
@@ -100,7 +110,7 @@ __global__ void __launch_bounds__(FT) k_persist(Dev d, PersistArgs a) {
     PDF_BARRIER();
     for (int vb = b0; vb < n_dat + n_reg; vb += G) {
       if (vb < n_dat) ph_gs_reduce(d, vb, d.gspart, d.n_gs_chunks, d.esca, d.rd, d.lpart + LP_DATA * PDF_LP_STRIDE);
-      else ph_reg(d, vb - n_dat);
+      else ph_reg(d, vb - n_dat, d.chi, nullptr);
       __syncthreads();
     }
     PDF_BARRIER();
@@ -187,7 +197,7 @@ pdf_status ps_run(pdf_problem* h, const pdf_solve_opts* o, int iters, unsigned* 
                   bool* done) {
   *done = false;
   const Dev& d = h->d;
-  if (!d.fast || h->tc || d.fold || d.Px != d.Py || iters < 1) return PDF_OK;   // unfolded data term only
+  if (!d.fast || h->tc || d.fold || d.cco_loss || d.Px != d.Py || iters < 1) return PDF_OK;   // unfolded data term only
   PersistArgs a;
   a.iters = iters;
   a.alpha = h->alpha;
@@ -203,6 +213,7 @@ pdf_status ps_run(pdf_problem* h, const pdf_solve_opts* o, int iters, unsigned* 
   a.terms = h->terms;
   a.bar = bar;
   a.err = err;
+  a.wait_cap = o->barrier_wait_cycles > 0 ? (long long)o->barrier_wait_cycles : (1ll << 31);
   a.n_data_blocks = (d.ni * d.nr + 255) / 256;
   PDF_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned), st));
   const size_t smem = persist_smem(d);

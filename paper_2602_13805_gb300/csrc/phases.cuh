@@ -619,6 +619,16 @@ __device__ __forceinline__ void ph_gsh(const Dev& d, int bx, float2* sm, const f
 }
 
 
+// The regularisers' cotangent c_chi on chi-hat carried to w = conj(d chi / d R) c_chi / D:
+// chi = R / (beta (1 - R)) gives d chi / d R = 1 / (beta (1 - R)^2), zero where the clamp is active.
+__device__ __forceinline__ float2 reg_w(const Dev& d, int n, float2 cchi) {
+  if (d.clamp[n]) return make_float2(0.f, 0.f);
+  const float2 R = d.R[n];
+  const float2 q = make_float2(1.f - R.x, -R.y);
+  const float2 dchi = cdivf(make_float2(1.f, 0.f), cmul(d.beta, cmul(q, q)));
+  return (1.f / d.D[n]) * cmul(cconj(dchi), cchi);
+}
+
 struct TVB {  // per-pixel pieces of the TV and bridge terms at one pixel
   float2 dx, dy;
   float t;          // TV magnitude
@@ -631,32 +641,35 @@ __device__ __forceinline__ float mag_at(const float2* chi, int nx, int y, int x,
   return sqrtf(cabs2(c) + eps);
 }
 
-__device__ __forceinline__ TVB tvb_at(const Dev& d, int y, int x) {
+__device__ __forceinline__ TVB tvb_at(const Dev& d, const float2* chi, int y, int x) {
   TVB o;
-  const float2 c = d.chi[y * d.nx + x];
+  const float2 c = chi[y * d.nx + x];
   const bool hx = x + 1 < d.nx, hy = y + 1 < d.ny;
-  o.dx = hx ? d.chi[y * d.nx + x + 1] - c : make_float2(0.f, 0.f);
-  o.dy = hy ? d.chi[(y + 1) * d.nx + x] - c : make_float2(0.f, 0.f);
+  o.dx = hx ? chi[y * d.nx + x + 1] - c : make_float2(0.f, 0.f);
+  o.dy = hy ? chi[(y + 1) * d.nx + x] - c : make_float2(0.f, 0.f);
   o.t = sqrtf(cabs2(o.dx) + cabs2(o.dy) + d.eps_tv);
   const float m = sqrtf(cabs2(c) + d.eps_abs);
-  o.gx = hx ? mag_at(d.chi, d.nx, y, x + 1, d.eps_abs) - m : 0.f;
-  o.gy = hy ? mag_at(d.chi, d.nx, y + 1, x, d.eps_abs) - m : 0.f;
+  o.gx = hx ? mag_at(chi, d.nx, y, x + 1, d.eps_abs) - m : 0.f;
+  o.gy = hy ? mag_at(chi, d.nx, y + 1, x, d.eps_abs) - m : 0.f;
   o.sg = 1.f / (1.f + expf(-(m - d.tau_b) / d.tau_b));
   o.e = expf(-(o.gx * o.gx + o.gy * o.gy));
   return o;
 }
 
 
-__device__ __forceinline__ void ph_reg(const Dev& d, int bx) {
+// Regularisers of Eq. (17)-(19) on the image `img` (chi-hat, or chi_CCO when the CCO is inside the
+// loss) and their cotangent on it: written to `cot` when given, else carried on through
+// chi = R / (beta (1 - R)) and R = N / D to w.
+__device__ __forceinline__ void ph_reg(const Dev& d, int bx, const float2* img, float2* cot) {
   __shared__ FF red_rg[3 * 32];
   const int n = bx * blockDim.x + threadIdx.x;
   float lb = 0.f, ltv = 0.f, lbr = 0.f;
   if (n < d.M) {
     const int y = n / d.nx, x = n - y * d.nx;
-    const float2 c = d.chi[n];
+    const float2 c = img[n];
     const float neg = fmaxf(-c.x, 0.f);
     lb = neg * neg;
-    const TVB o = tvb_at(d, y, x);
+    const TVB o = tvb_at(d, img, y, x);
     ltv = o.t;
     lbr = o.sg * o.e;
     // TV cotangent: -(dx + dy)/t at the own term, + dx/t of the left term, + dy/t of the upper term
@@ -664,28 +677,23 @@ __device__ __forceinline__ void ph_reg(const Dev& d, int bx) {
     // bridge cotangent on |chi|: own sigmoid term, own differences (-1), left / upper differences (+1)
     float dm = o.sg * (1.f - o.sg) / d.tau_b * o.e + 2.f * (o.gx + o.gy) * o.sg * o.e;
     if (x > 0) {
-      const TVB l = tvb_at(d, y, x - 1);
+      const TVB l = tvb_at(d, img, y, x - 1);
       ctv = ctv + (1.f / l.t) * l.dx;
       dm += -2.f * l.gx * l.sg * l.e;
     }
     if (y > 0) {
-      const TVB u = tvb_at(d, y - 1, x);
+      const TVB u = tvb_at(d, img, y - 1, x);
       ctv = ctv + (1.f / u.t) * u.dy;
       dm += -2.f * u.gy * u.sg * u.e;
     }
     const float m = sqrtf(cabs2(c) + d.eps_abs);
     float2 cchi = d.lam_tv * ctv + (d.lam_bridge * dm / m) * c;
     cchi.x += d.lam_bound * (-2.f * neg);
-    // chi = R / (beta (1 - R)):  d chi / d R = 1 / (beta (1 - R)^2), zero where clamped
-    float2 w = make_float2(0.f, 0.f);
-    if (!d.clamp[n]) {
-      const float2 R = d.R[n];
-      const float2 q = make_float2(1.f - R.x, -R.y);
-      const float2 dchi = cdivf(make_float2(1.f, 0.f), cmul(d.beta, cmul(q, q)));
-      const float2 cR = cmul(cconj(dchi), cchi);
-      w = (1.f / d.D[n]) * cR;
+    if (cot) {
+      cot[n] = cchi;
+    } else {
+      d.w[n] = reg_w(d, n, cchi);
     }
-    d.w[n] = w;
   }
   FF t3[3] = {ff_make(lb), ff_make(ltv), ff_make(lbr)};
   ff_block_sum_multi<3>(t3, red_rg);

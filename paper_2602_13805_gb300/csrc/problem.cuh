@@ -64,6 +64,17 @@ struct Dev {
   const float* invn;     // [2] 2 / ||E_inc||^2, 2 / ||E_sca||^2 (float)
   const float2* adam_tab;  // [cap] Adam step size lr / (1 - b1^t) and sqrt(1 - b2^t), t = 1..cap
   int gs_chunk;          // pixels per CTA of the SIMT G_S product
+
+  // CCO inside the loss (pdf_config.cco_in_loss): the regularisers act on chi_CCO (ccoloss.cu)
+  int cco_loss;
+  int cco_r;             // guided-filter box radius
+  float cco_eps, cco_eta_max, cco_tau, cco_delta;
+  float2* chic;          // [M] chi_CCO
+  float4* cca;           // [M] per window: 1 - a and the mean, Re then Im (guided-filter coefficients)
+  float2* ccc;           // [M] regulariser cotangent on chi_CCO
+  float2* ccd;           // [M] the part of the cotangent on chi-hat that needs no window sum
+  float4* ccu;           // [M] per pixel: cotangents headed for the window coefficients / count
+  float4* ccp;           // [M] per window: cotangents headed for the pixels / count
 };
 
 struct TC;
@@ -116,7 +127,9 @@ struct pdf_problem {
   int* used_warm;        // device flag
   unsigned* bar;         // grid-barrier counter of the persistent and cluster loops
   float4* cl_nd;         // cluster loop: per-incidence pixel sums (lazily allocated)
-  int* perr;             // its timeout flag
+  int* perr;             // [4]: loop error flag (1 barrier timeout, 2 wrong cluster shape), non-finite
+                         // output flag, the RelErr reduction's block counter, unused
+  double* relerr_part;   // [3 * RELERR_BLOCKS] per-block partial sums of the final RelErr
   float2* small1;        // [ni][nr] scratch
   float2* small2;
   cudaStream_t cap_stream;   // private stream used only for graph capture
@@ -130,6 +143,9 @@ struct pdf_problem {
   double adam_key[3];    // lr, b1, b2 of the table
   float* invn;
 };
+
+// blocks of the final RelErr reduction (solve.cu)
+#define RELERR_BLOCKS 148
 
 // coefficient-correcting network (fcnn.cu)
 pdf_status fc_prepare(pdf_problem* h, int hidden, const void* params0, cudaStream_t st);
@@ -156,6 +172,11 @@ pdf_status ws_alloc(pdf_problem* h, void** p, size_t bytes);
 // reductions defined in api.cu
 __global__ void k_sumsq(const float2* x, int n, double* out);
 __global__ void k_set_invn(const double* norms, float* invn);
+
+// CCO inside the loss (ccoloss.cu): chi_CCO from d.chi, the regularisers on it, and their
+// cotangent carried back through the CCO to chi-hat and on to w (replaces k_reg)
+pdf_status cc_reg(const Dev& d, cudaStream_t st);
+constexpr int CCO_LOSS_KERNELS = 6;
 
 // launchers (hotpath.cu)
 pdf_status hp_configure_kernels();

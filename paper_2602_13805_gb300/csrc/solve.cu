@@ -107,23 +107,6 @@ __global__ void k_cco_out(const float2* __restrict__ chi, const float4* __restri
   out[n] = (1.f + eta) * gq + (sign * eta) * c;
 }
 
-// ||a - b||^2 and ||b||^2 in double (single block) -> out[0], out[1]
-__global__ void k_relerr(const float2* __restrict__ a, const float2* __restrict__ b, int n, double* out) {
-  __shared__ double red[32];
-  double e = 0.0, t = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double2 bd = to_d(b[i]);
-    e += cabs2(to_d(a[i]) - bd);
-    t += cabs2(bd);
-  }
-  const double se = block_sum(e, red);
-  const double st = block_sum(t, red);
-  if (threadIdx.x == 0) {
-    out[0] = se;
-    out[1] = st;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // per-incidence reductions and small pointwise kernels of the initialisation
 // ---------------------------------------------------------------------------
@@ -400,6 +383,167 @@ static pdf_status build_graph(pdf_problem* h, const pdf_solve_opts* o) {
   return PDF_OK;
 }
 
+// The CCO of a solve's output: with the CCO inside the loss, the parameters the loss used.
+static pdf_status final_cco(pdf_problem* h, const pdf_solve_opts* o, const float2* chi, float2* out,
+                            cudaStream_t st) {
+  const pdf_config& c = h->cfg;
+  if (c.cco_in_loss) return sv_cco(h, chi, out, c.cco_radius, c.cco_eps, c.cco_eta_max, c.cco_tau, c.cco_delta, st);
+  return sv_cco(h, chi, out, o->cco_radius, o->cco_eps, o->cco_eta_max, o->cco_tau, o->cco_delta, st);
+}
+
+// Resets the Adam state of alpha (or of the network's weights) to step 0.
+static pdf_status reset_adam(pdf_problem* h, cudaStream_t st) {
+  const int NA = h->d.ni * h->d.ky * h->d.kx;
+  PDF_CUDA(cudaMemsetAsync(h->adam_m, 0, sizeof(float) * 2 * NA, st));
+  PDF_CUDA(cudaMemsetAsync(h->adam_v, 0, sizeof(float) * 2 * NA, st));
+  PDF_CUDA(cudaMemsetAsync(h->adam_t, 0, sizeof(int), st));
+  return PDF_OK;
+}
+
+// Runs the Adam iterations of a solve from the current alpha.  fused = 0 forbids the one-launch
+// loop forms (the fallback after a cluster launch that came up without its shape).
+static pdf_status run_loop(pdf_problem* h, const pdf_solve_opts* o, int fused, int* loop_mode, cudaStream_t st) {
+  const Dev& d = h->d;
+  pdf_status s;
+  int it = 0;
+  *loop_mode = 0;
+  if (o->history_every > 0) {
+    for (; it < o->iters; ++it) {
+      if ((s = iteration(h, o, st)) != PDF_OK) return s;
+      if (it % o->history_every == 0) {
+        double* row = o->history + 8 * (it / o->history_every);
+        PDF_CUDA(cudaMemcpyAsync(row, h->terms, 6 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        if (o->chi_true) {
+          // chi-hat of this iteration's alpha (before its Adam step) and its CCO image
+          k_relerr_to<<<1, 1024, 0, st>>>(d.chi, (const float2*)o->chi_true, d.M, row + 6);
+          pdf_count_launch(1);
+          if (o->apply_cco) {
+            if ((s = final_cco(h, o, d.chi, h->field3, st)) != PDF_OK) return s;
+            k_relerr_to<<<1, 1024, 0, st>>>(h->field3, (const float2*)o->chi_true, d.M, row + 7);
+            pdf_count_launch(1);
+          }
+          PDF_LAUNCHED("history relerr");
+        }
+      }
+    }
+    return PDF_OK;
+  }
+  bool persisted = false;
+  if (fused && o->use_graph == 3 && !h->fc_active) {
+    if ((s = cl_run(h, o, o->iters, st, &persisted)) != PDF_OK) return s;
+    if (persisted) {
+      it = o->iters;
+      *loop_mode = 3;
+    }
+  }
+  if (fused && !persisted && o->use_graph == 2 && !h->fc_active) {
+    if ((s = ps_run(h, o, o->iters, h->bar, h->perr, st, &persisted)) != PDF_OK) return s;
+    if (persisted) {
+      it = o->iters;
+      *loop_mode = 2;
+    }
+  }
+  if (!persisted && o->use_graph && o->iters >= GRAPH_UNROLL) {
+    if ((s = build_graph(h, o)) != PDF_OK) return s;
+    *loop_mode = 1;
+    for (; it + h->graph_iters <= o->iters; it += h->graph_iters) {
+      PDF_CUDA(cudaGraphLaunch(h->graph_exec, st));
+      pdf_count_launch(h->graph_kernels);
+    }
+  }
+  for (; it < o->iters; ++it)
+    if ((s = iteration(h, o, st)) != PDF_OK) return s;
+  return PDF_OK;
+}
+
+// flag[0] |= any element of x not finite
+__global__ void k_nonfinite(const float2* __restrict__ x, int n, int* __restrict__ flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const float2 v = x[i];
+    if (!isfinite(v.x) || !isfinite(v.y)) *flag = 1;
+  }
+}
+
+// ||a1 - b||^2, ||b||^2, ||a2 - b||^2 (a2 may be NULL) over n elements -> out[0], out[1], out[2],
+// out[3] = out[1]: FP32 Kahan sums per thread, FP64 sums per block into part[block][3], and the last
+// block to finish sums the partials in block order (deterministic).
+__global__ void __launch_bounds__(256) k_relerr2(const float2* __restrict__ a1, const float2* __restrict__ a2,
+                                                 const float2* __restrict__ b, int n, double* __restrict__ part,
+                                                 unsigned* __restrict__ count, double* __restrict__ out) {
+  __shared__ double red[32];
+  __shared__ bool last;
+  float s[3] = {0.f, 0.f, 0.f}, c[3] = {0.f, 0.f, 0.f};
+  auto kahan = [&](int k, float v) {
+    const float y = v - c[k], t = s[k] + y;
+    c[k] = (t - s[k]) - y;
+    s[k] = t;
+  };
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float2 bv = b[i];
+    kahan(0, cabs2(a1[i] - bv));
+    kahan(1, cabs2(bv));
+    if (a2) kahan(2, cabs2(a2[i] - bv));
+  }
+  for (int k = 0; k < 3; ++k) {
+    const double t = block_sum((double)s[k] - (double)c[k], red);
+    if (threadIdx.x == 0) part[3 * blockIdx.x + k] = t;
+  }
+  __threadfence();
+  if (threadIdx.x == 0) last = atomicAdd(count, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double t[3] = {0.0, 0.0, 0.0};
+  for (int j = threadIdx.x; j < (int)gridDim.x; j += blockDim.x)
+    for (int k = 0; k < 3; ++k) t[k] += __ldcg(&part[3 * j + k]);
+  for (int k = 0; k < 3; ++k) t[k] = block_sum(t[k], red);
+  if (threadIdx.x == 0) {
+    out[0] = t[0];
+    out[1] = t[1];
+    out[2] = t[2];
+    out[3] = t[1];
+    *count = 0u;
+  }
+}
+
+// Final chi-hat, CCO, outputs and (with a truth) the two RelErr sums; then the status check.
+static pdf_status finish(pdf_problem* h, const pdf_solve_opts* o, float2* chi_out, float2* chi_raw_out,
+                         float2* alpha_out, bool terms, cudaStream_t st) {
+  Dev& d = h->d;
+  const int NA = d.ni * d.ky * d.kx;
+  pdf_status s;
+  if (h->fc_active) {                                                  // alpha-hat at the final weights
+    if ((s = fc_forward(h, st)) != PDF_OK) return s;
+  }
+  // final chi-hat (and loss terms when a report is requested)
+  if (terms) {
+    if ((s = hp_loss_grad(h, h->alpha, h->grad, h->terms, st)) != PDF_OK) return s;
+  } else {
+    if ((s = hp_chi(h, h->alpha, nullptr, st)) != PDF_OK) return s;
+  }
+  if (chi_raw_out) PDF_CUDA(cudaMemcpyAsync(chi_raw_out, d.chi, sizeof(float2) * d.M, cudaMemcpyDeviceToDevice, st));
+  PDF_CUDA(cudaMemcpyAsync(h->field2, d.chi, sizeof(float2) * d.M, cudaMemcpyDeviceToDevice, st));
+  if (o->apply_cco) {
+    if ((s = final_cco(h, o, h->field2, h->field3, st)) != PDF_OK) return s;
+  } else {
+    PDF_CUDA(cudaMemcpyAsync(h->field3, h->field2, sizeof(float2) * d.M, cudaMemcpyDeviceToDevice, st));
+  }
+  if (chi_out) PDF_CUDA(cudaMemcpyAsync(chi_out, h->field3, sizeof(float2) * d.M, cudaMemcpyDeviceToDevice, st));
+  if (alpha_out) PDF_CUDA(cudaMemcpyAsync(alpha_out, h->alpha, sizeof(float2) * NA, cudaMemcpyDeviceToDevice, st));
+  const int nb = (d.M + 255) / 256;
+  k_nonfinite<<<nb, 256, 0, st>>>(h->field3, d.M, h->perr + 1);
+  pdf_count_launch(1);
+  if (o->chi_true) {
+    const int g = std::min(nb, RELERR_BLOCKS);
+    k_relerr2<<<g, 256, 0, st>>>(h->field2, h->field3, (const float2*)o->chi_true, d.M, h->relerr_part,
+                                 (unsigned*)(h->perr + 2), h->scratch_d + 40);
+    pdf_count_launch(1);
+  }
+  PDF_LAUNCHED("final contrast");
+  return PDF_OK;
+}
+
 pdf_status sv_solve(pdf_problem* h, const pdf_solve_opts* o, float2* chi_out, float2* chi_raw_out,
                     float2* alpha_out, pdf_solve_report* rep, cudaStream_t st) {
   Dev& d = h->d;
@@ -407,6 +551,7 @@ pdf_status sv_solve(pdf_problem* h, const pdf_solve_opts* o, float2* chi_out, fl
   pdf_status s;
   if ((s = ensure_adam_table(h, o)) != PDF_OK) return s;
   PDF_CUDA(cudaMemsetAsync(h->used_warm, 0, sizeof(int), st));
+  PDF_CUDA(cudaMemsetAsync(h->perr, 0, 2 * sizeof(int), st));      // loop error, non-finite output
   if (o->init == 0) {
     if ((s = init_bp_csi(h, st)) != PDF_OK) return s;
   } else if (o->init == 3) {
@@ -424,9 +569,7 @@ pdf_status sv_solve(pdf_problem* h, const pdf_solve_opts* o, float2* chi_out, fl
   } else {
     PDF_CUDA(cudaMemsetAsync(h->alpha, 0, sizeof(float2) * NA, st));
   }
-  PDF_CUDA(cudaMemsetAsync(h->adam_m, 0, sizeof(float) * 2 * NA, st));
-  PDF_CUDA(cudaMemsetAsync(h->adam_v, 0, sizeof(float) * 2 * NA, st));
-  PDF_CUDA(cudaMemsetAsync(h->adam_t, 0, sizeof(int), st));
+  if ((s = reset_adam(h, st)) != PDF_OK) return s;
   h->fc_active = 0;
   if (o->fcnn_hidden > 0) {                                           // the network's input is this alpha
     if (h->fc.H != o->fcnn_hidden && h->graph_exec) {                  // the graph holds the old buffers
@@ -436,105 +579,48 @@ pdf_status sv_solve(pdf_problem* h, const pdf_solve_opts* o, float2* chi_out, fl
     if ((s = fc_prepare(h, o->fcnn_hidden, o->fcnn_params0, st)) != PDF_OK) return s;
     h->fc_active = 1;
   }
-  int it = 0;
   int loop_mode = 0;                  // which loop form ran (reported)
-  if (o->history_every > 0) {
-    for (; it < o->iters; ++it) {
-      if ((s = iteration(h, o, st)) != PDF_OK) return s;
-      if (it % o->history_every == 0) {
-        double* row = o->history + 8 * (it / o->history_every);
-        PDF_CUDA(cudaMemcpyAsync(row, h->terms, 6 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        if (o->chi_true) {
-          // chi-hat of this iteration's alpha (before its Adam step) and its CCO image
-          k_relerr_to<<<1, 1024, 0, st>>>(d.chi, (const float2*)o->chi_true, d.M, row + 6);
-          pdf_count_launch(1);
-          if (o->apply_cco) {
-            if ((s = sv_cco(h, d.chi, h->field3, o->cco_radius, o->cco_eps, o->cco_eta_max, o->cco_tau,
-                            o->cco_delta, st)) != PDF_OK)
-              return s;
-            k_relerr_to<<<1, 1024, 0, st>>>(h->field3, (const float2*)o->chi_true, d.M, row + 7);
-            pdf_count_launch(1);
-          }
-          PDF_LAUNCHED("history relerr");
-        }
-      }
-    }
-  } else {
-    bool persisted = false;
-    if (o->use_graph == 3 && !h->fc_active) {
-      if ((s = cl_run(h, o, o->iters, st, &persisted)) != PDF_OK) return s;
-      if (persisted) {
-        it = o->iters;
-        loop_mode = 3;
-      }
-    }
-    if (!persisted && o->use_graph == 2 && !h->fc_active) {
-      if ((s = ps_run(h, o, o->iters, h->bar, h->perr, st, &persisted)) != PDF_OK) return s;
-      if (persisted) {
-        it = o->iters;
-        loop_mode = 2;
-      }
-    }
-    if (!persisted && o->use_graph && o->iters >= GRAPH_UNROLL) {
-      if ((s = build_graph(h, o)) != PDF_OK) return s;
-      loop_mode = 1;
-      for (; it + h->graph_iters <= o->iters; it += h->graph_iters) {
-        PDF_CUDA(cudaGraphLaunch(h->graph_exec, st));
-        pdf_count_launch(h->graph_kernels);
-      }
-    }
-    for (; it < o->iters; ++it)
-      if ((s = iteration(h, o, st)) != PDF_OK) return s;
+  if ((s = run_loop(h, o, 1, &loop_mode, st)) != PDF_OK) return s;
+  if ((s = finish(h, o, chi_out, chi_raw_out, alpha_out, rep != nullptr, st)) != PDF_OK) return s;
+  // device-side status: the one-launch loops' error flag and the finiteness of the output
+  int flag[2] = {0, 0};
+  PDF_CUDA(cudaMemcpyAsync(flag, h->perr, sizeof(flag), cudaMemcpyDeviceToHost, st));
+  PDF_CUDA(cudaStreamSynchronize(st));
+  if (flag[0] == 2 && loop_mode == 3) {
+    // the cluster kernel returned on entry without touching alpha or the Adam state: run the same
+    // iterations as the CUDA graph of the stand-alone kernels and finish again
+    PDF_CUDA(cudaMemsetAsync(h->perr, 0, 2 * sizeof(int), st));
+    if ((s = reset_adam(h, st)) != PDF_OK) return s;
+    if ((s = run_loop(h, o, 0, &loop_mode, st)) != PDF_OK) return s;
+    if ((s = finish(h, o, chi_out, chi_raw_out, alpha_out, rep != nullptr, st)) != PDF_OK) return s;
+    PDF_CUDA(cudaMemcpyAsync(flag, h->perr, sizeof(flag), cudaMemcpyDeviceToHost, st));
+    PDF_CUDA(cudaStreamSynchronize(st));
   }
-  if (h->fc_active) {                                                  // alpha-hat at the final weights
-    if ((s = fc_forward(h, st)) != PDF_OK) return s;
-  }
-  // final chi-hat (and loss terms when a report is requested)
-  if (rep) {
-    if ((s = hp_loss_grad(h, h->alpha, h->grad, h->terms, st)) != PDF_OK) return s;
-  } else {
-    if ((s = hp_chi(h, h->alpha, nullptr, st)) != PDF_OK) return s;
-  }
-  if (chi_raw_out) PDF_CUDA(cudaMemcpyAsync(chi_raw_out, d.chi, sizeof(float2) * d.M, cudaMemcpyDeviceToDevice, st));
-  PDF_CUDA(cudaMemcpyAsync(h->field2, d.chi, sizeof(float2) * d.M, cudaMemcpyDeviceToDevice, st));
-  if (o->apply_cco) {
-    if ((s = sv_cco(h, h->field2, h->field3, o->cco_radius, o->cco_eps, o->cco_eta_max, o->cco_tau, o->cco_delta,
-                    st)) != PDF_OK)
-      return s;
-  } else {
-    PDF_CUDA(cudaMemcpyAsync(h->field3, h->field2, sizeof(float2) * d.M, cudaMemcpyDeviceToDevice, st));
-  }
-  if (chi_out) PDF_CUDA(cudaMemcpyAsync(chi_out, h->field3, sizeof(float2) * d.M, cudaMemcpyDeviceToDevice, st));
-  if (alpha_out) PDF_CUDA(cudaMemcpyAsync(alpha_out, h->alpha, sizeof(float2) * NA, cudaMemcpyDeviceToDevice, st));
-  if (o->chi_true) {
-    k_relerr<<<1, 1024, 0, st>>>(h->field2, (const float2*)o->chi_true, d.M, h->scratch_d + 40);
-    k_relerr<<<1, 1024, 0, st>>>(h->field3, (const float2*)o->chi_true, d.M, h->scratch_d + 42);
-    pdf_count_launch(2);
-    PDF_LAUNCHED("relerr");
+  if (flag[0] != 0) {
+    PDF_CUDA(cudaMemset(h->perr, 0, 2 * sizeof(int)));
+    if (flag[0] == 1)
+      return set_err(PDF_ETIMEOUT, loop_mode == 3 ? "a grid barrier of the cluster solve loop timed out"
+                                                  : "a grid barrier of the persistent solve loop timed out");
+    return set_err(PDF_EUNSUPPORTED, "the one-launch solve loop was not launched in the form it needs");
   }
   if (rep) {
     memset(rep, 0, sizeof(*rep));
     rep->iters_run = o->iters;
     rep->loop_mode = loop_mode;
-    PDF_CUDA(cudaMemcpyAsync(rep->terms, h->terms, 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
     double re[4] = {NAN, NAN, NAN, NAN};
-    if (o->chi_true) PDF_CUDA(cudaMemcpyAsync(re, h->scratch_d + 40, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    PDF_CUDA(cudaStreamSynchronize(st));
+    int used = 0;
+    PDF_CUDA(cudaMemcpy(rep->terms, h->terms, 6 * sizeof(double), cudaMemcpyDeviceToHost));
+    if (o->chi_true) PDF_CUDA(cudaMemcpy(re, h->scratch_d + 40, 4 * sizeof(double), cudaMemcpyDeviceToHost));
+    PDF_CUDA(cudaMemcpy(&used, h->used_warm, sizeof(int), cudaMemcpyDeviceToHost));
     rep->relerr = o->chi_true ? sqrt(re[0] / re[1]) : NAN;
     rep->relerr_cco = o->chi_true ? sqrt(re[2] / re[3]) : NAN;
-    int used = 0, perr = 0;
-    PDF_CUDA(cudaMemcpy(&used, h->used_warm, sizeof(int), cudaMemcpyDeviceToHost));
-    PDF_CUDA(cudaMemcpy(&perr, h->perr, sizeof(int), cudaMemcpyDeviceToHost));
     rep->used_warm_start = used;
-    if (perr) {
-      cudaMemset(h->perr, 0, sizeof(int));
-      return set_err(PDF_ETIMEOUT, perr == 2 ? "the cluster solve loop was launched without its cluster shape"
-                                             : "a grid barrier of the persistent solve loop timed out");
-    }
     for (int k = 0; k < 6; ++k)
       if (!std::isfinite(rep->terms[k])) rep->nonfinite = 1;
-    if (rep->nonfinite) return set_err(PDF_ENONFINITE, "a loss term is not finite");
+    if (flag[1]) rep->nonfinite = 1;
   }
+  if (flag[1]) return set_err(PDF_ENONFINITE, "the reconstructed contrast is not finite");
+  if (rep && rep->nonfinite) return set_err(PDF_ENONFINITE, "a loss term is not finite");
   return PDF_OK;
 }
 

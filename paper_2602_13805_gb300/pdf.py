@@ -48,6 +48,9 @@ class pdf_config(ctypes.Structure):
         ("q_min", ctypes.c_double),
         ("precision", ctypes.c_int32), ("fft_path", ctypes.c_int32),
         ("fold_gs", ctypes.c_int32),
+        ("cco_in_loss", ctypes.c_int32), ("cco_radius", ctypes.c_int32),
+        ("cco_eps", ctypes.c_double), ("cco_eta_max", ctypes.c_double), ("cco_tau", ctypes.c_double),
+        ("cco_delta", ctypes.c_double),
     ]
 
 
@@ -63,6 +66,7 @@ class pdf_solve_opts(ctypes.Structure):
         ("use_graph", ctypes.c_int32), ("history_every", ctypes.c_int32),
         ("history", ctypes.c_void_p),
         ("fcnn_hidden", ctypes.c_int32), ("fcnn_params0", ctypes.c_void_p),
+        ("barrier_wait_cycles", ctypes.c_int64),
     ]
 
 
@@ -181,7 +185,8 @@ def _stream(stream) -> Optional[int]:
 
 def make_config(nx, ny, side_x, side_y, k0, tx, rx, kx, ky, beta=6.0 + 0j, inc_kind=0, precision=0,
                 lambda_bound=1e-3, lambda_tv=1e-5, lambda_bridge=1e-5, tau_b=0.5, eps_tv=1e-8, eps_abs=1e-12,
-                q_min=1e-6, fft_path=0, fold_gs=1):
+                q_min=1e-6, fft_path=0, fold_gs=1, cco_in_loss=0, cco_radius=2, cco_eps=1e-2, cco_eta_max=0.1,
+                cco_tau=3.0, cco_delta=0.5):
     """Returns (pdf_config, keep-alive antenna arrays)."""
     lib = load()
     c = pdf_config()
@@ -200,6 +205,8 @@ def make_config(nx, ny, side_x, side_y, k0, tx, rx, kx, ky, beta=6.0 + 0j, inc_k
     c.precision = precision
     c.fft_path = fft_path
     c.fold_gs = fold_gs
+    c.cco_in_loss, c.cco_radius = int(cco_in_loss), cco_radius
+    c.cco_eps, c.cco_eta_max, c.cco_tau, c.cco_delta = cco_eps, cco_eta_max, cco_tau, cco_delta
     return c, (tx, rx)
 
 
@@ -254,10 +261,31 @@ def pdf_forward(h: int, chi, esca_out, j_out=None, tol=1e-6, max_iter=2000, stre
 
 
 def pdf_gs_apply_static(gs, x, out, stream=None):
-    """out[p][r] = sum_n gs[r][n] x[p][n] with no device allocation (static library scratch)."""
-    nr, m = gs.shape[0], gs.shape[-1] if gs.dim() == 2 else gs.shape[1] * gs.shape[2]
+    """out[p][r] = sum_n gs[r][n] x[p][n] with no device allocation (static library scratch).
+
+    gs [nr][m...], x [ni][m...] and out [ni][nr] must be contiguous CUDA complex64 tensors without
+    a pending lazy conjugation (the library reads their raw device memory); anything else raises
+    ValueError before the library is called."""
+    import torch
+    for name, t in (("gs", gs), ("x", x), ("out", out)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor on the GPU, not {type(t).__name__}")
+        if t.dim() < 2 or t.dtype != torch.complex64:
+            raise ValueError(f"{name} must be a complex64 tensor of at least two dimensions")
+    nr = gs.shape[0]
+    m = gs.numel() // max(nr, 1)
     ni = x.shape[0]
-    _check(load().pdf_gs_apply_static(_ptr(gs), _ptr(x), _ptr(out), ni, nr, m, _stream(stream)))
+    if nr < 1 or m < 1 or ni < 1 or gs.numel() != nr * m or x.numel() != ni * m or out.numel() != ni * nr:
+        raise ValueError(f"sizes do not match: gs {tuple(gs.shape)} ([nr][m]), x {tuple(x.shape)} ([ni][m]), "
+                         f"out {tuple(out.shape)} ([ni][nr])")
+    for name, t in (("gs", gs), ("x", x), ("out", out)):
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be on the GPU")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.is_conj():
+            raise ValueError(f"{name} carries a lazy conjugation: pass torch.conj_physical(...)")
+    _check(load().pdf_gs_apply_static(gs.data_ptr(), x.data_ptr(), out.data_ptr(), ni, nr, m, _stream(stream)))
 
 
 def pdf_destroy(h: int):

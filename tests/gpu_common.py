@@ -11,9 +11,29 @@ TOL_FP32 = 1e-5
 
 
 def rel(a, b):
+    """Norm-wise relative error ||a - b|| / ||b||."""
     a = np.asarray(a)
     b = np.asarray(b)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def maxrel(a, b):
+    """Element-wise error max |a - b| / max |b|: a wrong small block (a few modes, the edge pixels)
+    that a norm-wise ratio can hide under a large correct one shows up here."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1e-300))
+
+
+def assert_close(name, gpu, ref, tol, tol_elem=None):
+    """Both the norm-wise and the element-wise error of `gpu` against the oracle's `ref` within
+    tol (tol_elem for the element-wise one when given)."""
+    gpu = gpu.cpu().numpy() if hasattr(gpu, "cpu") else np.asarray(gpu)
+    e, m = rel(gpu, ref), maxrel(gpu, ref)
+    te = tol if tol_elem is None else tol_elem
+    print(f"{name}: norm-wise {e:.2e}, element-wise {m:.2e}")
+    assert e < tol, f"{name}: norm-wise rel err {e:.2e} >= {tol:g}"
+    assert m < te, f"{name}: element-wise err {m:.2e} >= {te:g} (norm-wise {e:.2e})"
 
 
 class Case:

@@ -92,3 +92,22 @@ def test_fma_peak_rejects_bad_arguments_without_gpu(lib):
     out = ctypes.c_double(0.0)
     assert lib.pdf_fp32_fma_peak(0, ctypes.byref(out), None) == -1
     assert lib.pdf_fp32_fma_peak(3, None, None) == -1
+
+
+def test_static_gs_wrapper_rejects_host_and_missized_arguments():
+    # checked before the library is called: a host pointer or a short array would reach the device
+    torch = pytest.importorskip("torch")
+    from paper_2602_13805_gb300 import pdf
+    gs = torch.zeros((4, 6), dtype=torch.complex64)
+    x = torch.zeros((3, 6), dtype=torch.complex64)
+    out = torch.zeros((3, 4), dtype=torch.complex64)
+    with pytest.raises(ValueError, match="torch tensor"):
+        pdf.pdf_gs_apply_static(gs.numpy(), x, out)
+    with pytest.raises(ValueError, match="complex64"):
+        pdf.pdf_gs_apply_static(gs.to(torch.complex128), x, out)
+    with pytest.raises(ValueError, match="sizes"):
+        pdf.pdf_gs_apply_static(gs, torch.zeros((3, 5), dtype=torch.complex64), out)
+    with pytest.raises(ValueError, match="sizes"):
+        pdf.pdf_gs_apply_static(gs, x, torch.zeros((3, 3), dtype=torch.complex64))
+    with pytest.raises(ValueError, match="GPU"):
+        pdf.pdf_gs_apply_static(gs, x, out)              # right sizes, host memory

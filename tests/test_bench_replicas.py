@@ -68,10 +68,11 @@ def test_single_rank_needs_no_collective():
                                                               ("c3", 23.6, 70.8, 0.05), ("c5", 94.4, 283.1, 0.05)])
 def test_byte_models_per_iteration(name, bmin_mb, bmodel_mb, half_unit):
     # B_min = U + 2|G_S| and B_model = 11 U + 2|G_S| (U = Ni M 8 B, |G_S| = Nr M 8 B) for the
-    # workload sizes; the fractions divide them by the loop time per iteration and the copy peak
+    # workload sizes with the unfolded data term; the fractions divide them by the loop time per
+    # iteration and the copy peak
     import scenes
     w = scenes.workload(name)
-    m = bench.hbm_model(w, loop_ms=w.iters * 1e-3, peaks={"hbm_gbs": 1000.0})   # 1 us per iteration
+    m = bench.hbm_model(w, loop_ms=w.iters * 1e-3, peaks={"hbm_gbs": 1000.0}, fold=0)   # 1 us per iteration
     assert abs(m["B_min_MB"] - bmin_mb) <= half_unit            # the figures as printed, rounded
     assert abs(m["B_model_MB"] - bmodel_mb) <= half_unit
     assert abs(m["t_iter_us"] - 1.0) < 1e-9
@@ -106,3 +107,27 @@ def test_clock_sampler_without_nvidia_smi(monkeypatch, tmp_path):
     c = bench.Clocks(0)
     c.start()
     assert c.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_byte_models_count_the_folded_operator():
+    # with the folded data term the operator read twice per iteration is G_S Phi, Nr K^2 8 B
+    # (c2: 32 x 225 x 8 = 57.6 kB) instead of G_S (32 x 4096 x 8 = 1.05 MB); U = 16 x 4096 x 8
+    import scenes
+    w = scenes.workload("c2")
+    m = bench.hbm_model(w, loop_ms=w.iters * 1e-3, peaks={"hbm_gbs": 1000.0}, fold=1)
+    U, G = 16 * 4096 * 8, 32 * 225 * 8
+    assert m["B_min_MB"] == pytest.approx((U + 2 * G) / 1e6)
+    assert m["B_model_MB"] == pytest.approx((11 * U + 2 * G) / 1e6)
+
+
+def test_cluster_flops_c2_both_forms():
+    # c2 by hand: 64 x 64 grid, padding 128, K = 15, Nr = 32, Ni = 16.  Per incidence:
+    #   synthesis 8 (64 15 15 + 64 64 15) = 606 720, analysis the same;
+    #   G_D: 2 x 64 row + 2 x 128 column 128-point FFTs at 5 x 128 x 7 = 4 480 flops, plus
+    #        6 x 128 x 128 spectrum products = 1 818 624, G_D^H the same;
+    #   data term: folded 8 x 32 x 225 = 57 600 each way, unfolded 8 x 32 x 4096 = 1 048 576.
+    import scenes
+    w = scenes.workload("c2")
+    per_inc = 2 * 606720 + 2 * 1818624
+    assert bench.cluster_flops(w, fold=1) == 16 * (per_inc + 2 * 57600) == 79454208
+    assert bench.cluster_flops(w, fold=0) == 16 * (per_inc + 2 * 1048576) == 111165440

@@ -13,7 +13,7 @@ import pytest
 
 import scenes
 from oracle import fcnn, solve
-from tests.gpu_common import Case, rel
+from tests.gpu_common import Case, assert_close, rel
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -42,9 +42,8 @@ def test_one_step_matches_oracle(name, kw):
     ref = fcnn.reparam_solve(c.ops, c.esca, 1, th0, H, lr=1e-2, alpha0=a0.astype(np.complex128), apply_cco=False)
     d_gpu = out["alpha"].cpu().numpy() - a0
     d_ref = ref["alpha"] - a0
-    print(name, "one-step Delta alpha rel", rel(d_gpu, d_ref))
     assert np.abs(d_ref).max() > 0
-    assert rel(d_gpu, d_ref) < 1e-3
+    assert_close(f"{name} one-step Delta alpha", d_gpu, d_ref, 1e-3)
     prob.close()
 
 

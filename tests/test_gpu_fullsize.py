@@ -12,7 +12,7 @@ import scenes
 from oracle import loss
 from oracle.green import Operators
 from oracle.problem import from_workload
-from tests.gpu_common import TOL_FP32, rel
+from tests.gpu_common import TOL_FP32, assert_close, rel
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -41,5 +41,5 @@ def test_fullsize_loss_gradient(big, precision, fold):
     print(w.name, precision, fold, "loss rel", abs(t[0] - t_ref[0]) / abs(t_ref[0]), "grad rel", eg)
     for k in range(3):
         assert abs(t[k] - t_ref[k]) <= TOL_FP32 * abs(t_ref[k])
-    assert eg < TOL_FP32
+    assert_close(f"{w.name} gradient", grad, g_ref, TOL_FP32)
     prob.close()

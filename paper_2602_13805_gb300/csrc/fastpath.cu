@@ -27,6 +27,167 @@ __global__ void __launch_bounds__(FT, (PY <= 384 ? 3 : 2)) kf_colconv(Dev d, int
   extern __shared__ float2 sm[];
   ph_colconv<PY>(d, blockIdx.x, blockIdx.y, sm, conj);
 }
+// ---------------------------------------------------------------------------
+// Column convolution, pipelined: persistent CTAs walk tiles of PCOLS padded columns of one
+// incidence; the next tile's column data are copied into the second shared-memory buffer with
+// cp.async while the warps transform the current one (one column per warp: forward register FFT,
+// x G_D spectrum or its conjugate, inverse, in place), so the global-load latency of the tile
+// overlaps the FFT work instead of stalling every warp of the CTA at the start.
+// ---------------------------------------------------------------------------
+#define PCOLS 8            // columns per tile of the pipelined column convolution
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int PY>
+__global__ void __launch_bounds__(FT, (PY <= 384 ? 3 : 2)) kf_colconv_pipe(Dev d, int conj, int ntiles) {
+  constexpr int R = PY / 32;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;                                     // [PY]
+  const int LS = d.ny + 1;                             // column stride in the tile (odd: no bank conflicts)
+  float2* bufs = sm + PY;                              // [2][PCOLS][LS]
+  const int ngrp = d.Px / PCOLS;                       // tiles per incidence
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nel = PCOLS * d.ny;
+  auto issue = [&](int t, float2* tile) {
+    const int p = t / ngrp, c0 = (t - p * ngrp) * PCOLS;
+    const float2* Ap = d.A + (size_t)p * d.ny * d.Px + c0;
+    for (int i = threadIdx.x; i < nel; i += FT) {
+      const int y = i / PCOLS, c = i - y * PCOLS;
+      cp_async8(&tile[c * LS + y], &Ap[(size_t)y * d.Px + c]);
+    }
+  };
+  load_tw<PY>(tw, d.twy);
+  int t = blockIdx.x, cur = 0;
+  if (t < ntiles) issue(t, bufs);
+  cp_async_commit();
+  for (; t < ntiles; t += gridDim.x) {
+    float2* tile = bufs + cur * PCOLS * LS;
+    const int tn = t + gridDim.x;
+    if (tn < ntiles) issue(tn, bufs + (cur ^ 1) * PCOLS * LS);
+    cp_async_commit();
+    cp_async_wait<1>();                                // this tile's copies have landed (own thread)
+    __syncthreads();                                   // ... and every thread's
+    const int p = t / ngrp, c0 = (t - p * ngrp) * PCOLS;
+    for (int c = warp; c < PCOLS; c += FW) {
+      const int cx = c0 + c;
+      float2 v[R];
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int y = lane + 32 * m;
+        v[m] = (2 * m < R && y < d.ny) ? tile[c * LS + y] : make_float2(0.f, 0.f);
+      }
+      WarpFFT<PY>::forward(v, tw, lane);
+      const float2* g = d.ghat_perm + (size_t)cx * PY;
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        float2 s = __ldg(&g[k * 32 + lane]);
+        if (conj) s.y = -s.y;
+        v[k] = cmul(v[k], s);
+      }
+      WarpFFT<PY>::inverse(v, tw, lane);
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int y = lane + 32 * m;
+        if (2 * m < R && y < d.ny) tile[c * LS + y] = v[m];
+      }
+    }
+    __syncthreads();
+    float2* Ap = d.A + (size_t)p * d.ny * d.Px + c0;
+    for (int i = threadIdx.x; i < nel; i += FT) {
+      const int y = i / PCOLS, c = i - y * PCOLS;
+      Ap[(size_t)y * d.Px + c] = tile[c * LS + y];
+    }
+    __syncthreads();                                   // the buffer is refilled two tiles on
+    cur ^= 1;
+  }
+  cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint row IFFT + x-analysis, persistent: each CTA stages the twiddles and the x basis
+// Wx [kx][nx] in shared memory once and its warps then walk rows (p, y) independently: inverse
+// row DFT of dL/dJ's row spectrum, + v (+ the G_S^H term when unfolded), and
+// T2[p][y][jx] = sum_x g[x] conj(Wx[jx][x]) in blocks of 8 coefficients (per-lane partial sums
+// over the lane's x, then an 8-way warp reduce-scatter), all basis reads from shared memory.
+// ---------------------------------------------------------------------------
+// Warp reduce-scatter of 8 complex values: on return lane l holds in a[0] the warp-wide sum of
+// the values with index l >> 2.
+__device__ __forceinline__ void warp_reduce_scatter8(float2 (&a)[8], int lane) {
+#pragma unroll
+  for (int st = 0; st < 3; ++st) {
+    const int h = 16 >> st, n = 4 >> st;
+    const bool up = (lane & h) != 0;
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      const float2 send = up ? a[i] : a[i + n];
+      const float2 keep = up ? a[i + n] : a[i];
+      a[i] = keep + shfl_xor2(send, h);
+    }
+  }
+  a[0] = a[0] + shfl_xor2(a[0], 2);
+  a[0] = a[0] + shfl_xor2(a[0], 1);
+}
+
+template <int PX>
+__global__ void __launch_bounds__(FT, 3) kf_adj_ana_p(Dev d, const float2* in, int mode) {
+  constexpr int R = PX / 32;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;                       // [PX]
+  float2* wxs = sm + PX;                 // [kx][nx]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  load_tw<PX>(tw, d.twx);
+  for (int i = threadIdx.x; i < d.kx * d.nx; i += FT) wxs[i] = d.wx[i];
+  __syncthreads();
+  const int nrows = d.ni * d.ny;
+  for (int row = blockIdx.x * FW + warp; row < nrows; row += gridDim.x * FW) {
+    float2 g[R];
+    if (mode == 0) {
+#pragma unroll
+      for (int k = 0; k < R; ++k) g[k] = d.A[(size_t)row * PX + k * 32 + lane];
+      WarpFFT<PX>::inverse(g, tw, lane);
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int x = lane + 32 * m;
+        if (2 * m < R && x < d.nx) {
+          const size_t idx = (size_t)row * d.nx + x;
+          g[m] = d.fold ? g[m] + d.v[idx] : g[m] + d.v[idx] + d.gsh[idx];
+        } else {
+          g[m] = make_float2(0.f, 0.f);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int x = lane + 32 * m;
+        g[m] = (2 * m < R && x < d.nx) ? in[(size_t)row * d.nx + x] : make_float2(0.f, 0.f);
+      }
+    }
+    for (int j0 = 0; j0 < d.kx; j0 += 8) {
+      float2 acc[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int x = lane + 32 * m;
+        if (2 * m < R && x < d.nx) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (j0 + j < d.kx) acc[j] = acc[j] + cmulc(g[m], wxs[(j0 + j) * d.nx + x]);
+        }
+      }
+      warp_reduce_scatter8(acc, lane);
+      const int jx = j0 + (lane >> 2);
+      if ((lane & 3) == 0 && jx < d.kx) d.T2[(size_t)row * d.kx + jx] = acc[0];
+    }
+  }
+}
+
 template <int PX>
 __global__ void __launch_bounds__(FT) kf_rowifft_state(Dev d) {
   extern __shared__ float2 sm[];
@@ -70,6 +231,8 @@ pdf_status fp_configure() {
 #define CFG(P)                                                                                        \
   cudaFuncSetAttribute(kf_synth_rowfft<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);  \
   cudaFuncSetAttribute(kf_colconv<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);       \
+  cudaFuncSetAttribute(kf_colconv_pipe<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);  \
+  cudaFuncSetAttribute(kf_adj_ana_p<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);     \
   cudaFuncSetAttribute(kf_rowifft_state<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024); \
   cudaFuncSetAttribute(kf_adj_rowifft_ana<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024); \
   cudaFuncSetAttribute(kf_rowifft_sums<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
@@ -104,7 +267,35 @@ pdf_status fp_rowifft_field(const Dev& d, float2* out, cudaStream_t st) {
 #undef L
   return PDF_OK;
 }
+size_t fp_smem_colpipe(const Dev& d) { return ((size_t)d.Py + 2 * (size_t)PCOLS * (d.ny + 1)) * sizeof(float2); }
+
+// resident CTAs of the pipelined column convolution on this device (grid = that many, at most the
+// tile count)
+template <int P>
+static int colpipe_slots(const Dev& d) {
+  static size_t smem = 0;
+  static int slots = 0;
+  const size_t need = fp_smem_colpipe(d);
+  if (need != smem) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kf_colconv_pipe<P>, FT, need);
+    cudaGetLastError();
+    slots = std::max(1, sms * std::max(1, occ));
+    smem = need;
+  }
+  return slots;
+}
+
 pdf_status fp_colconv(const Dev& d, int conj, cudaStream_t st) {
+  if (d.Px % PCOLS == 0) {
+    const int ntiles = d.ni * (d.Px / PCOLS);
+#define L(P) kf_colconv_pipe<P><<<std::min(ntiles, colpipe_slots<P>(d)), FT, fp_smem_colpipe(d), st>>>(d, conj, ntiles)
+    FAST_SWITCH(d.Py, L)
+#undef L
+    return PDF_OK;
+  }
 #define L(P) kf_colconv<P><<<dim3(d.Px / FCOLS, d.ni), FT, fp_smem_col(d), st>>>(d, conj)
   FAST_SWITCH(d.Py, L)
 #undef L
@@ -151,7 +342,36 @@ int fp_choose_nsg(const Dev& d, int sms) {
 
 // number of L_State partials written per loss-and-gradient evaluation on this path
 int fp_n_state(const Dev& d) { return d.nsg > 0 ? (int)(frow_grid(d).x * frow_grid(d).y) : d.ny; }
+size_t fp_smem_ana_p(const Dev& d) { return ((size_t)d.Px + (size_t)d.kx * d.nx) * sizeof(float2); }
+
+// resident CTAs of a persistent row kernel with `smem` bytes of dynamic shared memory
+template <class K>
+static int persistent_slots(K kernel, size_t smem) {
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, FT, smem);
+  cudaGetLastError();
+  return std::max(1, sms * std::max(1, occ));
+}
+
 pdf_status fp_adj_rowifft_ana(const Dev& d, const float2* in, int mode, cudaStream_t st) {
+  if (fp_smem_ana_p(d) <= 64 * 1024) {
+    const int nrows = d.ni * d.ny, nb = (nrows + FW - 1) / FW;
+#define L(P)                                                                                     \
+  {                                                                                              \
+    static size_t sm_ = 0;                                                                       \
+    static int slots_ = 0;                                                                       \
+    if (sm_ != fp_smem_ana_p(d)) {                                                               \
+      sm_ = fp_smem_ana_p(d);                                                                    \
+      slots_ = persistent_slots(kf_adj_ana_p<P>, sm_);                                           \
+    }                                                                                            \
+    kf_adj_ana_p<P><<<std::min(nb, slots_), FT, sm_, st>>>(d, in, mode);                         \
+  }
+    FAST_SWITCH(d.Px, L)
+#undef L
+    return PDF_OK;
+  }
 #define L(P) kf_adj_rowifft_ana<P><<<frow_grid(d), FT, fp_smem_ana(d), st>>>(d, in, mode)
   FAST_SWITCH(d.Px, L)
 #undef L

@@ -36,6 +36,11 @@ __global__ void __launch_bounds__(FT, (PY <= 384 ? 3 : 2)) kf_colconv(Dev d, int
 // ---------------------------------------------------------------------------
 #define PCOLS 8            // columns per tile of the pipelined column convolution
 
+// Column stride of a tile, the first >= ny that is 2 mod 16 (in complex64 words): a warp's copies
+// and stores walk 4 rows x 8 columns, and with this stride each 16-thread half touches 16 distinct
+// 8-byte banks; the FFT's reads of one column (lanes along y) are contiguous whatever the stride.
+__host__ __device__ __forceinline__ int colpipe_ls(int ny) { return ny + ((18 - ny % 16) % 16); }
+
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
@@ -49,7 +54,7 @@ __global__ void __launch_bounds__(FT, (PY <= 384 ? 3 : 2)) kf_colconv_pipe(Dev d
   constexpr int R = PY / 32;
   extern __shared__ float2 sm[];
   float2* tw = sm;                                     // [PY]
-  const int LS = d.ny + 1;                             // column stride in the tile (odd: no bank conflicts)
+  const int LS = colpipe_ls(d.ny);
   float2* bufs = sm + PY;                              // [2][PCOLS][LS]
   const int ngrp = d.Px / PCOLS;                       // tiles per incidence
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -188,6 +193,59 @@ __global__ void __launch_bounds__(FT, 3) kf_adj_ana_p(Dev d, const float2* in, i
   }
 }
 
+// ---------------------------------------------------------------------------
+// Synthesis + padded row DFT, persistent: each CTA stages the twiddles and the x basis Wx [kx][nx]
+// in shared memory once; its warps then walk rows (p, y): T'[jx] = sum_jy Wy[jy][y] alpha_p[jy][jx]
+// (lanes over jx), J[y][x] = sum_jx T'[jx] Wx[jx][x] (Eq. 9) with the basis read from shared
+// memory, then the forward register FFT of the row into A.
+// ---------------------------------------------------------------------------
+template <int PX>
+__global__ void __launch_bounds__(FT, 3) kf_synth_p(Dev d, const float2* __restrict__ alpha, float2* __restrict__ Jout,
+                                                    int do_fft) {
+  constexpr int R = PX / 32;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;                       // [PX]
+  float2* wxs = sm + PX;                 // [kx][nx]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  load_tw<PX>(tw, d.twx);
+  for (int i = threadIdx.x; i < d.kx * d.nx; i += FT) wxs[i] = d.wx[i];
+  __syncthreads();
+  const int nrows = d.ni * d.ny, NA = d.ky * d.kx;
+  for (int row = blockIdx.x * FW + warp; row < nrows; row += gridDim.x * FW) {
+    const int p = row / d.ny, y = row - p * d.ny;
+    const float2* ap = alpha + (size_t)p * NA;
+    float2 t0 = make_float2(0.f, 0.f), t1 = make_float2(0.f, 0.f);
+    for (int jy = 0; jy < d.ky; ++jy) {
+      const float2 w = __ldg(&d.wy[jy * d.ny + y]);
+      if (lane < d.kx) t0 = t0 + cmul(w, __ldg(&ap[jy * d.kx + lane]));
+      if (lane + 32 < d.kx) t1 = t1 + cmul(w, __ldg(&ap[jy * d.kx + lane + 32]));
+    }
+    float2 v[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[m] = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (int jx = 0; jx < d.kx; ++jx) {
+      const float2 src = jx < 32 ? t0 : t1;
+      const float2 T = make_float2(__shfl_sync(0xffffffffu, src.x, jx & 31), __shfl_sync(0xffffffffu, src.y, jx & 31));
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int x = lane + 32 * m;
+        if (2 * m < R && x < d.nx) v[m] = v[m] + cmul(T, wxs[jx * d.nx + x]);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const int x = lane + 32 * m;
+      if (2 * m < R && x < d.nx) Jout[(size_t)row * d.nx + x] = v[m];
+    }
+    if (do_fft) {
+      WarpFFT<PX>::forward(v, tw, lane);
+#pragma unroll
+      for (int k = 0; k < R; ++k) d.A[(size_t)row * PX + k * 32 + lane] = v[k];
+    }
+  }
+}
+
 template <int PX>
 __global__ void __launch_bounds__(FT) kf_rowifft_state(Dev d) {
   extern __shared__ float2 sm[];
@@ -233,6 +291,7 @@ pdf_status fp_configure() {
   cudaFuncSetAttribute(kf_colconv<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);       \
   cudaFuncSetAttribute(kf_colconv_pipe<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);  \
   cudaFuncSetAttribute(kf_adj_ana_p<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);     \
+  cudaFuncSetAttribute(kf_synth_p<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);       \
   cudaFuncSetAttribute(kf_rowifft_state<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024); \
   cudaFuncSetAttribute(kf_adj_rowifft_ana<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024); \
   cudaFuncSetAttribute(kf_rowifft_sums<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
@@ -249,7 +308,27 @@ size_t fp_smem_state(const Dev& d) { return (size_t)d.Px * sizeof(float2) * 2 + 
 size_t fp_smem_ana(const Dev& d) { return (size_t)d.Px * sizeof(float2); }
 size_t fp_smem_sums(const Dev& d) { return (size_t)d.Px * sizeof(float2) + 3 * FW * (size_t)(d.Px / 2) * sizeof(float); }
 
+size_t fp_smem_ana_p(const Dev& d);
+template <class K>
+static int persistent_slots(K kernel, size_t smem);
+
 pdf_status fp_synth_rowfft(const Dev& d, const float2* alpha, float2* Jout, int do_fft, cudaStream_t st) {
+  if (fp_smem_ana_p(d) <= 64 * 1024) {                 // same staging: twiddles + Wx
+    const int nrows = d.ni * d.ny, nb = (nrows + FW - 1) / FW;
+#define L(P)                                                                                     \
+  {                                                                                              \
+    static size_t sm_ = 0;                                                                       \
+    static int slots_ = 0;                                                                       \
+    if (sm_ != fp_smem_ana_p(d)) {                                                               \
+      sm_ = fp_smem_ana_p(d);                                                                    \
+      slots_ = persistent_slots(kf_synth_p<P>, sm_);                                             \
+    }                                                                                            \
+    kf_synth_p<P><<<std::min(nb, slots_), FT, sm_, st>>>(d, alpha, Jout, do_fft);                \
+  }
+    FAST_SWITCH(d.Px, L)
+#undef L
+    return PDF_OK;
+  }
 #define L(P) kf_synth_rowfft<P><<<frow_grid(d), FT, fp_smem_synth(d), st>>>(d, alpha, Jout, do_fft)
   FAST_SWITCH(d.Px, L)
 #undef L
@@ -267,7 +346,7 @@ pdf_status fp_rowifft_field(const Dev& d, float2* out, cudaStream_t st) {
 #undef L
   return PDF_OK;
 }
-size_t fp_smem_colpipe(const Dev& d) { return ((size_t)d.Py + 2 * (size_t)PCOLS * (d.ny + 1)) * sizeof(float2); }
+size_t fp_smem_colpipe(const Dev& d) { return ((size_t)d.Py + 2 * (size_t)PCOLS * colpipe_ls(d.ny)) * sizeof(float2); }
 
 // resident CTAs of the pipelined column convolution on this device (grid = that many, at most the
 // tile count)

@@ -345,8 +345,9 @@ __global__ void __launch_bounds__(ROW_THREADS) k_adj_rowifft_ana(Dev d, const fl
 
 // analysis along y: out[p][jy][jx] = sum_y conj(wy[jy][y]) T2[p][y][jx]; one CTA per (jy, p),
 // eight warps over interleaved y, lanes over jx (kx <= 64)
-__global__ void __launch_bounds__(256) k_ana_y(Dev d, const float2* T2, float2* out) {
+__global__ void __launch_bounds__(256) k_ana_y(Dev d, const float2* T2, float2* out, int* step_inc) {
   ph_ana_y(d, blockIdx.x, blockIdx.y, T2, out);
+  if (step_inc && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *step_inc += 1;
 }
 
 // terms[6] = L, State, Data, Bound, TV, Bridge from the partial sums
@@ -452,9 +453,13 @@ static int gsf_nsplit(const Dev& d) { return (d.ky * d.kx + gsf_kc(d) - 1) / gsf
 // Analysis along y (second half of Phi^H): out[p][jy][jx] = sum_y T2[p][y][jx] conj(Wy[jy][y]).
 // Block (p, jy group of 8) stages T2[p] and the 8 rows of Wy in shared memory; warp jl owns
 // coefficient row jy = 8 blockIdx.y + jl, its lanes the jx (kx <= 64).
-__global__ void __launch_bounds__(256) k_ana_y_sm(Dev d, const float2* __restrict__ T2, float2* __restrict__ out) {
+__global__ void __launch_bounds__(256) k_ana_y_sm(Dev d, const float2* __restrict__ T2, float2* __restrict__ out,
+                                                  int* step_inc) {
   extern __shared__ float2 smy[];
   const int p = blockIdx.x, jl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // the Adam step counter of a solve-loop evaluation (no k_finalize there); nothing before the
+  // Adam step that follows reads it
+  if (step_inc && p == 0 && blockIdx.y == 0 && threadIdx.x == 0) *step_inc += 1;
   const int ny = d.ny, kx = d.kx, jy0 = blockIdx.y * 8;
   float2* Ts = smy;                 // [ny][kx]
   float2* Ws = smy + ny * kx;       // [8][ny]
@@ -583,6 +588,9 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
   const int nout = d.ni * d.nr;
   const int n_data_blocks = (nout + 255) / 256;
   const bool tc = h->tc != nullptr;
+  // an evaluation inside the solve loop (an Adam step counter, no loss terms wanted): the loss
+  // partials are not summed (no k_finalize) and the y-analysis advances the step counter
+  const bool loop_eval = step_inc != nullptr && terms == nullptr && ev == nullptr;
   pdf_status s;
   int k = 0;
   auto mark = [&]() {
@@ -665,18 +673,20 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
   mark();
   float2* g = grad ? grad : h->grad;
   if (ana_y_sm_ok(d))
-    k_ana_y_sm<<<dim3(d.ni, (d.ky + 7) / 8), 256, sm_ana_y(d), st>>>(d, T2, g);
+    k_ana_y_sm<<<dim3(d.ni, (d.ky + 7) / 8), 256, sm_ana_y(d), st>>>(d, T2, g, loop_eval ? step_inc : nullptr);
   else
-    k_ana_y<<<dim3(d.ky, d.ni), 256, 0, st>>>(d, T2, g);
+    k_ana_y<<<dim3(d.ky, d.ni), 256, 0, st>>>(d, T2, g, loop_eval ? step_inc : nullptr);
   mark();
   if (d.fold) {
     k_gsf_adj<<<dim3((d.ky * d.kx + 31) / 32, (d.ni + 7) / 8), 256, 0, st>>>(d, d.rd, g);
     mark();
   }
-  k_finalize<<<1, 1024, 0, st>>>(d, terms ? terms : h->terms, d.fast ? fp_n_state(d) : d.ny, n_data_blocks,
-                                d.n_reg_blocks, step_inc);
-  mark();
-  pdf_count_launch(d.fold ? (tc ? 10 : 12) : (tc ? 7 : 12));
+  if (!loop_eval) {
+    k_finalize<<<1, 1024, 0, st>>>(d, terms ? terms : h->terms, d.fast ? fp_n_state(d) : d.ny, n_data_blocks,
+                                  d.n_reg_blocks, step_inc);
+    mark();
+  }
+  pdf_count_launch((d.fold ? (tc ? 10 : 12) : (tc ? 7 : 12)) - (loop_eval ? 1 : 0));
   PDF_LAUNCHED("pdf_loss_grad");
   return PDF_OK;
 }
@@ -749,9 +759,9 @@ pdf_status hp_analysis(pdf_problem* h, const float2* in, float2* out, cudaStream
     k_adj_rowifft_ana<<<row_grid(d), ROW_THREADS, sm_row(d), st>>>(d, in, 1);
   }
   if (ana_y_sm_ok(d))
-    k_ana_y_sm<<<dim3(d.ni, (d.ky + 7) / 8), 256, sm_ana_y(d), st>>>(d, T2, out);
+    k_ana_y_sm<<<dim3(d.ni, (d.ky + 7) / 8), 256, sm_ana_y(d), st>>>(d, T2, out, nullptr);
   else
-    k_ana_y<<<dim3(d.ky, d.ni), 256, 0, st>>>(d, T2, out);
+    k_ana_y<<<dim3(d.ky, d.ni), 256, 0, st>>>(d, T2, out, nullptr);
   pdf_count_launch(2);
   PDF_LAUNCHED("analysis");
   return PDF_OK;

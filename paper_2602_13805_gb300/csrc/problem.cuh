@@ -184,7 +184,7 @@ pdf_status hp_check_limits(const Dev& d);
 pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, double* terms, cudaStream_t st,
                         int* step_inc = nullptr, cudaEvent_t* ev = nullptr);
 const char* hp_kernel_name(int k, int precision, int fold);
-__global__ void k_ana_y(Dev d, const float2* T2, float2* out);
+__global__ void k_ana_y(Dev d, const float2* T2, float2* out, int* step_inc);
 pdf_status hp_gd(pdf_problem* h, const float2* in, float2* out, int adjoint, cudaStream_t st);
 pdf_status hp_gs(pdf_problem* h, const float2* in, float2* out, const float2* subtract, FF* sumsq, cudaStream_t st);
 pdf_status hp_gsh(pdf_problem* h, const float2* in, float2* out, float scale, cudaStream_t st);

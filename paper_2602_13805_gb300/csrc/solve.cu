@@ -327,11 +327,13 @@ static pdf_status adam_step(pdf_problem* h, const pdf_solve_opts* o, cudaStream_
 }
 
 static pdf_status iteration(pdf_problem* h, const pdf_solve_opts* o, cudaStream_t st) {
+  // the loss terms are summed only when a history row wants them
+  double* terms = o->history_every > 0 ? h->terms : nullptr;
   if (h->fc_active) {
     // alpha = alpha0 + Delta alpha(theta); loss gradient; chain rule to theta; Adam on theta
     pdf_status s = fc_forward(h, st);
     if (s != PDF_OK) return s;
-    if ((s = hp_loss_grad(h, h->alpha, h->grad, h->terms, st, h->adam_t)) != PDF_OK) return s;
+    if ((s = hp_loss_grad(h, h->alpha, h->grad, terms, st, h->adam_t)) != PDF_OK) return s;
     if ((s = fc_backward(h, st)) != PDF_OK) return s;
     const int n = (int)h->fc.np;
     k_adam<<<(n + 255) / 256, 256, 0, st>>>(h->fc.theta, h->fc.gtheta, h->fc.m, h->fc.v, n, h->adam_t, h->adam_tab,
@@ -340,7 +342,7 @@ static pdf_status iteration(pdf_problem* h, const pdf_solve_opts* o, cudaStream_
     PDF_LAUNCHED("Adam on the network weights");
     return PDF_OK;
   }
-  pdf_status s = hp_loss_grad(h, h->alpha, h->grad, h->terms, st, h->adam_t);
+  pdf_status s = hp_loss_grad(h, h->alpha, h->grad, terms, st, h->adam_t);
   if (s != PDF_OK) return s;
   return adam_step(h, o, st);
 }

@@ -175,7 +175,8 @@ def test_solve_parity_relerr():
     assert abs(out["relerr"] - ref["relerr"]) < 1e-3
     assert abs(out["relerr_cco"] - ref["relerr_cco"]) < 1e-3
     # eager and graph loops run the same kernels in the same order: bit-identical; the persistent
-    # loop runs the same phase code inlined into one kernel (different FMA contraction is allowed)
+    # loop runs the phase code inlined into one kernel, where the stand-alone synthesis and
+    # x-analysis kernels sum in a different order (8-coefficient reduce-scatters): FP32 drift only
     out_eager = prob.solve(iters=w.iters, chi_true=chi_t, use_graph=0)
     out_graph = prob.solve(iters=w.iters, chi_true=chi_t, use_graph=1)
     assert torch.equal(out_eager["alpha"], out_graph["alpha"])
@@ -185,7 +186,7 @@ def test_solve_parity_relerr():
     out_eager = prob.solve(iters=w.iters, chi_true=chi_t, use_graph=0)
     out_pers = prob.solve(iters=w.iters, chi_true=chi_t, use_graph=2)
     scale = out_eager["alpha"].abs().max().item()
-    assert (out_eager["alpha"] - out_pers["alpha"]).abs().max().item() < 1e-6 * scale
+    assert (out_eager["alpha"] - out_pers["alpha"]).abs().max().item() < 1e-5 * scale
     assert abs(out_pers["relerr_cco"] - ref["relerr_cco"]) < 1e-3
     prob.close()
 
@@ -200,8 +201,10 @@ def test_persistent_loop_matches_graph(name):
     b = prob.solve(iters=w.iters, chi_true=chi_t, use_graph=2)
     b2 = prob.solve(iters=w.iters, chi_true=chi_t, use_graph=2)
     assert torch.equal(b["alpha"], b2["alpha"])                     # deterministic
-    assert (a["alpha"] - b["alpha"]).abs().max().item() < 1e-6 * a["alpha"].abs().max().item()
-    assert abs(a["relerr_cco"] - b["relerr_cco"]) < 1e-6
+    # same formulas; the graph's synthesis and x-analysis kernels sum in another order than the
+    # phase code the persistent kernel inlines (measured 3.4e-6 of max |alpha| after 40 steps at c2)
+    assert (a["alpha"] - b["alpha"]).abs().max().item() < 1e-5 * a["alpha"].abs().max().item()
+    assert abs(a["relerr_cco"] - b["relerr_cco"]) < 1e-5
     prob.close()
 
 

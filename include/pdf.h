@@ -290,6 +290,11 @@ pdf_status pdf_mlp_train_step(pdf_mlp* m, const float* X, const float* T, int32_
                               void* stream);
 /* 1 if a tensor-core wait timed out in an earlier call, 0 otherwise (synchronises). */
 int32_t pdf_mlp_error_flag(pdf_mlp* m);
+/* The network's input for B scenes: esca [B][n] complex64 (n = ni nr, each scene's measured field,
+ * device) -> X [B][2 n] float32 (device), X[b][2 i + c] = (Re, Im) of esca[b][i] divided by the
+ * scene's RMS magnitude ||esca[b]|| / sqrt(n) (unscaled when the field is zero).  Errors:
+ * PDF_EINVAL for NULL pointers or sizes < 1. */
+pdf_status pdf_mlp_features(const void* esca, int32_t B, int32_t n, float* X, void* stream);
 
 /* Number of kernels this library has launched in the calling process (graph launches count
  * every kernel node they execute).  For benchmarking evidence. */

@@ -378,3 +378,35 @@ extern "C" int32_t pdf_mlp_error_flag(pdf_mlp* m) {
   cudaMemcpy(&v, m->err, sizeof(int), cudaMemcpyDeviceToHost);
   return v;
 }
+
+// Warm-start network input: X[b][2 i + c] = (Re, Im) of E[b][i] / (||E[b]|| / sqrt(n)), one CTA per
+// scene (FP32 Kahan partial sums per thread, FP64 across threads).
+__global__ void __launch_bounds__(256) k_mlp_features(const float2* __restrict__ E, int n, float* __restrict__ X) {
+  __shared__ double red[32];
+  __shared__ float inv;
+  const int b = blockIdx.x;
+  const float2* e = E + (size_t)b * n;
+  float s = 0.f, c = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float2 v = e[i];
+    const float y = (v.x * v.x + v.y * v.y) - c, t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  const double tot = block_sum((double)s - (double)c, red);
+  if (threadIdx.x == 0) inv = tot > 0.0 ? (float)(1.0 / sqrt(tot / n)) : 1.f;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float2 v = e[i];
+    X[(size_t)b * 2 * n + 2 * i] = v.x * inv;
+    X[(size_t)b * 2 * n + 2 * i + 1] = v.y * inv;
+  }
+}
+
+extern "C" pdf_status pdf_mlp_features(const void* esca, int32_t B, int32_t n, float* X, void* stream) {
+  if (!esca || !X || B < 1 || n < 1) return set_err(PDF_EINVAL, "pdf_mlp_features: NULL pointer or size < 1");
+  k_mlp_features<<<B, 256, 0, (cudaStream_t)stream>>>((const float2*)esca, n, X);
+  pdf_count_launch(1);
+  PDF_LAUNCHED("pdf_mlp_features");
+  return PDF_OK;
+}

@@ -86,7 +86,7 @@ EXPORTS = ("pdf_config_default", "pdf_setup", "pdf_set_data", "pdf_loss_grad", "
            "pdf_last_error", "pdf_profile_loss_grad", "pdf_kernel_name", "pdf_gs_apply_static",
            "pdf_stage_name", "pdf_mlp_create", "pdf_mlp_destroy", "pdf_mlp_set_params", "pdf_mlp_get_params",
            "pdf_mlp_forward", "pdf_mlp_loss_grad", "pdf_mlp_train_step", "pdf_mlp_error_flag",
-           "pdf_phase_stamps", "pdf_cluster_plan", "pdf_fp32_fma_peak")
+           "pdf_phase_stamps", "pdf_cluster_plan", "pdf_fp32_fma_peak", "pdf_mlp_features")
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -148,6 +148,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pdf_mlp_train_step.restype = ctypes.c_int
     lib.pdf_mlp_error_flag.argtypes = [vp]
     lib.pdf_mlp_error_flag.restype = i32
+    lib.pdf_mlp_features.argtypes = [vp, i32, i32, vp, vp]
+    lib.pdf_mlp_features.restype = ctypes.c_int
     lib.pdf_last_error.argtypes = []
     lib.pdf_last_error.restype = ctypes.c_char_p
     _lib = lib

@@ -95,12 +95,15 @@ class WarmStartMLP:
 
 
 def features(esca):
-    """x from E_sca [B][ni][nr] complex64 (device): normalised, [Re, Im] interleaved, flattened."""
+    """x from E_sca [B][ni][nr] complex64 (device): each scene divided by its RMS magnitude, [Re, Im]
+    interleaved, flattened (pdf_mlp_features)."""
     import torch
+    esca = esca.contiguous()
     B = esca.shape[0]
-    flat = esca.reshape(B, -1)
-    scale = torch.linalg.norm(flat, dim=1, keepdim=True) / math.sqrt(flat.shape[1])
-    return torch.view_as_real((flat / scale).contiguous()).reshape(B, -1).contiguous()
+    n = esca[0].numel()
+    X = torch.empty((B, 2 * n), dtype=torch.float32, device=esca.device)
+    pdf._check(pdf.load().pdf_mlp_features(_dev_ptr(esca), B, n, _dev_ptr(X), pdf._stream(None)))
+    return X
 
 
 @dataclass

@@ -98,3 +98,18 @@ def test_warm_start_gain():
     assert np.mean([r["loss0_warm"] for r in res]) < np.mean([r["loss0_plain"] for r in res])
     net.close()
     prob.close()
+
+
+def test_features_match_the_definition():
+    # each scene's field divided by its RMS magnitude, (Re, Im) interleaved; a zero scene unscaled
+    from paper_2602_13805_gb300.warmstart import features
+    rng = np.random.default_rng(3)
+    E = (rng.standard_normal((5, 16, 32)) + 1j * rng.standard_normal((5, 16, 32))) * rng.uniform(0.1, 10, (5, 1, 1))
+    E[3] = 0.0
+    E = E.astype(np.complex64)
+    X = features(torch.from_numpy(E).cuda()).cpu().numpy()
+    flat = E.reshape(5, -1).astype(np.complex128)
+    rms = np.linalg.norm(flat, axis=1) / np.sqrt(flat.shape[1])
+    rms[3] = 1.0
+    ref = np.stack([(flat / rms[:, None]).real, (flat / rms[:, None]).imag], axis=-1).reshape(5, -1)
+    assert np.abs(X - ref).max() <= 1e-6 * np.abs(ref).max()

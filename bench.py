@@ -166,9 +166,9 @@ def kernel_bytes(w):
 
 
 # the CUDA kernel behind each profiled stage of the register-FFT path at the bench's sizes
-KERNEL_OF_STAGE = {"k_colconv": "kf_colconv_pipe<P>", "k_synth_rowfft": "kf_synth_rowfft<P>",
+KERNEL_OF_STAGE = {"k_colconv": "kf_colconv_pipe<P>", "k_synth_rowfft": "kf_synth_p<P>",
                    "k_adj_rowifft_ana": "kf_adj_ana_p<P>", "k_rowifft_state": "kf_rowifft_sums<P> + k_state_combine",
-                   "k_adj_rowfft": "kf_adj_rowfft<P>"}
+                   "k_adj_rowfft": "kf_adj_rowfft<P>", "k_gsf_fwd": "k_gsf_fwd_p"}
 
 # DRAM bytes (read + write) per launch from one ncu capture, by (workload, stage); None until the
 # kernel has been captured in its current form (see profiles/)

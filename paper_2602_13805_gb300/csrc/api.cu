@@ -562,6 +562,7 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
   k_synth_table<<<dim3((d.ny + 127) / 128, d.ky), 128, 0, s>>>(wy, d.ky, d.ny);
   pdf_count_launch(10);
   d.fold = cfg->fold_gs;
+  d.rdwarp = 0;
   d.gsf = nullptr;
   if (d.fold) {
     float2 *gsf, *tfold;
@@ -571,6 +572,7 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
     k_fold_x<<<dim3((d.ky * d.kx + 127) / 128, d.nr), 128, 0, s>>>(tfold, wx, gsf, d.nx, d.ky, d.kx);
     pdf_count_launch(2);
     d.gsf = gsf;
+    d.rdwarp = hp_rdwarp_ok(d) ? 1 : 0;
   }
   {
     cudaError_t e = cudaGetLastError();

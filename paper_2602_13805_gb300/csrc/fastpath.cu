@@ -139,15 +139,19 @@ __device__ __forceinline__ void warp_reduce_scatter8(float2 (&a)[8], int lane) {
   a[0] = a[0] + shfl_xor2(a[0], 1);
 }
 
-template <int PX>
+// FULL: nx = PX / 2, so every one of the first R/2 slots of a row holds a grid column and no
+// per-slot bound checks are needed.  The x basis is staged with its rows padded to a multiple of 8
+// (zeros), so the last coefficient block needs no check either.
+template <int PX, bool FULL>
 __global__ void __launch_bounds__(FT, 3) kf_adj_ana_p(Dev d, const float2* in, int mode) {
   constexpr int R = PX / 32;
   extern __shared__ float2 sm[];
   float2* tw = sm;                       // [PX]
-  float2* wxs = sm + PX;                 // [kx][nx]
+  float2* wxs = sm + PX;                 // [kx8][nx]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kx8 = (d.kx + 7) & ~7;
   load_tw<PX>(tw, d.twx);
-  for (int i = threadIdx.x; i < d.kx * d.nx; i += FT) wxs[i] = d.wx[i];
+  for (int i = threadIdx.x; i < kx8 * d.nx; i += FT) wxs[i] = i < d.kx * d.nx ? d.wx[i] : make_float2(0.f, 0.f);
   __syncthreads();
   const int nrows = d.ni * d.ny;
   for (int row = blockIdx.x * FW + warp; row < nrows; row += gridDim.x * FW) {
@@ -159,7 +163,7 @@ __global__ void __launch_bounds__(FT, 3) kf_adj_ana_p(Dev d, const float2* in, i
 #pragma unroll
       for (int m = 0; m < R; ++m) {
         const int x = lane + 32 * m;
-        if (2 * m < R && x < d.nx) {
+        if (2 * m < R && (FULL || x < d.nx)) {
           const size_t idx = (size_t)row * d.nx + x;
           g[m] = d.fold ? g[m] + d.v[idx] : g[m] + d.v[idx] + d.gsh[idx];
         } else {
@@ -170,20 +174,19 @@ __global__ void __launch_bounds__(FT, 3) kf_adj_ana_p(Dev d, const float2* in, i
 #pragma unroll
       for (int m = 0; m < R; ++m) {
         const int x = lane + 32 * m;
-        g[m] = (2 * m < R && x < d.nx) ? in[(size_t)row * d.nx + x] : make_float2(0.f, 0.f);
+        g[m] = (2 * m < R && (FULL || x < d.nx)) ? in[(size_t)row * d.nx + x] : make_float2(0.f, 0.f);
       }
     }
     for (int j0 = 0; j0 < d.kx; j0 += 8) {
       float2 acc[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
+      const float2* wb = wxs + j0 * d.nx + lane;
 #pragma unroll
-      for (int m = 0; m < R; ++m) {
-        const int x = lane + 32 * m;
-        if (2 * m < R && x < d.nx) {
+      for (int m = 0; m < R / 2; ++m) {
+        if (FULL || lane + 32 * m < d.nx) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            if (j0 + j < d.kx) acc[j] = acc[j] + cmulc(g[m], wxs[(j0 + j) * d.nx + x]);
+          for (int j = 0; j < 8; ++j) acc[j] = acc[j] + cmulc(g[m], wb[j * d.nx + 32 * m]);
         }
       }
       warp_reduce_scatter8(acc, lane);
@@ -199,17 +202,21 @@ __global__ void __launch_bounds__(FT, 3) kf_adj_ana_p(Dev d, const float2* in, i
 // (lanes over jx), J[y][x] = sum_jx T'[jx] Wx[jx][x] (Eq. 9) with the basis read from shared
 // memory, then the forward register FFT of the row into A.
 // ---------------------------------------------------------------------------
-template <int PX>
+// FULL: nx = PX / 2 (no per-slot bound checks).  T' of the warp's row goes through a per-warp
+// shared-memory line and is read back as a broadcast, one load per coefficient.
+template <int PX, bool FULL>
 __global__ void __launch_bounds__(FT, 3) kf_synth_p(Dev d, const float2* __restrict__ alpha, float2* __restrict__ Jout,
                                                     int do_fft) {
   constexpr int R = PX / 32;
   extern __shared__ float2 sm[];
   float2* tw = sm;                       // [PX]
   float2* wxs = sm + PX;                 // [kx][nx]
+  float2* tl = wxs + d.kx * d.nx;        // [FW][64] T' of each warp's current row
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   load_tw<PX>(tw, d.twx);
   for (int i = threadIdx.x; i < d.kx * d.nx; i += FT) wxs[i] = d.wx[i];
   __syncthreads();
+  float2* tr = tl + warp * 64;
   const int nrows = d.ni * d.ny, NA = d.ky * d.kx;
   for (int row = blockIdx.x * FW + warp; row < nrows; row += gridDim.x * FW) {
     const int p = row / d.ny, y = row - p * d.ny;
@@ -220,23 +227,25 @@ __global__ void __launch_bounds__(FT, 3) kf_synth_p(Dev d, const float2* __restr
       if (lane < d.kx) t0 = t0 + cmul(w, __ldg(&ap[jy * d.kx + lane]));
       if (lane + 32 < d.kx) t1 = t1 + cmul(w, __ldg(&ap[jy * d.kx + lane + 32]));
     }
+    __syncwarp();
+    tr[lane] = t0;
+    tr[lane + 32] = t1;
+    __syncwarp();
     float2 v[R];
 #pragma unroll
     for (int m = 0; m < R; ++m) v[m] = make_float2(0.f, 0.f);
+    const float2* wb = wxs + lane;
 #pragma unroll 4
     for (int jx = 0; jx < d.kx; ++jx) {
-      const float2 src = jx < 32 ? t0 : t1;
-      const float2 T = make_float2(__shfl_sync(0xffffffffu, src.x, jx & 31), __shfl_sync(0xffffffffu, src.y, jx & 31));
+      const float2 T = tr[jx];
 #pragma unroll
-      for (int m = 0; m < R; ++m) {
-        const int x = lane + 32 * m;
-        if (2 * m < R && x < d.nx) v[m] = v[m] + cmul(T, wxs[jx * d.nx + x]);
-      }
+      for (int m = 0; m < R / 2; ++m)
+        if (FULL || lane + 32 * m < d.nx) v[m] = v[m] + cmul(T, wb[jx * d.nx + 32 * m]);
     }
 #pragma unroll
     for (int m = 0; m < R; ++m) {
       const int x = lane + 32 * m;
-      if (2 * m < R && x < d.nx) Jout[(size_t)row * d.nx + x] = v[m];
+      if (2 * m < R && (FULL || x < d.nx)) Jout[(size_t)row * d.nx + x] = v[m];
     }
     if (do_fft) {
       WarpFFT<PX>::forward(v, tw, lane);
@@ -290,8 +299,10 @@ pdf_status fp_configure() {
   cudaFuncSetAttribute(kf_synth_rowfft<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);  \
   cudaFuncSetAttribute(kf_colconv<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);       \
   cudaFuncSetAttribute(kf_colconv_pipe<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);  \
-  cudaFuncSetAttribute(kf_adj_ana_p<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);     \
-  cudaFuncSetAttribute(kf_synth_p<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);       \
+  cudaFuncSetAttribute(kf_adj_ana_p<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024); \
+  cudaFuncSetAttribute(kf_adj_ana_p<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024); \
+  cudaFuncSetAttribute(kf_synth_p<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);   \
+  cudaFuncSetAttribute(kf_synth_p<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);  \
   cudaFuncSetAttribute(kf_rowifft_state<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024); \
   cudaFuncSetAttribute(kf_adj_rowifft_ana<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024); \
   cudaFuncSetAttribute(kf_rowifft_sums<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
@@ -309,21 +320,25 @@ size_t fp_smem_ana(const Dev& d) { return (size_t)d.Px * sizeof(float2); }
 size_t fp_smem_sums(const Dev& d) { return (size_t)d.Px * sizeof(float2) + 3 * FW * (size_t)(d.Px / 2) * sizeof(float); }
 
 size_t fp_smem_ana_p(const Dev& d);
+size_t fp_smem_synth_p(const Dev& d);
 template <class K>
 static int persistent_slots(K kernel, size_t smem);
 
 pdf_status fp_synth_rowfft(const Dev& d, const float2* alpha, float2* Jout, int do_fft, cudaStream_t st) {
-  if (fp_smem_ana_p(d) <= 64 * 1024) {                 // same staging: twiddles + Wx
+  if (fp_smem_synth_p(d) <= 64 * 1024) {               // twiddles + Wx + the warps' T' lines
     const int nrows = d.ni * d.ny, nb = (nrows + FW - 1) / FW;
 #define L(P)                                                                                     \
   {                                                                                              \
     static size_t sm_ = 0;                                                                       \
     static int slots_ = 0;                                                                       \
-    if (sm_ != fp_smem_ana_p(d)) {                                                               \
-      sm_ = fp_smem_ana_p(d);                                                                    \
-      slots_ = persistent_slots(kf_synth_p<P>, sm_);                                             \
+    if (sm_ != fp_smem_synth_p(d)) {                                                             \
+      sm_ = fp_smem_synth_p(d);                                                                  \
+      slots_ = persistent_slots(kf_synth_p<P, true>, sm_);                                       \
     }                                                                                            \
-    kf_synth_p<P><<<std::min(nb, slots_), FT, sm_, st>>>(d, alpha, Jout, do_fft);                \
+    if (2 * d.nx == P)                                                                           \
+      kf_synth_p<P, true><<<std::min(nb, slots_), FT, sm_, st>>>(d, alpha, Jout, do_fft);        \
+    else                                                                                         \
+      kf_synth_p<P, false><<<std::min(nb, slots_), FT, sm_, st>>>(d, alpha, Jout, do_fft);       \
   }
     FAST_SWITCH(d.Px, L)
 #undef L
@@ -421,7 +436,8 @@ int fp_choose_nsg(const Dev& d, int sms) {
 
 // number of L_State partials written per loss-and-gradient evaluation on this path
 int fp_n_state(const Dev& d) { return d.nsg > 0 ? (int)(frow_grid(d).x * frow_grid(d).y) : d.ny; }
-size_t fp_smem_ana_p(const Dev& d) { return ((size_t)d.Px + (size_t)d.kx * d.nx) * sizeof(float2); }
+size_t fp_smem_ana_p(const Dev& d) { return ((size_t)d.Px + (size_t)((d.kx + 7) & ~7) * d.nx) * sizeof(float2); }
+size_t fp_smem_synth_p(const Dev& d) { return ((size_t)d.Px + (size_t)d.kx * d.nx + FW * 64) * sizeof(float2); }
 
 // resident CTAs of a persistent row kernel with `smem` bytes of dynamic shared memory
 template <class K>
@@ -443,9 +459,12 @@ pdf_status fp_adj_rowifft_ana(const Dev& d, const float2* in, int mode, cudaStre
     static int slots_ = 0;                                                                       \
     if (sm_ != fp_smem_ana_p(d)) {                                                               \
       sm_ = fp_smem_ana_p(d);                                                                    \
-      slots_ = persistent_slots(kf_adj_ana_p<P>, sm_);                                           \
+      slots_ = persistent_slots(kf_adj_ana_p<P, true>, sm_);                                     \
     }                                                                                            \
-    kf_adj_ana_p<P><<<std::min(nb, slots_), FT, sm_, st>>>(d, in, mode);                         \
+    if (2 * d.nx == P)                                                                           \
+      kf_adj_ana_p<P, true><<<std::min(nb, slots_), FT, sm_, st>>>(d, in, mode);                 \
+    else                                                                                         \
+      kf_adj_ana_p<P, false><<<std::min(nb, slots_), FT, sm_, st>>>(d, in, mode);                \
   }
     FAST_SWITCH(d.Px, L)
 #undef L

@@ -14,6 +14,8 @@
 //   k_gsh              2/||Esca||^2 G_S^H r_d
 //   k_adj_rowifft_ana  dL/dJ = v + G_D^H u + G_S^H term, then analysis along x
 //   k_ana_y            analysis along y -> dL/d alpha;  k_finalize sums the loss partials
+//   (with the folded data term and coefficients that fit, the data residual is k_gsf_fwd_p: a
+//   warp per receiver, alpha_p in shared memory, no separate reduction)
 //
 // FP32 arithmetic with compensated FP32 per-thread sums and FP64 cross-thread/cross-block
 // reductions (FP64 is a small fraction of FP32 throughput on this part, so it is kept out of
@@ -497,6 +499,54 @@ __global__ void __launch_bounds__(256) k_ana_y_sm(Dev d, const float2* __restric
   if (lane + 32 < kx) o[lane + 32] = a1;
 }
 
+// Data residual through the folded operator: CTA (p, block of 8 receivers), alpha_p in shared
+// memory, a warp per receiver (lanes split the coefficients, four independent partial sums, a
+// fixed-order warp sum), r_d[p][r] = sum_j gsf[r][j] alpha[p][j] - E_sca[p][r], and the CTA's
+// ||r_d||^2 (float-float, warp order) -> lp[p nrb + block].  Replaces k_gsf_fwd + k_gsf_reduce
+// where the partials fit (d.rdwarp).
+__global__ void __launch_bounds__(256) k_gsf_fwd_p(Dev d, const float2* __restrict__ alpha, float2* __restrict__ rd,
+                                                   FF* __restrict__ lp) {
+  extern __shared__ float2 sap[];
+  __shared__ FF wpart[8];
+  const int p = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int NA = d.ky * d.kx, r = blockIdx.y * 8 + warp;
+  for (int i = threadIdx.x; i < NA; i += blockDim.x) sap[i] = alpha[(size_t)p * NA + i];
+  __syncthreads();
+  FF part = FF{0.f, 0.f};
+  if (r < d.nr) {
+    const float2* gr = d.gsf + (size_t)r * NA;
+    float2 a[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    int j = lane;
+    for (; j + 96 < NA; j += 128)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a[q] = a[q] + cmul(__ldg(&gr[j + 32 * q]), sap[j + 32 * q]);
+    for (; j < NA; j += 32) a[0] = a[0] + cmul(__ldg(&gr[j]), sap[j]);
+    float2 acc = (a[0] + a[1]) + (a[2] + a[3]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc = acc + make_float2(__shfl_xor_sync(0xffffffffu, acc.x, o),
+                                                         __shfl_xor_sync(0xffffffffu, acc.y, o));
+    if (lane == 0) {
+      const size_t o = (size_t)p * d.nr + r;
+      const float2 v = acc - d.esca[o];
+      rd[o] = v;
+      part = ff_make(cabs2(v));
+    }
+  }
+  if (lane == 0) wpart[warp] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    FF t = FF{0.f, 0.f};
+    for (int w = 0; w < 8; ++w) t = ff_add(t, wpart[w]);
+    lp[(size_t)p * gridDim.y + blockIdx.y] = t;
+  }
+}
+
+// the per-receiver-block data residual kernel: folded data term, coefficients that fit in shared
+// memory, and one loss partial per (incidence, receiver block) within the partial buffer
+bool hp_rdwarp_ok(const Dev& d) {
+  return d.fold && d.ky * d.kx <= 4096 && (size_t)d.ni * ((d.nr + 7) / 8) <= PDF_LP_STRIDE;
+}
+
 static size_t sm_ana_y(const Dev& d) { return ((size_t)d.ny * d.kx + 8 * (size_t)d.ny) * sizeof(float2); }
 static bool ana_y_sm_ok(const Dev& d) { return d.kx <= 64 && sm_ana_y(d) <= 100 * 1024; }
 
@@ -537,6 +587,7 @@ pdf_status hp_configure_kernels() {
   cudaFuncSetAttribute(k_adj_rowfft, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_adj_rowifft_ana, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_ana_y_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  cudaFuncSetAttribute(k_gsf_fwd_p, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(e, "cudaFuncSetAttribute");
   return PDF_OK;
@@ -618,7 +669,10 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
     k_rowifft_state<<<d.ny, ROW_THREADS, sm_row(d), st>>>(d);
   }
   mark();
-  if (d.fold) {
+  if (d.rdwarp) {
+    k_gsf_fwd_p<<<dim3(d.ni, (d.nr + 7) / 8), 256, sizeof(float2) * d.ky * d.kx, st>>>(d, alpha, d.rd,
+                                                                                       d.lpart + LP_DATA * PDF_LP_STRIDE);
+  } else if (d.fold) {
     k_gsf_fwd<<<dim3((d.nr + 31) / 32, (d.ni + 7) / 8, gsf_nsplit(d)), 256, 0, st>>>(d, alpha, d.gspart, gsf_kc(d));
     k_gsf_reduce<<<n_data_blocks, 256, 0, st>>>(d, d.gspart, gsf_nsplit(d), d.esca, d.rd,
                                                  d.lpart + LP_DATA * PDF_LP_STRIDE);
@@ -682,11 +736,11 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
     mark();
   }
   if (!loop_eval) {
-    k_finalize<<<1, 1024, 0, st>>>(d, terms ? terms : h->terms, d.fast ? fp_n_state(d) : d.ny, n_data_blocks,
-                                  d.n_reg_blocks, step_inc);
+    k_finalize<<<1, 1024, 0, st>>>(d, terms ? terms : h->terms, d.fast ? fp_n_state(d) : d.ny,
+                                  d.rdwarp ? d.ni * ((d.nr + 7) / 8) : n_data_blocks, d.n_reg_blocks, step_inc);
     mark();
   }
-  pdf_count_launch((d.fold ? (tc ? 10 : 12) : (tc ? 7 : 12)) - (loop_eval ? 1 : 0));
+  pdf_count_launch((d.fold ? (tc ? 10 : 12) : (tc ? 7 : 12)) - (loop_eval ? 1 : 0) - (d.rdwarp ? 1 : 0));
   PDF_LAUNCHED("pdf_loss_grad");
   return PDF_OK;
 }

@@ -64,6 +64,7 @@ struct Dev {
   const float* invn;     // [2] 2 / ||E_inc||^2, 2 / ||E_sca||^2 (float)
   const float2* adam_tab;  // [cap] Adam step size lr / (1 - b1^t) and sqrt(1 - b2^t), t = 1..cap
   int gs_chunk;          // pixels per CTA of the SIMT G_S product
+  int rdwarp;             // 1: the data residual runs as k_gsf_fwd_p (a warp per receiver, no reduction)
 
   // CCO inside the loss (pdf_config.cco_in_loss): the regularisers act on chi_CCO (ccoloss.cu)
   int cco_loss;
@@ -184,6 +185,7 @@ pdf_status hp_check_limits(const Dev& d);
 pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, double* terms, cudaStream_t st,
                         int* step_inc = nullptr, cudaEvent_t* ev = nullptr);
 const char* hp_kernel_name(int k, int precision, int fold);
+bool hp_rdwarp_ok(const Dev& d);
 __global__ void k_ana_y(Dev d, const float2* T2, float2* out, int* step_inc);
 pdf_status hp_gd(pdf_problem* h, const float2* in, float2* out, int adjoint, cudaStream_t st);
 pdf_status hp_gs(pdf_problem* h, const float2* in, float2* out, const float2* subtract, FF* sumsq, cudaStream_t st);

@@ -166,13 +166,13 @@ def kernel_bytes(w):
 
 
 # the CUDA kernel behind each profiled stage of the register-FFT path at the bench's sizes
-KERNEL_OF_STAGE = {"k_colconv": "kf_colconv_pipe<P>", "k_synth_rowfft": "kf_synth_p<P>",
+KERNEL_OF_STAGE = {"k_colconv": "kf_colconv_2p<P/16>", "k_synth_rowfft": "kf_synth_p<P>",
                    "k_adj_rowifft_ana": "kf_adj_ana_p<P>", "k_rowifft_state": "kf_rowifft_sums<P> + k_state_combine",
                    "k_adj_rowfft": "kf_adj_rowfft<P>", "k_gsf_fwd": "k_gsf_fwd_p"}
 
 # DRAM bytes (read + write) per launch from one ncu capture, by (workload, stage); None until the
 # kernel has been captured in its current form (see profiles/)
-TRAFFIC_PER_LAUNCH = {("c5", "k_colconv"): 38997248 + 22784}      # kf_colconv_pipe<384>, profiles/ncu_c5_colconv_pipe.md
+TRAFFIC_PER_LAUNCH = {}
 
 
 def cluster_flops(w, fold=1):
@@ -376,7 +376,7 @@ def run_ours(args, rank, world, local):
                     "bytes_per_launch": kb[dom_name], "launch_ms": dom_ms,
                     "launches_per_iteration": len(agg[dom_name]),
                     "share_of_loss_grad": sum(agg[dom_name]) / per_iter_ms,
-                    "note": "algorithmic bytes per launch (DESIGN's per-kernel formula) / the mean CUDA-event "
+                    "note": "algorithmic bytes per launch (kernel_bytes, the per-kernel byte model) / the mean CUDA-event "
                             "duration of its launches inside one loss-and-gradient evaluation on the "
                             "launching stream; peak = the measured copy bandwidth; traffic = DRAM read + "
                             "write bytes per launch from one ncu capture of this kernel at this workload",

@@ -585,6 +585,7 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
   d.twy = twy;
   d.ghat = ghat;
   d.ghat_perm = nullptr;
+  d.ghat_col = nullptr;
   if (d.fast) {
     float2* gp;
     TRY(dalloc(h, &gp, (size_t)d.Px * d.Py));
@@ -593,6 +594,13 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
       return st;
     }
     d.ghat_perm = gp;
+    float2* gc;
+    TRY(dalloc(h, &gc, (size_t)d.Px * d.Py));
+    if ((st = fp_col_ghat(d, gc, s)) != PDF_OK) {
+      free_all(h);
+      return st;
+    }
+    d.ghat_col = gc;
   }
   d.what = nullptr;
   if (d.fast && d.Px <= 128) {                       // sizes the cluster loop can take
@@ -608,6 +616,16 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
   d.gs = gs;
   d.wx = wx;
   d.wy = wy;
+  d.ux = nullptr;
+  if (d.fast) {
+    float2* u;
+    TRY(dalloc(h, &u, (size_t)d.nx));
+    if ((st = fp_unit_table(d.nx, u, s)) != PDF_OK) {
+      free_all(h);
+      return st;
+    }
+    d.ux = u;
+  }
   d.esca = esca_d;
   d.norms = norms;
   cudaMemsetAsync(esca_d, 0, NI * NR * sizeof(float2), s);

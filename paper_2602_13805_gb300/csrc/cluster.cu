@@ -218,7 +218,7 @@ __device__ __forceinline__ void cl_cgemm(int M, int N, int K, const float2* __re
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = acc[i][j] + cmul(av[i], bv[j]);
+        for (int j = 0; j < TN; ++j) acc[i][j] = cmac(acc[i][j], av[i], bv[j]);
     }
 #pragma unroll
     for (int o = 1; o < KS; o <<= 1)
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     for (int t = CL_NW - 1 - warp; t < NRK; t += CL_NW) {               // r_d,p = (G_S Phi) alpha_p - E_sca,p, own receivers
       float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 4
-      for (int j = lane; j < NA; j += 32) acc = acc + cmul(gsf[t * NA + j], al[j]);
+      for (int j = lane; j < NA; j += 32) acc = cmac(acc, gsf[t * NA + j], al[j]);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc = acc + shfl_xor2(acc, o);
       if (lane == 0) rd[t] = acc - es[t];
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
       for (int i = threadIdx.x - 32; i < NA; i += CL_NT - 32) {            // (G_S Phi)^H r_d, own receivers (Eq. 16)
         float2 g = make_float2(0.f, 0.f);
 #pragma unroll 4
-        for (int t = 0; t < NRK; ++t) g = g + cmulc(rd[t], gsf[t * NA + i]);
+        for (int t = 0; t < NRK; ++t) g = cmacc(g, rd[t], gsf[t * NA + i]);
         gdv[i] = g;
       }
     });

@@ -40,6 +40,14 @@ __host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
 __host__ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
   return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
+// acc + a b and acc + a conj(b) as four FMAs: the accumulation is fused into the products (a plain
+// acc + cmul(a, b) costs two multiplies, two FMAs and two adds)
+__host__ __device__ __forceinline__ float2 cmac(float2 acc, float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
+}
+__host__ __device__ __forceinline__ float2 cmacc(float2 acc, float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x)), fmaf(a.y, b.x, fmaf(-a.x, b.y, acc.y)));
+}
 __host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 __host__ __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }

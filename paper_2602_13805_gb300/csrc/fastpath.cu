@@ -115,6 +115,133 @@ __global__ void __launch_bounds__(FT, (PY <= 384 ? 3 : 2)) kf_colconv_pipe(Dev d
 }
 
 // ---------------------------------------------------------------------------
+// Column convolution in two passes through shared memory, for P = 16 Q (Q = 8, 16, 24) and
+// ny <= P / 2.  With n = n1 + Q n2 and k = 16 k1 + k2 (n1, k1 < Q; n2, k2 < 16),
+//   X[16 k1 + k2] = sum_n1 W_Q^{n1 k1} W_P^{n1 k2} sum_n2 x[n1 + Q n2] W_16^{n2 k2}.
+// Pass A, one thread per (column, n1): the 16-point DFT over n2, of which only n2 < 8 can be
+// non-zero (the column is zero-padded from ny <= P/2 rows), as two 8-point DFTs, and the twiddle.
+// Pass B, one thread per (column, k2): the Q-point DFT over n1, the product with the G_D
+// spectrum (or its conjugate), and the inverse Q-point DFT.  Pass A^-1, one thread per (column,
+// n1): the conjugate twiddle, the inverse 16-point DFT evaluated only at the rows n2 < 8 that are
+// kept, and the store.  Lines stay in registers; the two exchanges go through a padded
+// [n1][column][k2] array in shared memory, so no cross-lane shuffles are needed.  Persistent CTAs
+// walk tiles of C2P_COLS columns of one incidence; the next tile's column data are copied with
+// cp.async during passes B and A^-1 of the current one, and the spectrum of the next tile's
+// columns during pass A^-1 (skipped when the columns are the same).
+// ---------------------------------------------------------------------------
+#define C2P_COLS 8
+template <int Q> struct Col2p {
+  static constexpr int P = 16 * Q;
+  static constexpr int NT = C2P_COLS * (Q > 16 ? Q : 16);   // threads per CTA
+  static constexpr int MINB = Q > 16 ? 3 : 4;
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+template <int Q, bool CONJ>
+__global__ void __launch_bounds__(Col2p<Q>::NT, Col2p<Q>::MINB) kf_colconv_2p(Dev d, int ntiles) {
+  constexpr int P = 16 * Q, NT = Col2p<Q>::NT, C = C2P_COLS, SL = 17;
+  extern __shared__ float2 sm[];
+  float2* twA = sm;                      // [16][Q]  W_P^{n1 k2} at k2 * Q + n1
+  float2* gsp = twA + 16 * Q;            // [C][P]   spectrum of the tile's columns, natural order
+  float2* S = gsp + C * P;               // [Q][C][SL]
+  float2* tile = S + Q * C * SL;         // [C][LS]  column data, rows < ny
+  const int LS = colpipe_ls(d.ny);
+  const int ngrp = d.Px / C;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 16 * Q; i += NT) {
+    const int k2 = i / Q, n1 = i - k2 * Q;
+    twA[i] = d.twy[n1 * k2];
+  }
+  auto issue_cols = [&](int t) {
+    const int p = t / ngrp, c0 = (t - p * ngrp) * C;
+    const float2* Ap = d.A + (size_t)p * d.ny * d.Px + c0;
+    for (int i = tid; i < C * d.ny; i += NT) {
+      const int y = i / C, c = i - y * C;
+      cp_async8(&tile[c * LS + y], &Ap[(size_t)y * d.Px + c]);
+    }
+  };
+  auto issue_spec = [&](int t) {
+    const float2* src = d.ghat_col + (size_t)(t % ngrp) * C * P;
+    for (int i = tid; i < C * P / 2; i += NT) cp_async16(&gsp[2 * i], &src[2 * i]);
+  };
+  int t = blockIdx.x;
+  if (t < ntiles) issue_cols(t);
+  cp_async_commit();
+  if (t < ntiles) issue_spec(t);
+  cp_async_commit();
+  for (; t < ntiles; t += gridDim.x) {
+    const int p = t / ngrp, c0 = (t - p * ngrp) * C;
+    const int tn = t + gridDim.x;
+    cp_async_wait<1>();                  // this tile's column data (the spectrum may still fly)
+    __syncthreads();
+    if (tid < C * Q) {                   // pass A
+      const int c = tid % C, n1 = tid / C;
+      float2 e[8], o[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int n = n1 + Q * j;
+        const float2 x = n < d.ny ? tile[c * LS + n] : make_float2(0.f, 0.f);
+        e[j] = x;
+        o[j] = j == 0 ? x : cmul(x, c_tw16[j]);
+      }
+      SmallDFT<8, false>::run(e);
+      SmallDFT<8, false>::run(o);
+      float2* s = S + (n1 * C + c) * SL;
+      s[0] = e[0];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (k > 0) s[2 * k] = cmul(e[k], twA[2 * k * Q + n1]);
+        s[2 * k + 1] = cmul(o[k], twA[(2 * k + 1) * Q + n1]);
+      }
+    }
+    cp_async_wait<0>();                  // the spectrum of this tile's columns
+    __syncthreads();
+    if (tn < ntiles) issue_cols(tn);
+    cp_async_commit();
+    if (tid < C * 16) {                  // pass B
+      const int k2 = tid & 15, c = tid >> 4;
+      float2* s = S + c * SL + k2;
+      float2 v[Q];
+#pragma unroll
+      for (int n1 = 0; n1 < Q; ++n1) v[n1] = s[n1 * C * SL];
+      SmallDFT<Q, false>::run(v);
+      const float2* g = gsp + c * P + k2;
+#pragma unroll
+      for (int k1 = 0; k1 < Q; ++k1) v[k1] = CONJ ? cmulc(v[k1], g[16 * k1]) : cmul(v[k1], g[16 * k1]);
+      SmallDFT<Q, true>::run(v);
+#pragma unroll
+      for (int n1 = 0; n1 < Q; ++n1) s[n1 * C * SL] = v[n1];
+    }
+    __syncthreads();
+    if (tn < ntiles && (tn % ngrp) != (t % ngrp)) issue_spec(tn);
+    cp_async_commit();
+    if (tid < C * Q) {                   // pass A^-1
+      const int c = tid % C, n1 = tid / C;
+      const float2* s = S + (n1 * C + c) * SL;
+      float2 e[8], o[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {              // conjugate twiddle W_P^{-n1 k2}, k2 = 2k, 2k + 1
+        e[k] = k == 0 ? s[0] : cmul(s[2 * k], cconj(twA[2 * k * Q + n1]));
+        o[k] = cmul(s[2 * k + 1], cconj(twA[(2 * k + 1) * Q + n1]));
+      }
+      SmallDFT<8, true>::run(e);
+      SmallDFT<8, true>::run(o);
+      float2* Ap = d.A + (size_t)p * d.ny * d.Px + c0 + c;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int n = n1 + Q * j;
+        if (n < d.ny) Ap[(size_t)n * d.Px] = e[j] + (j == 0 ? o[0] : cmul(o[j], cconj(c_tw16[j])));
+      }
+    }
+  }
+  cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
 // Adjoint row IFFT + x-analysis, persistent: each CTA stages the twiddles and the x basis
 // Wx [kx][nx] in shared memory once and its warps then walk rows (p, y) independently: inverse
 // row DFT of dL/dJ's row spectrum, + v (+ the G_S^H term when unfolded), and
@@ -186,7 +313,7 @@ __global__ void __launch_bounds__(FT, 3) kf_adj_ana_p(Dev d, const float2* in, i
       for (int m = 0; m < R / 2; ++m) {
         if (FULL || lane + 32 * m < d.nx) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) acc[j] = acc[j] + cmulc(g[m], wb[j * d.nx + 32 * m]);
+          for (int j = 0; j < 8; ++j) acc[j] = cmacc(acc[j], g[m], wb[j * d.nx + 32 * m]);
         }
       }
       warp_reduce_scatter8(acc, lane);
@@ -224,8 +351,8 @@ __global__ void __launch_bounds__(FT, 3) kf_synth_p(Dev d, const float2* __restr
     float2 t0 = make_float2(0.f, 0.f), t1 = make_float2(0.f, 0.f);
     for (int jy = 0; jy < d.ky; ++jy) {
       const float2 w = __ldg(&d.wy[jy * d.ny + y]);
-      if (lane < d.kx) t0 = t0 + cmul(w, __ldg(&ap[jy * d.kx + lane]));
-      if (lane + 32 < d.kx) t1 = t1 + cmul(w, __ldg(&ap[jy * d.kx + lane + 32]));
+      if (lane < d.kx) t0 = cmac(t0, w, __ldg(&ap[jy * d.kx + lane]));
+      if (lane + 32 < d.kx) t1 = cmac(t1, w, __ldg(&ap[jy * d.kx + lane + 32]));
     }
     __syncwarp();
     tr[lane] = t0;
@@ -240,7 +367,7 @@ __global__ void __launch_bounds__(FT, 3) kf_synth_p(Dev d, const float2* __restr
       const float2 T = tr[jx];
 #pragma unroll
       for (int m = 0; m < R / 2; ++m)
-        if (FULL || lane + 32 * m < d.nx) v[m] = v[m] + cmul(T, wb[jx * d.nx + 32 * m]);
+        if (FULL || lane + 32 * m < d.nx) v[m] = cmac(v[m], T, wb[jx * d.nx + 32 * m]);
     }
 #pragma unroll
     for (int m = 0; m < R; ++m) {
@@ -253,6 +380,295 @@ __global__ void __launch_bounds__(FT, 3) kf_synth_p(Dev d, const float2* __restr
       for (int k = 0; k < R; ++k) d.A[(size_t)row * PX + k * 32 + lane] = v[k];
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Synthesis (Eq. 9) and padded row DFT by tiles of 8 rows of one incidence, for P = Px = 16 Q
+// (Q = 8, 16, 24) and nx <= P / 2.  Per tile: T'[r][jx] = sum_jy Wy[jy][y0 + r] alpha_p[jy][jx]
+// (alpha_p and the tile's Wy entries staged in shared memory by cp.async one tile ahead); the J
+// rows J[r][x] = sum_jx T'[r][jx] Wx[jx][x], one thread per x accumulating all 8 rows; then the
+// row DFT in two passes through shared memory as in kf_colconv_2p (16-point DFTs over n2 from
+// the nx <= P/2 non-zero points, twiddle, Q-point DFTs over n1).  The spectra are staged in the
+// register FFT's digit-reversed order (position (f mod R) 32 + brev5(f / R) holds frequency f,
+// R = P / 32; rows padded to 33 per 32) and stored as whole rows, so the row-spectrum plane A
+// keeps the layout the other kernels read.
+// ---------------------------------------------------------------------------
+#define S2P_ROWS 8
+template <int Q>
+__global__ void __launch_bounds__(Col2p<Q>::NT, Col2p<Q>::MINB)
+    kf_synth_2p(Dev d, const float2* __restrict__ alpha, float2* __restrict__ Jout, int do_fft, int ntiles) {
+  constexpr int P = 16 * Q, NT = Col2p<Q>::NT, C = S2P_ROWS, SL = 17, R = P / 32, YS = R * 33;
+  extern __shared__ float2 sm[];
+  const int NA = d.ky * d.kx;
+  const int LS = colpipe_ls(d.nx);
+  float2* twA = sm;                        // [16][Q]  W_P^{n1 k2} at k2 * Q + n1
+  float2* as = twA + 16 * Q;               // [na2]    alpha of the tile's incidence
+  float2* wys = as + ((NA + 1) & ~1);      // [ky][C]  Wy entries of the tile's rows
+  float2* ts = wys + d.ky * C;             // [kx][C]  T'
+  float2* xt = ts + d.kx * C;              // [C][LS]  J rows (pass A input), then the staged spectra [C][YS]
+  float2* S = xt + (C * LS > C * YS ? C * LS : C * YS);   // [Q][C][SL] exchange array
+  float2* ux = S + Q * C * SL;             // [nx] exp(2 pi i m / nx) / sqrt(nx): Wx[jx][x] = ux[f_jx x mod nx]
+  int* posf = reinterpret_cast<int*>(ux + d.nx);          // [P] staging position of frequency f
+  const int tid = threadIdx.x;
+  const int tpi = (d.ny + C - 1) / C;      // tiles per incidence
+  const int hx = (d.kx + 1) / 2;           // modes jx < hx have frequency jx, the others nx - kx + jx
+  for (int i = tid; i < 16 * Q; i += NT) {
+    const int k2 = i / Q, n1 = i - k2 * Q;
+    twA[i] = d.twx[n1 * k2];
+  }
+  for (int f = tid; f < P; f += NT) posf[f] = (f % R) * 33 + brev5(f / R);
+  for (int m = tid; m < d.nx; m += NT) ux[m] = d.ux[m];
+  auto issue = [&](int t) {
+    const int p = t / tpi, y0 = (t - p * tpi) * C;
+    const float2* ap = alpha + (size_t)p * NA;
+    for (int i = tid; i < NA; i += NT) cp_async8(&as[i], &ap[i]);
+    for (int i = tid; i < d.ky * C; i += NT) {
+      const int jy = i / C, r = i - jy * C;
+      if (y0 + r < d.ny) cp_async8(&wys[i], &d.wy[(size_t)jy * d.ny + y0 + r]);
+      else wys[i] = make_float2(0.f, 0.f);
+    }
+  };
+  int t = blockIdx.x;
+  if (t < ntiles) issue(t);
+  cp_async_commit();
+  for (; t < ntiles; t += gridDim.x) {
+    const int p = t / tpi, y0 = (t - p * tpi) * C;
+    cp_async_wait<0>();
+    __syncthreads();
+    for (int i = tid; i < d.kx * C; i += NT) {   // T' = Wy^T alpha_p on the tile's rows
+      const int r = i / d.kx, jx = i - r * d.kx;
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 4
+      for (int jy = 0; jy < d.ky; ++jy) acc = cmac(acc, wys[jy * C + r], as[jy * d.kx + jx]);
+      ts[jx * C + r] = acc;
+    }
+    __syncthreads();
+    if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x);   // alpha and Wy are free until the next tile
+    cp_async_commit();
+    if (tid < d.nx) {                      // J rows: thread x, all C rows
+      const int x = tid;
+      float2 acc[C];
+#pragma unroll
+      for (int r = 0; r < C; ++r) acc[r] = make_float2(0.f, 0.f);
+      int m = 0;                           // f_jx x mod nx, stepped by x as f_jx steps by 1
+#pragma unroll 2
+      for (int jx = 0; jx < d.kx; ++jx) {
+        if (jx == hx) m = (int)(((long)(d.nx - d.kx + hx) * x) % d.nx);
+        const float2 w = ux[m];
+        m += x;
+        if (m >= d.nx) m -= d.nx;
+        const float4* tp = reinterpret_cast<const float4*>(ts + jx * C);
+#pragma unroll
+        for (int h = 0; h < C / 2; ++h) {
+          const float4 tt = tp[h];
+          acc[2 * h] = cmac(acc[2 * h], make_float2(tt.x, tt.y), w);
+          acc[2 * h + 1] = cmac(acc[2 * h + 1], make_float2(tt.z, tt.w), w);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < C; ++r) {
+        if (y0 + r < d.ny) Jout[((size_t)p * d.ny + y0 + r) * d.nx + x] = acc[r];
+        xt[r * LS + x] = acc[r];
+      }
+    }
+    if (!do_fft) continue;
+    __syncthreads();
+    if (tid < C * Q) {                     // pass A: 16-point DFTs over n2 (n2 < 8 non-zero), twiddle
+      const int r = tid % C, n1 = tid / C;
+      float2 e[8], o[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int n = n1 + Q * j;
+        const float2 x = n < d.nx ? xt[r * LS + n] : make_float2(0.f, 0.f);
+        e[j] = x;
+        o[j] = j == 0 ? x : cmul(x, c_tw16[j]);
+      }
+      SmallDFT<8, false>::run(e);
+      SmallDFT<8, false>::run(o);
+      float2* s = S + (n1 * C + r) * SL;
+      s[0] = e[0];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (k > 0) s[2 * k] = cmul(e[k], twA[2 * k * Q + n1]);
+        s[2 * k + 1] = cmul(o[k], twA[(2 * k + 1) * Q + n1]);
+      }
+    }
+    __syncthreads();
+    if (tid < C * 16) {                    // pass B: Q-point DFTs over n1, staged in storage order
+      const int k2 = tid & 15, rb = tid >> 4;
+      float2 v[Q];
+#pragma unroll
+      for (int n1 = 0; n1 < Q; ++n1) v[n1] = S[(n1 * C + rb) * SL + k2];
+      SmallDFT<Q, false>::run(v);
+      float2* yr = xt + rb * YS;
+#pragma unroll
+      for (int k1 = 0; k1 < Q; ++k1) yr[posf[16 * k1 + k2]] = v[k1];
+    }
+    __syncthreads();
+    const int nr = min(C, d.ny - y0);
+    float2* Ar = d.A + ((size_t)p * d.ny + y0) * P;
+    for (int c = tid; c < P; c += NT) {
+      const float2* yc = xt + (c >> 5) * 33 + (c & 31);
+      for (int r = 0; r < nr; ++r) Ar[(size_t)r * P + c] = yc[r * YS];
+    }
+  }
+  cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint row IFFT + x-analysis by tiles of 8 rows of one incidence (the tiled counterpart of
+// kf_adj_ana_p; P = Px = 16 Q, nx <= P / 2).  The tile's row spectra are copied (cp.async, one
+// tile ahead) into the staging layout of kf_synth_2p; pass B^-1, one thread per (row, k2), takes
+// the inverse Q-point DFTs over k1; pass A^-1, one thread per (row, n1), the conjugate twiddle and
+// the inverse 16-point DFT evaluated at the columns n2 < 8, then adds v (and the unfolded data
+// term's G_S^H r_d): the rows g of dL/dJ (mode 0), or the rows of `in` (mode 1).  The x-analysis
+// T2[r][jx] = sum_x g[r][x] conj(Wx[jx][x]) runs with lanes over jx, warps over chunks of x, all 8
+// rows per thread (the rows of g broadcast from shared memory), then a fixed-order sum over the
+// chunks; Wx[jx][x] = u[f_jx x mod nx] is read from the nx-entry table u in shared memory.
+// ---------------------------------------------------------------------------
+#define YPAD 34        // staged spectrum rows: 32 positions + 2 pad (16-byte aligned pairs)
+template <int Q>
+__global__ void __launch_bounds__(Col2p<Q>::NT, Col2p<Q>::MINB)
+    kf_adj_ana_2p(Dev d, const float2* __restrict__ in, int mode, int ntiles) {
+  constexpr int P = 16 * Q, NT = Col2p<Q>::NT, C = S2P_ROWS, SL = 17, R = P / 32, YS = R * YPAD;
+  constexpr int NCH = NT / 32;             // x chunks of the analysis
+  extern __shared__ float2 sm[];
+  float2* twA = sm;                        // [16][Q]
+  float2* ys = twA + 16 * Q;               // [C][YS]  staged row spectra
+  float2* S = ys + C * YS;                 // [Q][C][SL] exchange array, then the analysis partials
+  float2* G = S + Q * C * SL;              // [nx][C]  rows of g by column
+  float2* ux = G + d.nx * C;               // [nx] exp(2 pi i m / nx) / sqrt(nx): Wx[jx][x] = ux[f_jx x mod nx]
+  int* posf = reinterpret_cast<int*>(ux + d.nx);      // [P]
+  const int tid = threadIdx.x;
+  const int tpi = (d.ny + C - 1) / C;
+  for (int i = tid; i < 16 * Q; i += NT) {
+    const int k2 = i / Q, n1 = i - k2 * Q;
+    twA[i] = d.twx[n1 * k2];
+  }
+  for (int f = tid; f < P; f += NT) posf[f] = (f % R) * YPAD + brev5(f / R);
+  for (int m = tid; m < d.nx; m += NT) ux[m] = d.ux[m];
+  auto issue = [&](int t) {
+    const int p = t / tpi, y0 = (t - p * tpi) * C;
+    const int nr = min(C, d.ny - y0);
+    const float2* Ar = d.A + ((size_t)p * d.ny + y0) * P;
+    for (int i = tid; i < nr * (P / 2); i += NT) {
+      const int r = i / (P / 2), c = 2 * (i - r * (P / 2));
+      cp_async16(&ys[r * YS + (c >> 5) * YPAD + (c & 31)], &Ar[(size_t)r * P + c]);
+    }
+  };
+  const int xc = (d.nx + NCH - 1) / NCH;   // columns per analysis chunk
+  int t = blockIdx.x;
+  if (mode == 0 && t < ntiles) issue(t);
+  cp_async_commit();
+  for (; t < ntiles; t += gridDim.x) {
+    const int p = t / tpi, y0 = (t - p * tpi) * C;
+    const size_t rowbase = (size_t)p * d.ny + y0;
+    cp_async_wait<0>();
+    __syncthreads();
+    if (mode == 0) {
+      if (tid < C * 16) {                  // pass B^-1: inverse Q-point DFTs over k1
+        const int k2 = tid & 15, rb = tid >> 4;
+        const float2* yr = ys + rb * YS;
+        float2 v[Q];
+#pragma unroll
+        for (int k1 = 0; k1 < Q; ++k1) v[k1] = yr[posf[16 * k1 + k2]];
+        SmallDFT<Q, true>::run(v);
+#pragma unroll
+        for (int n1 = 0; n1 < Q; ++n1) S[(n1 * C + rb) * SL + k2] = v[n1];
+      }
+      __syncthreads();
+      if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
+      cp_async_commit();
+      if (tid < C * Q) {                   // pass A^-1: twiddle, inverse 16-point DFTs, + v
+        const int r = tid % C, n1 = tid / C;
+        const bool live = y0 + r < d.ny;
+        const size_t pix = (rowbase + r) * d.nx;
+        float2 vp[8];                      // v (+ G_S^H r_d) at this thread's columns, loaded ahead
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int x = n1 + Q * j;
+          vp[j] = make_float2(0.f, 0.f);
+          if (live && x < d.nx) vp[j] = d.fold ? d.v[pix + x] : d.v[pix + x] + d.gsh[pix + x];
+        }
+        const float2* s = S + (n1 * C + r) * SL;
+        float2 e[8], o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          e[k] = k == 0 ? s[0] : cmul(s[2 * k], cconj(twA[2 * k * Q + n1]));
+          o[k] = cmul(s[2 * k + 1], cconj(twA[(2 * k + 1) * Q + n1]));
+        }
+        SmallDFT<8, true>::run(e);
+        SmallDFT<8, true>::run(o);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int x = n1 + Q * j;
+          if (x < d.nx) {
+            const float2 g = e[j] + (j == 0 ? o[0] : cmul(o[j], cconj(c_tw16[j])));
+            G[x * C + r] = live ? g + vp[j] : make_float2(0.f, 0.f);
+          }
+        }
+      }
+    } else {
+      for (int i = tid; i < C * d.nx; i += NT) {
+        const int r = i / d.nx, x = i - r * d.nx;
+        G[x * C + r] = y0 + r < d.ny ? in[(rowbase + r) * d.nx + x] : make_float2(0.f, 0.f);
+      }
+    }
+    __syncthreads();
+    {                                      // x-analysis partials over chunk `ch`
+      const int jx = tid & 31, ch = tid >> 5;
+      float2 acc[C];
+#pragma unroll
+      for (int r = 0; r < C; ++r) acc[r] = make_float2(0.f, 0.f);
+      if (jx < d.kx) {
+        const int x0 = ch * xc, xe = min(d.nx, x0 + xc);
+        const int f = jx < (d.kx + 1) / 2 ? jx : d.nx - d.kx + jx;
+        int m = (int)(((long)f * x0) % d.nx);   // f x mod nx, stepped by f as x steps by 1
+#pragma unroll 2
+        for (int x = x0; x < xe; ++x) {
+          const float2 w = ux[m];
+          m += f;
+          if (m >= d.nx) m -= d.nx;
+          const float4* gp = reinterpret_cast<const float4*>(G + x * C);
+#pragma unroll
+          for (int h = 0; h < C / 2; ++h) {
+            const float4 gg = gp[h];
+            acc[2 * h] = cmacc(acc[2 * h], make_float2(gg.x, gg.y), w);
+            acc[2 * h + 1] = cmacc(acc[2 * h + 1], make_float2(gg.z, gg.w), w);
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < C; ++r) S[(ch * C + r) * 32 + jx] = acc[r];
+    }
+    __syncthreads();
+    for (int i = tid; i < C * d.kx; i += NT) {
+      const int r = i / d.kx, jx = i - r * d.kx;
+      if (y0 + r < d.ny) {
+        float2 a = S[r * 32 + jx];
+        for (int ch = 1; ch < NCH; ++ch) a = a + S[(ch * C + r) * 32 + jx];
+        d.T2[(rowbase + r) * d.kx + jx] = a;
+      }
+    }
+  }
+  cp_async_wait<0>();
+}
+
+// u[m] = exp(+2 pi i m / n) / sqrt(n), assembled exactly as the synthesis tables (FP64, the same
+// reduced numerator), so that Wx[jx][x] = u[f_jx x mod nx] holds bit for bit
+__global__ void k_unit_table(float2* __restrict__ u, int n) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n) return;
+  double s, c;
+  sincospi(2.0 * (double)m / (double)n, &s, &c);
+  const double sc = 1.0 / sqrt((double)n);
+  u[m] = make_float2((float)(c * sc), (float)(s * sc));
+}
+pdf_status fp_unit_table(int n, float2* u, cudaStream_t st) {
+  k_unit_table<<<(n + 127) / 128, 128, 0, st>>>(u, n);
+  pdf_count_launch(1);
+  PDF_LAUNCHED("unit-circle table of the x basis");
+  return PDF_OK;
 }
 
 template <int PX>
@@ -308,6 +724,17 @@ pdf_status fp_configure() {
   cudaFuncSetAttribute(kf_rowifft_sums<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
   CFG(64) CFG(128) CFG(256) CFG(384) CFG(512)
 #undef CFG
+#define CFG2(Q)                                                                                        \
+  cudaFuncSetAttribute(kf_colconv_2p<Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024); \
+  cudaFuncSetAttribute(kf_colconv_2p<Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  CFG2(8) CFG2(16) CFG2(24)
+#undef CFG2
+  cudaFuncSetAttribute(kf_synth_2p<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  cudaFuncSetAttribute(kf_synth_2p<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  cudaFuncSetAttribute(kf_synth_2p<24>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  cudaFuncSetAttribute(kf_adj_ana_2p<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  cudaFuncSetAttribute(kf_adj_ana_2p<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  cudaFuncSetAttribute(kf_adj_ana_2p<24>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(e, "cudaFuncSetAttribute(register FFT)");
   return PDF_OK;
@@ -324,7 +751,50 @@ size_t fp_smem_synth_p(const Dev& d);
 template <class K>
 static int persistent_slots(K kernel, size_t smem);
 
+size_t fp_smem_synth2p(const Dev& d) {
+  const int Q = d.Px / 16, NA = d.ky * d.kx;
+  const size_t stage = std::max((size_t)colpipe_ls(d.nx), (size_t)(d.Px / 32) * 33) * S2P_ROWS;
+  return ((size_t)16 * Q + (size_t)((NA + 1) & ~1) + (size_t)d.ky * S2P_ROWS + (size_t)d.kx * S2P_ROWS + stage +
+          (size_t)Q * S2P_ROWS * 17 + d.nx) *
+             sizeof(float2) +
+         (size_t)d.Px * sizeof(int);
+}
+// the tiled synthesis covers Px = 128, 256, 384 with nx <= Px / 2, kx <= 32
+static bool synth2p_ok(const Dev& d) {
+  return (d.Px == 128 || d.Px == 256 || d.Px == 384) && 2 * d.nx <= d.Px && d.kx <= 32 && d.ux &&
+         fp_smem_synth2p(d) <= 96 * 1024;
+}
+template <int Q>
+static int synth2p_slots(const Dev& d) {
+  static size_t smem = 0;
+  static int slots = 0;
+  const size_t need = fp_smem_synth2p(d);
+  if (need != smem) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kf_synth_2p<Q>, Col2p<Q>::NT, need);
+    cudaGetLastError();
+    slots = std::max(1, sms * std::max(1, occ));
+    smem = need;
+  }
+  return slots;
+}
+
 pdf_status fp_synth_rowfft(const Dev& d, const float2* alpha, float2* Jout, int do_fft, cudaStream_t st) {
+  if (synth2p_ok(d)) {
+    const int ntiles = d.ni * ((d.ny + S2P_ROWS - 1) / S2P_ROWS);
+#define L(Q)                                                                                     \
+  kf_synth_2p<Q><<<std::min(ntiles, synth2p_slots<Q>(d)), Col2p<Q>::NT, fp_smem_synth2p(d), st>>>( \
+      d, alpha, Jout, do_fft, ntiles)
+    switch (d.Px / 16) {
+      case 8: L(8); break;
+      case 16: L(16); break;
+      default: L(24); break;
+    }
+#undef L
+    return PDF_OK;
+  }
   if (fp_smem_synth_p(d) <= 64 * 1024) {               // twiddles + Wx + the warps' T' lines
     const int nrows = d.ni * d.ny, nb = (nrows + FW - 1) / FW;
 #define L(P)                                                                                     \
@@ -382,7 +852,51 @@ static int colpipe_slots(const Dev& d) {
   return slots;
 }
 
+size_t fp_smem_col2p(const Dev& d) {
+  const int Q = d.Py / 16;
+  return ((size_t)16 * Q + (size_t)C2P_COLS * d.Py + (size_t)Q * C2P_COLS * 17 + (size_t)C2P_COLS * colpipe_ls(d.ny)) *
+         sizeof(float2);
+}
+// the two-pass column convolution covers P = 128, 256, 384 with ny <= P / 2
+static bool col2p_ok(const Dev& d) {
+  return (d.Py == 128 || d.Py == 256 || d.Py == 384) && 2 * d.ny <= d.Py && d.Px % C2P_COLS == 0 && d.ghat_col;
+}
+template <int Q>
+static int col2p_slots(const Dev& d) {
+  static size_t smem = 0;
+  static int slots = 0;
+  const size_t need = fp_smem_col2p(d);
+  if (need != smem) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kf_colconv_2p<Q, false>, Col2p<Q>::NT, need);
+    cudaGetLastError();
+    slots = std::max(1, sms * std::max(1, occ));
+    smem = need;
+  }
+  return slots;
+}
+
 pdf_status fp_colconv(const Dev& d, int conj, cudaStream_t st) {
+  if (col2p_ok(d)) {
+    const int ntiles = d.ni * (d.Px / C2P_COLS);
+#define L(Q)                                                                                              \
+  {                                                                                                       \
+    const int g_ = std::min(ntiles, col2p_slots<Q>(d));                                                   \
+    if (conj)                                                                                             \
+      kf_colconv_2p<Q, true><<<g_, Col2p<Q>::NT, fp_smem_col2p(d), st>>>(d, ntiles);                      \
+    else                                                                                                  \
+      kf_colconv_2p<Q, false><<<g_, Col2p<Q>::NT, fp_smem_col2p(d), st>>>(d, ntiles);                     \
+  }
+    switch (d.Py / 16) {
+      case 8: L(8); break;
+      case 16: L(16); break;
+      default: L(24); break;
+    }
+#undef L
+    return PDF_OK;
+  }
   if (d.Px % PCOLS == 0) {
     const int ntiles = d.ni * (d.Px / PCOLS);
 #define L(P) kf_colconv_pipe<P><<<std::min(ntiles, colpipe_slots<P>(d)), FT, fp_smem_colpipe(d), st>>>(d, conj, ntiles)
@@ -450,7 +964,51 @@ static int persistent_slots(K kernel, size_t smem) {
   return std::max(1, sms * std::max(1, occ));
 }
 
+size_t fp_smem_ana2p(const Dev& d) {
+  const int Q = d.Px / 16;
+  return ((size_t)16 * Q + (size_t)S2P_ROWS * (d.Px / 32) * YPAD + (size_t)Q * S2P_ROWS * 17 +
+          (size_t)d.nx * S2P_ROWS + d.nx) *
+             sizeof(float2) +
+         (size_t)d.Px * sizeof(int);
+}
+// the tiled adjoint analysis covers Px = 128, 256 (384 compiles too) with nx <= Px / 2 and kx <= 32
+// (the chunk partials, NT / 32 chunks x 8 rows x 32, fit the exchange array); at Px = 384 the
+// warp-per-row kf_adj_ana_p measured faster (38.9 against 45 us a launch at c5), at Px = 256 the
+// tiles (14.3 against 15.2 us at c3)
+static bool ana2p_ok(const Dev& d) {
+  return (d.Px == 128 || d.Px == 256) && 2 * d.nx <= d.Px && d.kx <= 32 && d.ux && fp_smem_ana2p(d) <= 96 * 1024;
+}
+template <int Q>
+static int ana2p_slots(const Dev& d) {
+  static size_t smem = 0;
+  static int slots = 0;
+  const size_t need = fp_smem_ana2p(d);
+  if (need != smem) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kf_adj_ana_2p<Q>, Col2p<Q>::NT, need);
+    cudaGetLastError();
+    slots = std::max(1, sms * std::max(1, occ));
+    smem = need;
+  }
+  return slots;
+}
+
 pdf_status fp_adj_rowifft_ana(const Dev& d, const float2* in, int mode, cudaStream_t st) {
+  if (ana2p_ok(d)) {
+    const int ntiles = d.ni * ((d.ny + S2P_ROWS - 1) / S2P_ROWS);
+#define L(Q)                                                                                          \
+  kf_adj_ana_2p<Q><<<std::min(ntiles, ana2p_slots<Q>(d)), Col2p<Q>::NT, fp_smem_ana2p(d), st>>>(d, in, mode, \
+                                                                                                  ntiles)
+    switch (d.Px / 16) {
+      case 8: L(8); break;
+      case 16: L(16); break;
+      default: L(24); break;
+    }
+#undef L
+    return PDF_OK;
+  }
   if (fp_smem_ana_p(d) <= 64 * 1024) {
     const int nrows = d.ni * d.ny, nb = (nrows + FW - 1) / FW;
 #define L(P)                                                                                     \
@@ -511,6 +1069,21 @@ pdf_status fp_row_dft_table(const Dev& d, float2* what, cudaStream_t st) {
   k_row_dft_table<<<dim3((d.Px + 127) / 128, d.kx), 128, 0, st>>>(what, d.kx, d.nx, d.Px);
   pdf_count_launch(1);
   PDF_LAUNCHED("row DFT table of the x basis");
+  return PDF_OK;
+}
+
+// spectrum by column, natural frequency order: gc[cx][ky] = ghat[ky][kx(cx)]
+__global__ void k_col_ghat(const float2* __restrict__ ghat, float2* __restrict__ gc, int Px, int Py) {
+  const int ky = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cx = blockIdx.y;
+  if (ky >= Py) return;
+  gc[(size_t)cx * Py + ky] = ghat[(size_t)ky * Px + perm_to_freq(cx, Px / 32)];
+}
+
+pdf_status fp_col_ghat(const Dev& d, float2* gc, cudaStream_t st) {
+  k_col_ghat<<<dim3((d.Py + 127) / 128, d.Px), 128, 0, st>>>(d.ghat, gc, d.Px, d.Py);
+  pdf_count_launch(1);
+  PDF_LAUNCHED("spectrum by column");
   return PDF_OK;
 }
 

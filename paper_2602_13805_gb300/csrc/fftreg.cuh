@@ -32,9 +32,20 @@ static __constant__ float2 c_tw16[16] = {{1.000000000f, 0.000000000f},  {0.92387
                                          {0.000000000f, 1.000000000f},  {0.382683432f, 0.923879533f},
                                          {0.707106781f, 0.707106781f},  {0.923879533f, 0.382683432f}};
 
+// W_24^e (cos 15 e degrees, -sin 15 e degrees)
+static __constant__ float2 c_tw24[24] = {
+    {1.000000000f, 0.000000000f},   {0.965925826f, -0.258819045f},  {0.866025404f, -0.500000000f},
+    {0.707106781f, -0.707106781f},  {0.500000000f, -0.866025404f},  {0.258819045f, -0.965925826f},
+    {0.000000000f, -1.000000000f},  {-0.258819045f, -0.965925826f}, {-0.500000000f, -0.866025404f},
+    {-0.707106781f, -0.707106781f}, {-0.866025404f, -0.500000000f}, {-0.965925826f, -0.258819045f},
+    {-1.000000000f, 0.000000000f},  {-0.965925826f, 0.258819045f},  {-0.866025404f, 0.500000000f},
+    {-0.707106781f, 0.707106781f},  {-0.500000000f, 0.866025404f},  {-0.258819045f, 0.965925826f},
+    {0.000000000f, 1.000000000f},   {0.258819045f, 0.965925826f},   {0.500000000f, 0.866025404f},
+    {0.707106781f, 0.707106781f},   {0.866025404f, 0.500000000f},   {0.965925826f, 0.258819045f}};
+
 template <int R>
 __device__ __forceinline__ float2 tw_small(int e) {
-  return R == 8 ? c_tw8[e] : (R == 12 ? c_tw12[e] : c_tw16[e]);
+  return R == 8 ? c_tw8[e] : (R == 12 ? c_tw12[e] : (R == 16 ? c_tw16[e] : c_tw24[e]));
 }
 
 // R = 4 Q points, m = Q a + b:  X[k1 + 4 k2] = DFT_Q over b of ( W_R^{b k1} DFT_4 over a of x[Q a + b] )
@@ -83,6 +94,37 @@ template <bool INV> struct SmallDFT<12, INV> {
 };
 template <bool INV> struct SmallDFT<16, INV> {
   static __device__ __forceinline__ void run(float2* v) { dft_4xq<4, INV>(v); }
+};
+
+// R = 8 * 3 points, m = 3 a + b:  X[k1 + 8 k2] = DFT_3 over b of ( W_24^{b k1} DFT_8 over a of x[3 a + b] )
+template <bool INV> struct SmallDFT<24, INV> {
+  static __device__ __forceinline__ void run(float2* v) {
+    float2 F[3][8];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      float2 t[8];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) t[a] = v[3 * a + b];
+      dft_4xq<2, INV>(t);
+#pragma unroll
+      for (int k1 = 0; k1 < 8; ++k1) {
+        if (b * k1 == 0) {
+          F[b][k1] = t[k1];
+        } else {
+          float2 w = tw_small<24>(b * k1);
+          if (INV) w.y = -w.y;
+          F[b][k1] = cmul(t[k1], w);
+        }
+      }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) {
+      float2 t[3] = {F[0][k1], F[1][k1], F[2][k1]};
+      Butterfly<float2, 3>::run(t, INV);
+#pragma unroll
+      for (int k2 = 0; k2 < 3; ++k2) v[k1 + 8 * k2] = t[k2];
+    }
+  }
 };
 
 __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {

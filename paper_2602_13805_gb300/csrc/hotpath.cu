@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_synth_rowfft(Dev d, const float
     float2 acc = make_float2(0.f, 0.f);
     if (rr < nrow) {
       const int y = y0 + rr;
-      for (int jy = 0; jy < ky; ++jy) acc = acc + cmul(__ldg(&d.wy[jy * d.ny + y]), sa[jy * kx + jx]);
+      for (int jy = 0; jy < ky; ++jy) acc = cmac(acc, __ldg(&d.wy[jy * d.ny + y]), sa[jy * kx + jx]);
     }
     ty[i] = acc;
   }
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_synth_rowfft(Dev d, const float
     const int rr = i / d.Px, x = i - rr * d.Px;
     float2 v = make_float2(0.f, 0.f);
     if (rr < nrow && x < d.nx) {
-      for (int jx = 0; jx < kx; ++jx) v = v + cmul(ty[rr * kx + jx], __ldg(&d.wx[jx * d.nx + x]));
+      for (int jx = 0; jx < kx; ++jx) v = cmac(v, ty[rr * kx + jx], __ldg(&d.wx[jx * d.nx + x]));
       Jout[((size_t)p * d.ny + y0 + rr) * d.nx + x] = v;
     }
     b0[i] = v;
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_adj_rowifft_ana(Dev d, const fl
     const int rr = i / d.kx, jx = i - rr * d.kx;
     if (rr < nrow) {
       float2 acc = make_float2(0.f, 0.f);
-      for (int x = 0; x < d.nx; ++x) acc = acc + cmulc(g[rr * d.Px + x], __ldg(&d.wx[jx * d.nx + x]));
+      for (int x = 0; x < d.nx; ++x) acc = cmacc(acc, g[rr * d.Px + x], __ldg(&d.wx[jx * d.nx + x]));
       d.T2[((size_t)p * d.ny + y0 + rr) * d.kx + jx] = acc;
     }
   }
@@ -379,8 +379,8 @@ __global__ void __launch_bounds__(256) k_gsf_fwd(Dev d, const float2* __restrict
     __syncthreads();
 #pragma unroll 8
     for (int jj = 0; jj < 64; jj += 2) {
-      a0 = a0 + cmul(sG[ri][jj], sA[pi][jj]);
-      a1 = a1 + cmul(sG[ri][jj + 1], sA[pi][jj + 1]);
+      a0 = cmac(a0, sG[ri][jj], sA[pi][jj]);
+      a1 = cmac(a1, sG[ri][jj + 1], sA[pi][jj + 1]);
     }
   }
   if (r < d.nr && p < d.ni) part[((size_t)blockIdx.z * d.ni + p) * d.nr + r] = a0 + a1;
@@ -433,8 +433,8 @@ __global__ void __launch_bounds__(256) k_gsf_adj(Dev d, const float2* __restrict
     __syncthreads();
 #pragma unroll 8
     for (int rr = 0; rr < 32; rr += 2) {
-      a0 = a0 + cmulc(sR[pi][rr], sG[rr][ji]);
-      a1 = a1 + cmulc(sR[pi][rr + 1], sG[rr + 1][ji]);
+      a0 = cmacc(a0, sR[pi][rr], sG[rr][ji]);
+      a1 = cmacc(a1, sR[pi][rr + 1], sG[rr + 1][ji]);
     }
   }
   if (j < NA && p < d.ni) {
@@ -482,16 +482,16 @@ __global__ void __launch_bounds__(256) k_ana_y_sm(Dev d, const float2* __restric
     for (; y + 3 < ny; y += 4)
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (lane < kx) b[q] = b[q] + cmulc(Ts[(y + q) * kx + lane], w[y + q]);
+        if (lane < kx) b[q] = cmacc(b[q], Ts[(y + q) * kx + lane], w[y + q]);
     for (; y < ny; ++y)
-      if (lane < kx) b[0] = b[0] + cmulc(Ts[y * kx + lane], w[y]);
+      if (lane < kx) b[0] = cmacc(b[0], Ts[y * kx + lane], w[y]);
     a0 = (b[0] + b[1]) + (b[2] + b[3]);
   } else {
 #pragma unroll 4
     for (int y = 0; y < ny; ++y) {
       const float2 wv = w[y];
-      if (lane < kx) a0 = a0 + cmulc(Ts[y * kx + lane], wv);
-      if (lane + 32 < kx) a1 = a1 + cmulc(Ts[y * kx + lane + 32], wv);
+      if (lane < kx) a0 = cmacc(a0, Ts[y * kx + lane], wv);
+      if (lane + 32 < kx) a1 = cmacc(a1, Ts[y * kx + lane + 32], wv);
     }
   }
   float2* o = out + ((size_t)p * d.ky + jy) * kx;
@@ -519,8 +519,8 @@ __global__ void __launch_bounds__(256) k_gsf_fwd_p(Dev d, const float2* __restri
     int j = lane;
     for (; j + 96 < NA; j += 128)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) a[q] = a[q] + cmul(__ldg(&gr[j + 32 * q]), sap[j + 32 * q]);
-    for (; j < NA; j += 32) a[0] = a[0] + cmul(__ldg(&gr[j]), sap[j]);
+      for (int q = 0; q < 4; ++q) a[q] = cmac(a[q], __ldg(&gr[j + 32 * q]), sap[j + 32 * q]);
+    for (; j < NA; j += 32) a[0] = cmac(a[0], __ldg(&gr[j]), sap[j]);
     float2 acc = (a[0] + a[1]) + (a[2] + a[3]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc = acc + make_float2(__shfl_xor_sync(0xffffffffu, acc.x, o),

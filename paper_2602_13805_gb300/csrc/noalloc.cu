@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256) k_gs_partial_static(const float2* __restr
     const float2* gr = gs + (size_t)r * m;
     const float2* xp = x + (size_t)p * m;
     float2 acc = make_float2(0.f, 0.f);
-    for (int n = n0; n < n1; ++n) acc = acc + cmul(__ldg(&gr[n]), __ldg(&xp[n]));
+    for (int n = n0; n < n1; ++n) acc = cmac(acc, __ldg(&gr[n]), __ldg(&xp[n]));
     part[(size_t)c * nout + o] = acc;
   }
 }

@@ -48,8 +48,8 @@ __device__ __forceinline__ void ph_synth_rowfft(const Dev& d, int bx, int by, fl
   float2 t0 = make_float2(0.f, 0.f), t1 = make_float2(0.f, 0.f);
   for (int jy = 0; jy < d.ky; ++jy) {
     const float2 w = __ldg(&d.wy[jy * d.ny + y]);
-    if (lane < d.kx) t0 = t0 + cmul(w, sa[jy * d.kx + lane]);
-    if (lane + 32 < d.kx) t1 = t1 + cmul(w, sa[jy * d.kx + lane + 32]);
+    if (lane < d.kx) t0 = cmac(t0, w, sa[jy * d.kx + lane]);
+    if (lane + 32 < d.kx) t1 = cmac(t1, w, sa[jy * d.kx + lane + 32]);
   }
   float2 v[R];
 #pragma unroll
@@ -61,7 +61,7 @@ __device__ __forceinline__ void ph_synth_rowfft(const Dev& d, int bx, int by, fl
 #pragma unroll
     for (int m = 0; m < R; ++m) {
       const int x = lane + 32 * m;
-      if (2 * m < R && x < d.nx) v[m] = v[m] + cmul(T, __ldg(&d.wx[jx * d.nx + x]));
+      if (2 * m < R && x < d.nx) v[m] = cmac(v[m], T, __ldg(&d.wx[jx * d.nx + x]));
     }
   }
   const size_t row = (size_t)p * d.ny + y;
@@ -423,7 +423,7 @@ __device__ __forceinline__ void ph_adj_rowifft_ana(const Dev& d, int bx, int by,
         if (2 * m < R && x < d.nx) {
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            if (j0 + j < d.kx) acc[j] = acc[j] + cmulc(g[m], __ldg(&d.wx[(size_t)(j0 + j) * d.nx + x]));
+            if (j0 + j < d.kx) acc[j] = cmacc(acc[j], g[m], __ldg(&d.wx[(size_t)(j0 + j) * d.nx + x]));
         }
       }
       warp_reduce_scatter16(acc, lane);
@@ -485,7 +485,7 @@ __device__ __forceinline__ void ph_gs_partial(const Dev& d, int bx, float2* sm, 
 #pragma unroll
           for (int a = 0; a < GS_TP; ++a)
 #pragma unroll
-            for (int b = 0; b < GS_TR; ++b) acc[a][b] = acc[a][b] + cmul(gv[b], xv[a]);
+            for (int b = 0; b < GS_TR; ++b) acc[a][b] = cmac(acc[a][b], gv[b], xv[a]);
         }
       }
     }
@@ -590,7 +590,7 @@ __device__ __forceinline__ void ph_gsh(const Dev& d, int bx, float2* sm, const f
 #pragma unroll
           for (int a = 0; a < GSH_TP; ++a)
 #pragma unroll
-            for (int b = 0; b < GSH_TN; ++b) acc[a][b] = acc[a][b] + cmulc(dv[a], gv[b]);
+            for (int b = 0; b < GSH_TN; ++b) acc[a][b] = cmacc(acc[a][b], dv[a], gv[b]);
         }
       }
     }
@@ -712,8 +712,8 @@ __device__ __forceinline__ void ph_ana_y(const Dev& d, int bx, int by, const flo
   float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
   for (int y = g; y < d.ny; y += 8) {
     const float2 w = __ldg(&d.wy[jy * d.ny + y]);
-    if (lane < d.kx) a0 = a0 + cmulc(T[(size_t)y * d.kx + lane], w);
-    if (lane + 32 < d.kx) a1 = a1 + cmulc(T[(size_t)y * d.kx + lane + 32], w);
+    if (lane < d.kx) a0 = cmacc(a0, T[(size_t)y * d.kx + lane], w);
+    if (lane + 32 < d.kx) a1 = cmacc(a1, T[(size_t)y * d.kx + lane + 32], w);
   }
   part_ay[g][lane] = a0;
   part_ay[g][lane + 32] = a1;

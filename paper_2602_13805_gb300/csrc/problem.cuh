@@ -32,6 +32,7 @@ struct Dev {
   const float2* twy;     // [Py]
   const float2* ghat;    // [Py][Px] spectrum of the circulant G_D kernel / (Px Py)
   const float2* ghat_perm; // [Px][Py] the same in the register FFT's digit-reversed order (fast path)
+  const float2* ghat_col;  // [Px][Py] by column (register FFT's order), natural y-frequency order
   const float2* what;    // [kx][Px] row DFT of the x basis, columns in that order (cluster loop)
   const float2* einc;    // [ni][M]
   const float2* gs;      // [nr][M]
@@ -39,6 +40,7 @@ struct Dev {
   int fold;              // 1: data term through gsf on the coefficients
   const float2* wx;      // [kx][nx] exp(+2 pi i f_k x / nx) / sqrt(nx)
   const float2* wy;      // [ky][ny]
+  const float2* ux;      // [nx] exp(2 pi i m / nx) / sqrt(nx), Wx[jx][x] = ux[f_jx x mod nx] (register-FFT path)
   const float2* esca;    // [ni][nr]
   const double* norms;   // [2] ||E_inc||^2, ||E_sca||^2
 
@@ -205,6 +207,8 @@ pdf_status fp_rowifft_state(const Dev& d, cudaStream_t st);
 pdf_status fp_adj_rowfft(const Dev& d, cudaStream_t st);
 pdf_status fp_adj_rowifft_ana(const Dev& d, const float2* in, int mode, cudaStream_t st);
 pdf_status fp_perm_ghat(const Dev& d, float2* gp, cudaStream_t st);
+pdf_status fp_col_ghat(const Dev& d, float2* gc, cudaStream_t st);
+pdf_status fp_unit_table(int n, float2* u, cudaStream_t st);
 size_t fp_smem_synth(const Dev& d);
 size_t fp_smem_col(const Dev& d);
 size_t fp_smem_state(const Dev& d);

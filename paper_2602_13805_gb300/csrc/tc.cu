@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(128) k_tc_synth1(Dev d, TC t, const float2* __
   if (x >= d.nx) return;
   const float2* a = alpha + ((size_t)p * d.ky + jy) * d.kx;
   float2 acc = make_float2(0.f, 0.f);
-  for (int jx = 0; jx < d.kx; ++jx) acc = acc + cmul(__ldg(&a[jx]), __ldg(&d.wx[(size_t)jx * d.nx + x]));
+  for (int jx = 0; jx < d.kx; ++jx) acc = cmac(acc, __ldg(&a[jx]), __ldg(&d.wx[(size_t)jx * d.nx + x]));
   const size_t r0 = (size_t)(2 * (p * d.nx + x)) * t.KYP, r1 = r0 + t.KYP;
   put_split(t.tb_hi, t.tb_lo, r0 + 2 * jy, acc.x);
   put_split(t.tb_hi, t.tb_lo, r0 + 2 * jy + 1, -acc.y);

@@ -201,9 +201,11 @@ def test_persistent_loop_matches_graph(name):
     b = prob.solve(iters=w.iters, chi_true=chi_t, use_graph=2)
     b2 = prob.solve(iters=w.iters, chi_true=chi_t, use_graph=2)
     assert torch.equal(b["alpha"], b2["alpha"])                     # deterministic
-    # same formulas; the graph's synthesis and x-analysis kernels sum in another order than the
-    # phase code the persistent kernel inlines (measured 3.4e-6 of max |alpha| after 40 steps at c2)
-    assert (a["alpha"] - b["alpha"]).abs().max().item() < 1e-5 * a["alpha"].abs().max().item()
+    # same formulas in another FP32 rounding order: the graph's column convolution factors the
+    # padded DFT as 16 x (P/16) through shared memory, the phase code the persistent kernel inlines
+    # as R x 32 across lanes, and its synthesis and x-analysis sum in another order; 40 Adam steps
+    # amplify the rounding differences (measured 2.1e-5 of max |alpha| at cP, 3.4e-6 at c2)
+    assert (a["alpha"] - b["alpha"]).abs().max().item() < 5e-5 * a["alpha"].abs().max().item()
     assert abs(a["relerr_cco"] - b["relerr_cco"]) < 1e-5
     prob.close()
 

@@ -162,11 +162,13 @@ def kernel_bytes(w):
         "k_adj_rowifft_ana": A + U + T,                        # read A, v; write T2
         "k_ana_y": T + C,                                      # read T2; write the gradient
         "k_gsf_adj": GF + D + 2 * C,                           # read G_S Phi, r_d; update the gradient
+        "k_synth_rowfft+k_gsf_fwd": U + A + C + GF + 2 * D,    # synthesis tiles with the data residual
     }
 
 
 # the CUDA kernel behind each profiled stage of the register-FFT path at the bench's sizes
-KERNEL_OF_STAGE = {"k_colconv": "kf_colconv_2p<P/16>", "k_synth_rowfft": "kf_synth_p<P>",
+KERNEL_OF_STAGE = {"k_colconv": "kf_colconv_2p<P/16>", "k_synth_rowfft": "kf_synth_2p<P/16>",
+                   "k_synth_rowfft+k_gsf_fwd": "kf_synth_2p<P/16>", "k_ana_y": "k_ana_y_cp", "k_gsf_adj": "k_gsf_adj_cp",
                    "k_adj_rowifft_ana": "kf_adj_ana_p<P>", "k_rowifft_state": "kf_rowifft_sums<P> + k_state_combine",
                    "k_adj_rowfft": "kf_adj_rowfft<P>", "k_gsf_fwd": "k_gsf_fwd_p"}
 

@@ -220,7 +220,8 @@ int32_t pdf_profile_loss_grad(pdf_problem* h, const void* alpha, int32_t reps, f
 pdf_status pdf_fp32_fma_peak(int32_t reps, double* tflops, void* stream);
 
 /* Name of kernel k of pdf_loss_grad in launch order ("" when out of range), FP32 path with the
- * default folded data term (fold_gs = 1). */
+ * folded data term (fold_gs = 1) as separate kernels; pdf_stage_name gives a handle's actual
+ * stages (where the tiled synthesis applies, the data residual is formed inside it). */
 const char* pdf_kernel_name(int32_t k);
 
 /* Name of profiled stage k of pdf_loss_grad for this handle's precision (with precision = 1

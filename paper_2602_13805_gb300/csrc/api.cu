@@ -626,6 +626,10 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
     }
     d.ux = u;
   }
+  // the folded data term's residual formed inside the tiled synthesis (FP32 register-FFT path, one
+  // loss partial per tile)
+  d.rd_synth = (d.fold && d.fast && cfg->precision != 1 && fp_synth2p_ok(d) && d.ky * d.kx <= 4096 &&
+                (size_t)d.ni * fp_synth2p_tpi(d) <= PDF_LP_STRIDE) ? 1 : 0;
   d.esca = esca_d;
   d.norms = norms;
   cudaMemsetAsync(esca_d, 0, NI * NR * sizeof(float2), s);
@@ -834,8 +838,9 @@ extern "C" pdf_status pdf_fp32_fma_peak(int32_t reps, double* tflops, void* stre
   return PDF_OK;
 }
 
-extern "C" const char* pdf_kernel_name(int32_t k) { return hp_kernel_name(k, 0, 1); }
+extern "C" const char* pdf_kernel_name(int32_t k) { return hp_kernel_name(k, 0, 1, 0); }
 
 extern "C" const char* pdf_stage_name(pdf_problem* h, int32_t k) {
-  return hp_kernel_name(k, h ? h->cfg.precision : 0, h ? h->d.fold : 1);
+  if (!h) return hp_kernel_name(k, 0, 1, 0);
+  return hp_kernel_name(k, h->cfg.precision, h->d.fold, h->d.rd_synth);
 }

@@ -391,12 +391,15 @@ __global__ void __launch_bounds__(FT, 3) kf_synth_p(Dev d, const float2* __restr
 // the nx <= P/2 non-zero points, twiddle, Q-point DFTs over n1).  The spectra are staged in the
 // register FFT's digit-reversed order (position (f mod R) 32 + brev5(f / R) holds frequency f,
 // R = P / 32; rows padded to 33 per 32) and stored as whole rows, so the row-spectrum plane A
-// keeps the layout the other kernels read.
+// keeps the layout the other kernels read.  With `dterm` each tile also forms the data residual
+// r_d[p][r] = sum_j (G_S Phi)[r][j] alpha_p[j] - E_sca[p][r] of its share of the receivers (a warp
+// per receiver, alpha_p already in shared memory) and its ||r_d||^2 partial (slot: tile index).
 // ---------------------------------------------------------------------------
 #define S2P_ROWS 8
 template <int Q>
 __global__ void __launch_bounds__(Col2p<Q>::NT, Col2p<Q>::MINB)
-    kf_synth_2p(Dev d, const float2* __restrict__ alpha, float2* __restrict__ Jout, int do_fft, int ntiles) {
+    kf_synth_2p(Dev d, const float2* __restrict__ alpha, float2* __restrict__ Jout, int do_fft, int ntiles,
+                int dterm) {
   constexpr int P = 16 * Q, NT = Col2p<Q>::NT, C = S2P_ROWS, SL = 17, R = P / 32, YS = R * 33;
   extern __shared__ float2 sm[];
   const int NA = d.ky * d.kx;
@@ -409,6 +412,7 @@ __global__ void __launch_bounds__(Col2p<Q>::NT, Col2p<Q>::MINB)
   float2* S = xt + (C * LS > C * YS ? C * LS : C * YS);   // [Q][C][SL] exchange array
   float2* ux = S + Q * C * SL;             // [nx] exp(2 pi i m / nx) / sqrt(nx): Wx[jx][x] = ux[f_jx x mod nx]
   int* posf = reinterpret_cast<int*>(ux + d.nx);          // [P] staging position of frequency f
+  __shared__ FF wsum[NT / 32];             // per-warp ||r_d||^2 of the tile's receivers
   const int tid = threadIdx.x;
   const int tpi = (d.ny + C - 1) / C;      // tiles per incidence
   const int hx = (d.kx + 1) / 2;           // modes jx < hx have frequency jx, the others nx - kx + jx
@@ -442,7 +446,37 @@ __global__ void __launch_bounds__(Col2p<Q>::NT, Col2p<Q>::MINB)
       for (int jy = 0; jy < d.ky; ++jy) acc = cmac(acc, wys[jy * C + r], as[jy * d.kx + jx]);
       ts[jx * C + r] = acc;
     }
+    if (dterm) {                           // data residual (Eq. 16) of this tile's share of the receivers
+      const int ti = t - p * tpi, warp = tid >> 5, lane = tid & 31;
+      const int r0 = (int)((long)ti * d.nr / tpi), r1 = (int)((long)(ti + 1) * d.nr / tpi);
+      FF e2 = FF{0.f, 0.f};
+      for (int rr = r0 + warp; rr < r1; rr += NT / 32) {
+        const float2* gr = d.gsf + (size_t)rr * NA;
+        float2 a4[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        int j = lane;
+        for (; j + 96 < NA; j += 128)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) a4[q] = cmac(a4[q], __ldg(&gr[j + 32 * q]), as[j + 32 * q]);
+        for (; j < NA; j += 32) a4[0] = cmac(a4[0], __ldg(&gr[j]), as[j]);
+        float2 a = (a4[0] + a4[1]) + (a4[2] + a4[3]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+          a = a + make_float2(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o));
+        if (lane == 0) {
+          const size_t o = (size_t)p * d.nr + rr;
+          const float2 v = a - d.esca[o];
+          d.rd[o] = v;
+          e2 = ff_add(e2, cabs2(v));
+        }
+      }
+      if (lane == 0) wsum[warp] = e2;
+    }
     __syncthreads();
+    if (dterm && tid == 0) {
+      FF e2 = FF{0.f, 0.f};
+      for (int w = 0; w < NT / 32; ++w) e2 = ff_add(e2, wsum[w]);
+      d.lpart[LP_DATA * PDF_LP_STRIDE + t] = e2;
+    }
     if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x);   // alpha and Wy are free until the next tile
     cp_async_commit();
     if (tid < d.nx) {                      // J rows: thread x, all C rows
@@ -781,12 +815,16 @@ static int synth2p_slots(const Dev& d) {
   return slots;
 }
 
-pdf_status fp_synth_rowfft(const Dev& d, const float2* alpha, float2* Jout, int do_fft, cudaStream_t st) {
+bool fp_synth2p_ok(const Dev& d) { return synth2p_ok(d); }
+int fp_synth2p_tpi(const Dev& d) { return (d.ny + S2P_ROWS - 1) / S2P_ROWS; }
+
+pdf_status fp_synth_rowfft(const Dev& d, const float2* alpha, float2* Jout, int do_fft, cudaStream_t st,
+                           int dterm) {
   if (synth2p_ok(d)) {
     const int ntiles = d.ni * ((d.ny + S2P_ROWS - 1) / S2P_ROWS);
 #define L(Q)                                                                                     \
   kf_synth_2p<Q><<<std::min(ntiles, synth2p_slots<Q>(d)), Col2p<Q>::NT, fp_smem_synth2p(d), st>>>( \
-      d, alpha, Jout, do_fft, ntiles)
+      d, alpha, Jout, do_fft, ntiles, dterm)
     switch (d.Px / 16) {
       case 8: L(8); break;
       case 16: L(16); break;

@@ -499,6 +499,103 @@ __global__ void __launch_bounds__(256) k_ana_y_sm(Dev d, const float2* __restric
   if (lane + 32 < kx) o[lane + 32] = a1;
 }
 
+__device__ __forceinline__ void cp_async8_g(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_g() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_g() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// y-analysis with its operands staged in one round (cp.async): CTA (p, coefficient rows jy0 ..
+// jy0 + 7) copies T2[p] [ny][kx] and the 8 rows of Wy into shared memory, then warp w accumulates,
+// lanes over jx (kx <= 32), out[p][jy][jx] = sum_y T2[p][y][jx] conj(Wy[jy][y]) over y = w, w + 8,
+// ...; the eight warps' partial sums are added in warp order.  Advances the Adam step counter
+// inside the solve loop, as k_ana_y_sm does.
+__global__ void __launch_bounds__(256) k_ana_y_cp(Dev d, const float2* __restrict__ T2, float2* __restrict__ out,
+                                                  int* step_inc) {
+  extern __shared__ float2 smg[];
+  const int p = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ny = d.ny, kx = d.kx, jy0 = blockIdx.y * 8;
+  const int nj = min(8, d.ky - jy0);
+  float2* ts = smg;                        // [ny][kx] T2[p]
+  float2* ws = ts + ny * kx;               // [8][ny]  Wy rows jy0 ..
+  float2* part = ws + 8 * ny;              // [8 warps][8 rows][32]
+  if (step_inc && p == 0 && blockIdx.y == 0 && threadIdx.x == 0) *step_inc += 1;
+  const float2* T = T2 + (size_t)p * ny * kx;
+  for (int i = threadIdx.x; i < ny * kx; i += blockDim.x) cp_async8_g(&ts[i], &T[i]);
+  const float2* W = d.wy + (size_t)jy0 * ny;
+  for (int i = threadIdx.x; i < nj * ny; i += blockDim.x) cp_async8_g(&ws[i], &W[i]);
+  cp_async_commit_g();
+  cp_async_wait_all_g();
+  __syncthreads();
+  float2 acc[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) acc[a] = make_float2(0.f, 0.f);
+  if (lane < kx) {
+#pragma unroll 4
+    for (int y = warp; y < ny; y += 8) {
+      const float2 t = ts[y * kx + lane];
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+        if (a < nj) acc[a] = cmacc(acc[a], t, ws[a * ny + y]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) part[(warp * 8 + a) * 32 + lane] = acc[a];
+  __syncthreads();
+  const int a = warp, jx = lane;
+  if (a < nj && jx < kx) {
+    float2 sum = part[a * 32 + jx];
+    for (int w = 1; w < 8; ++w) sum = sum + part[(w * 8 + a) * 32 + jx];
+    out[(size_t)p * d.ky * kx + (size_t)(jy0 + a) * kx + jx] = sum;
+  }
+}
+static size_t sm_ana_y_cp(const Dev& d) { return ((size_t)d.ny * d.kx + 8 * (size_t)d.ny + 8 * 8 * 32) * sizeof(float2); }
+static bool ana_y_cp_ok(const Dev& d) { return d.kx <= 32 && sm_ana_y_cp(d) <= 100 * 1024; }
+
+// Adjoint data term on the coefficients with its operands staged in one round (cp.async): CTA
+// (32 coefficients j0 .., 8 incidences p0 ..) copies gsf[r][j0 .. j0 + 31] for every receiver and
+// r_d[p0 .. p0 + 7][r], then thread (j, p) adds g[p][j] += (2 / ||E_sca||^2) sum_r r_d[p][r]
+// conj(gsf[r][j]) (two chains over even and odd r).
+__global__ void __launch_bounds__(256) k_gsf_adj_cp(Dev d, const float2* __restrict__ rd, float2* __restrict__ g) {
+  extern __shared__ float2 sma[];
+  const int NA = d.ky * d.kx, nr = d.nr;
+  const int j0 = blockIdx.x * 32, p0 = blockIdx.y * 8;
+  const int nj = min(32, NA - j0), np = min(8, d.ni - p0);
+  float2* gs = sma;                        // [nr][32]
+  float2* rs = gs + nr * 32;               // [8][nr]
+  for (int i = threadIdx.x; i < nr * 32; i += blockDim.x) {
+    const int r = i >> 5, jj = i & 31;
+    if (jj < nj) cp_async8_g(&gs[i], &d.gsf[(size_t)r * NA + j0 + jj]);
+    else gs[i] = make_float2(0.f, 0.f);
+  }
+  for (int i = threadIdx.x; i < 8 * nr; i += blockDim.x) {
+    const int pp = i / nr, r = i - pp * nr;
+    if (pp < np) cp_async8_g(&rs[i], &rd[(size_t)(p0 + pp) * nr + r]);
+    else rs[i] = make_float2(0.f, 0.f);
+  }
+  cp_async_commit_g();
+  cp_async_wait_all_g();
+  __syncthreads();
+  const int jj = threadIdx.x & 31, pp = threadIdx.x >> 5;
+  float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+  const float2* rp = rs + pp * nr;
+  int r = 0;
+#pragma unroll 4
+  for (; r + 1 < nr; r += 2) {
+    a0 = cmacc(a0, rp[r], gs[r * 32 + jj]);
+    a1 = cmacc(a1, rp[r + 1], gs[(r + 1) * 32 + jj]);
+  }
+  if (r < nr) a0 = cmacc(a0, rp[r], gs[r * 32 + jj]);
+  if (jj < nj && pp < np) {
+    const size_t i = (size_t)(p0 + pp) * NA + j0 + jj;
+    g[i] = g[i] + d.invn[1] * (a0 + a1);
+  }
+}
+static size_t sm_gsf_adj_cp(const Dev& d) { return ((size_t)d.nr * 32 + 8 * (size_t)d.nr) * sizeof(float2); }
+static bool gsf_adj_cp_ok(const Dev& d) { return sm_gsf_adj_cp(d) <= 100 * 1024; }
+
+
 // Data residual through the folded operator: CTA (p, block of 8 receivers), alpha_p in shared
 // memory, a warp per receiver (lanes split the coefficients, four independent partial sums, a
 // fixed-order warp sum), r_d[p][r] = sum_j gsf[r][j] alpha[p][j] - E_sca[p][r], and the CTA's
@@ -588,6 +685,8 @@ pdf_status hp_configure_kernels() {
   cudaFuncSetAttribute(k_adj_rowifft_ana, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_ana_y_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
   cudaFuncSetAttribute(k_gsf_fwd_p, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  cudaFuncSetAttribute(k_ana_y_cp, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  cudaFuncSetAttribute(k_gsf_adj_cp, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(e, "cudaFuncSetAttribute");
   return PDF_OK;
@@ -596,7 +695,6 @@ pdf_status hp_configure_kernels() {
 static inline dim3 row_grid(const Dev& d) { return dim3((d.ny + ROWS_PER_CTA - 1) / ROWS_PER_CTA, d.ni); }
 static inline dim3 col_grid(const Dev& d) { return dim3((d.Px + COL_CW - 1) / COL_CW, d.ni); }
 
-int hp_kernels_per_loss_grad(const pdf_problem* h) { return (h->tc || h->d.fold) ? 11 : 12; }
 
 pdf_status hp_check_limits(const Dev& d) {
   const size_t lim = 200 * 1024;
@@ -623,8 +721,19 @@ static const char* kLossGradKernelsFold[] = {
 static const char* kLossGradStagesTCFold[] = {
     "tc_synth(synth1+gemm+post)", "k_colconv", "k_rowifft_state", "k_gsf_fwd", "k_reg", "k_adj_rowfft",
     "k_colconv(conj)", "tc_adj(rowifft+gemm)", "k_ana_y", "k_gsf_adj", "k_finalize"};
+// folded data term with the residual inside the tiled synthesis
+static const char* kLossGradKernelsFused[] = {
+    "k_synth_rowfft+k_gsf_fwd", "k_colconv", "k_rowifft_state", "k_reg", "k_adj_rowfft",
+    "k_colconv(conj)", "k_adj_rowifft_ana", "k_ana_y", "k_gsf_adj", "k_finalize"};
 
-const char* hp_kernel_name(int k, int precision, int fold) {
+int hp_kernels_per_loss_grad(const pdf_problem* h) {
+  const Dev& d = h->d;
+  if (!d.fold) return h->tc ? 11 : 12;
+  return d.rd_synth ? 10 : 11;
+}
+
+const char* hp_kernel_name(int k, int precision, int fold, int rd_synth) {
+  if (fold && rd_synth) return (k >= 0 && k < 10) ? kLossGradKernelsFused[k] : "";
   if (fold) {
     if (k < 0 || k >= 11) return "";
     return precision == 1 ? kLossGradStagesTCFold[k] : kLossGradKernelsFold[k];
@@ -652,7 +761,7 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
   if (tc) {
     if ((s = tc_synth(h, alpha, d.J, 1, st)) != PDF_OK) return s;
   } else if (d.fast) {
-    if ((s = fp_synth_rowfft(d, alpha, d.J, 1, st)) != PDF_OK) return s;
+    if ((s = fp_synth_rowfft(d, alpha, d.J, 1, st, d.rd_synth)) != PDF_OK) return s;
   } else {
     k_synth_rowfft<<<row_grid(d), ROW_THREADS, sm_synth(d), st>>>(d, alpha, d.J, 1);
   }
@@ -669,7 +778,9 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
     k_rowifft_state<<<d.ny, ROW_THREADS, sm_row(d), st>>>(d);
   }
   mark();
-  if (d.rdwarp) {
+  if (d.rd_synth) {
+    // formed by the synthesis tiles
+  } else if (d.rdwarp) {
     k_gsf_fwd_p<<<dim3(d.ni, (d.nr + 7) / 8), 256, sizeof(float2) * d.ky * d.kx, st>>>(d, alpha, d.rd,
                                                                                        d.lpart + LP_DATA * PDF_LP_STRIDE);
   } else if (d.fold) {
@@ -684,7 +795,7 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
     k_gs_reduce<<<n_data_blocks, 256, 0, st>>>(d, d.gspart, d.n_gs_chunks, d.esca, d.rd,
                                                 d.lpart + LP_DATA * PDF_LP_STRIDE);
   }
-  mark();
+  if (!d.rd_synth) mark();
   if (d.cco_loss) {
     if ((s = cc_reg(d, st)) != PDF_OK) return s;
     pdf_count_launch(CCO_LOSS_KERNELS - 1);
@@ -726,21 +837,28 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
   }
   mark();
   float2* g = grad ? grad : h->grad;
-  if (ana_y_sm_ok(d))
+  if (ana_y_cp_ok(d))
+    k_ana_y_cp<<<dim3(d.ni, (d.ky + 7) / 8), 256, sm_ana_y_cp(d), st>>>(d, T2, g, loop_eval ? step_inc : nullptr);
+  else if (ana_y_sm_ok(d))
     k_ana_y_sm<<<dim3(d.ni, (d.ky + 7) / 8), 256, sm_ana_y(d), st>>>(d, T2, g, loop_eval ? step_inc : nullptr);
   else
     k_ana_y<<<dim3(d.ky, d.ni), 256, 0, st>>>(d, T2, g, loop_eval ? step_inc : nullptr);
   mark();
   if (d.fold) {
-    k_gsf_adj<<<dim3((d.ky * d.kx + 31) / 32, (d.ni + 7) / 8), 256, 0, st>>>(d, d.rd, g);
+    if (gsf_adj_cp_ok(d))
+      k_gsf_adj_cp<<<dim3((d.ky * d.kx + 31) / 32, (d.ni + 7) / 8), 256, sm_gsf_adj_cp(d), st>>>(d, d.rd, g);
+    else
+      k_gsf_adj<<<dim3((d.ky * d.kx + 31) / 32, (d.ni + 7) / 8), 256, 0, st>>>(d, d.rd, g);
     mark();
   }
   if (!loop_eval) {
-    k_finalize<<<1, 1024, 0, st>>>(d, terms ? terms : h->terms, d.fast ? fp_n_state(d) : d.ny,
-                                  d.rdwarp ? d.ni * ((d.nr + 7) / 8) : n_data_blocks, d.n_reg_blocks, step_inc);
+    const int n_data = d.rd_synth ? d.ni * fp_synth2p_tpi(d) : d.rdwarp ? d.ni * ((d.nr + 7) / 8) : n_data_blocks;
+    k_finalize<<<1, 1024, 0, st>>>(d, terms ? terms : h->terms, d.fast ? fp_n_state(d) : d.ny, n_data,
+                                  d.n_reg_blocks, step_inc);
     mark();
   }
-  pdf_count_launch((d.fold ? (tc ? 10 : 12) : (tc ? 7 : 12)) - (loop_eval ? 1 : 0) - (d.rdwarp ? 1 : 0));
+  pdf_count_launch((d.fold ? (tc ? 10 : 12) : (tc ? 7 : 12)) - (loop_eval ? 1 : 0) - (d.rdwarp ? 1 : 0) -
+                   (d.rd_synth ? 1 : 0));
   PDF_LAUNCHED("pdf_loss_grad");
   return PDF_OK;
 }

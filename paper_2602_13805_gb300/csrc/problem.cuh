@@ -67,6 +67,7 @@ struct Dev {
   const float2* adam_tab;  // [cap] Adam step size lr / (1 - b1^t) and sqrt(1 - b2^t), t = 1..cap
   int gs_chunk;          // pixels per CTA of the SIMT G_S product
   int rdwarp;             // 1: the data residual runs as k_gsf_fwd_p (a warp per receiver, no reduction)
+  int rd_synth;           // 1: the data residual is formed inside the tiled synthesis (kf_synth_2p)
 
   // CCO inside the loss (pdf_config.cco_in_loss): the regularisers act on chi_CCO (ccoloss.cu)
   int cco_loss;
@@ -186,7 +187,7 @@ pdf_status hp_configure_kernels();
 pdf_status hp_check_limits(const Dev& d);
 pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, double* terms, cudaStream_t st,
                         int* step_inc = nullptr, cudaEvent_t* ev = nullptr);
-const char* hp_kernel_name(int k, int precision, int fold);
+const char* hp_kernel_name(int k, int precision, int fold, int rd_synth);
 bool hp_rdwarp_ok(const Dev& d);
 __global__ void k_ana_y(Dev d, const float2* T2, float2* out, int* step_inc);
 pdf_status hp_gd(pdf_problem* h, const float2* in, float2* out, int adjoint, cudaStream_t st);
@@ -199,7 +200,10 @@ int hp_kernels_per_loss_grad(const pdf_problem* h);
 
 // register-FFT path (fastpath.cu)
 pdf_status fp_configure();
-pdf_status fp_synth_rowfft(const Dev& d, const float2* alpha, float2* Jout, int do_fft, cudaStream_t st);
+pdf_status fp_synth_rowfft(const Dev& d, const float2* alpha, float2* Jout, int do_fft, cudaStream_t st,
+                           int dterm = 0);
+bool fp_synth2p_ok(const Dev& d);
+int fp_synth2p_tpi(const Dev& d);
 pdf_status fp_rowfft_field(const Dev& d, const float2* in, cudaStream_t st);
 pdf_status fp_rowifft_field(const Dev& d, float2* out, cudaStream_t st);
 pdf_status fp_colconv(const Dev& d, int conj, cudaStream_t st);

@@ -630,6 +630,7 @@ extern "C" pdf_status pdf_setup(const pdf_config* cfg, const void* esca, int esc
   // loss partial per tile)
   d.rd_synth = (d.fold && d.fast && cfg->precision != 1 && fp_synth2p_ok(d) && d.ky * d.kx <= 4096 &&
                 (size_t)d.ni * fp_synth2p_tpi(d) <= PDF_LP_STRIDE) ? 1 : 0;
+  d.row2p = (d.fast && fp_row2p_ok(d)) ? 1 : 0;
   d.esca = esca_d;
   d.norms = norms;
   cudaMemsetAsync(esca_d, 0, NI * NR * sizeof(float2), s);

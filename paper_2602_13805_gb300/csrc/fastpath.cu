@@ -688,6 +688,117 @@ __global__ void __launch_bounds__(Col2p<Q>::NT, Col2p<Q>::MINB)
   cp_async_wait<0>();
 }
 
+// ---------------------------------------------------------------------------
+// Split state pass by tiles of one row y and one incidence group g (the FW = 8 incidences
+// p = 8 g + r), P = Px = 16 Q, nx <= P / 2: the inverse row DFT of the convolved plane in two passes
+// through shared memory (as kf_colconv_2p; rows by (r, k2) for pass B^-1, by (r, n1) for pass A^-1,
+// the exchange array [r][n1][k2]) -> G_D J, s = beta J + E_inc + G_D J (Eq. 6) stored, and the
+// group's per-pixel float-float sums of beta J conj(s) and |s|^2 (incidences in increasing order),
+// as kf_rowifft_sums.  Persistent CTAs walk the tiles t = y nsg + g and copy the next tile's row
+// spectra with cp.async during the current one.  (The same tiling for the adjoint row DFT,
+// kf_adj_rowfft, measured slower: 38.9 against 26.6 us at c5, its 8 row groups re-reading the
+// per-pixel w and R-hat.)
+// ---------------------------------------------------------------------------
+template <int Q>
+__global__ void __launch_bounds__(Col2p<Q>::NT, Col2p<Q>::MINB) kf_state_2p(Dev d, int ntiles) {
+  constexpr int P = 16 * Q, NT = Col2p<Q>::NT, C = FW, SL = 17, R = P / 32, YS = R * YPAD;
+  extern __shared__ float2 sm[];
+  float2* twA = sm;                        // [16][Q]
+  float2* ys = twA + 16 * Q;               // [C][YS]  staged row spectra
+  float2* S = ys + C * YS;                 // [C][Q][SL]
+  float* part = reinterpret_cast<float*>(S + C * Q * SL);   // [3][C][nx]
+  int* posf = reinterpret_cast<int*>(part + 3 * C * d.nx);  // [P]
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 16 * Q; i += NT) {
+    const int k2 = i / Q, n1 = i - k2 * Q;
+    twA[i] = d.twx[n1 * k2];
+  }
+  for (int f = tid; f < P; f += NT) posf[f] = (f % R) * YPAD + brev5(f / R);
+  auto issue = [&](int t) {
+    const int y = t / d.nsg, g = t - y * d.nsg;
+    const int nr = min(C, d.ni - g * C);
+    for (int i = tid; i < nr * (P / 2); i += NT) {
+      const int r = i / (P / 2), c = 2 * (i - r * (P / 2));
+      cp_async16(&ys[r * YS + (c >> 5) * YPAD + (c & 31)], &d.A[((size_t)(g * C + r) * d.ny + y) * P + c]);
+    }
+  };
+  int t = blockIdx.x;
+  if (t < ntiles) issue(t);
+  cp_async_commit();
+  for (; t < ntiles; t += gridDim.x) {
+    const int y = t / d.nsg, g = t - y * d.nsg;
+    cp_async_wait<0>();
+    __syncthreads();
+    if (tid < C * 16) {                    // pass B^-1
+      const int k2 = tid & 15, r = tid >> 4;
+      const float2* yr = ys + r * YS;
+      float2 v[Q];
+#pragma unroll
+      for (int k1 = 0; k1 < Q; ++k1) v[k1] = yr[posf[16 * k1 + k2]];
+      SmallDFT<Q, true>::run(v);
+#pragma unroll
+      for (int n1 = 0; n1 < Q; ++n1) S[(r * Q + n1) * SL + k2] = v[n1];
+    }
+    __syncthreads();
+    if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
+    cp_async_commit();
+    if (tid < C * Q) {                     // pass A^-1 and the state at this thread's pixels
+      const int r = tid / Q, n1 = tid - r * Q, p = g * C + r;
+      const bool live = p < d.ni;
+      const size_t rowpix = ((size_t)p * d.ny + y) * d.nx;
+      float2 Jv[8], Ev[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int x = n1 + Q * j;
+        Jv[j] = Ev[j] = make_float2(0.f, 0.f);
+        if (live && x < d.nx) {
+          Jv[j] = d.J[rowpix + x];
+          Ev[j] = d.einc[rowpix + x];
+        }
+      }
+      const float2* sr = S + (r * Q + n1) * SL;
+      float2 e[8], o[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        e[k] = k == 0 ? sr[0] : cmul(sr[2 * k], cconj(twA[2 * k * Q + n1]));
+        o[k] = cmul(sr[2 * k + 1], cconj(twA[(2 * k + 1) * Q + n1]));
+      }
+      SmallDFT<8, true>::run(e);
+      SmallDFT<8, true>::run(o);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int x = n1 + Q * j;
+        if (x < d.nx) {
+          float3 c = make_float3(0.f, 0.f, 0.f);
+          if (live) {
+            const float2 gd = e[j] + (j == 0 ? o[0] : cmul(o[j], cconj(c_tw16[j])));
+            const float2 sv = cmul(d.beta, Jv[j]) + Ev[j] + gd;
+            d.s[rowpix + x] = sv;
+            const float2 nv = cmul(d.beta, cmulc(Jv[j], sv));
+            c = make_float3(nv.x, nv.y, cabs2(sv));
+          }
+          part[(0 * C + r) * d.nx + x] = c.x;
+          part[(1 * C + r) * d.nx + x] = c.y;
+          part[(2 * C + r) * d.nx + x] = c.z;
+        }
+      }
+    }
+    __syncthreads();
+    for (int x = tid; x < d.nx; x += NT) {
+      FF a = FF{0.f, 0.f}, b = FF{0.f, 0.f}, c = FF{0.f, 0.f};
+      for (int r = 0; r < C; ++r) {
+        a = ff_add(a, part[(0 * C + r) * d.nx + x]);
+        b = ff_add(b, part[(1 * C + r) * d.nx + x]);
+        c = ff_add(c, part[(2 * C + r) * d.nx + x]);
+      }
+      const size_t o = (size_t)g * d.M + (size_t)y * d.nx + x;
+      d.sgA[o] = make_float4(a.hi, a.lo, b.hi, b.lo);
+      d.sgB[o] = make_float2(c.hi, c.lo);
+    }
+  }
+  cp_async_wait<0>();
+}
+
 // u[m] = exp(+2 pi i m / n) / sqrt(n), assembled exactly as the synthesis tables (FP64, the same
 // reduced numerator), so that Wx[jx][x] = u[f_jx x mod nx] holds bit for bit
 __global__ void k_unit_table(float2* __restrict__ u, int n) {
@@ -769,6 +880,9 @@ pdf_status fp_configure() {
   cudaFuncSetAttribute(kf_adj_ana_2p<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
   cudaFuncSetAttribute(kf_adj_ana_2p<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
   cudaFuncSetAttribute(kf_adj_ana_2p<24>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+#define CFG3(Q) cudaFuncSetAttribute(kf_state_2p<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  CFG3(8) CFG3(16) CFG3(24)
+#undef CFG3
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(e, "cudaFuncSetAttribute(register FFT)");
   return PDF_OK;
@@ -949,7 +1063,49 @@ pdf_status fp_colconv(const Dev& d, int conj, cudaStream_t st) {
 }
 // State pass: split over incidence groups (d.nsg > 0: row IFFT + group sums, then a per-pixel
 // combine; r and L_State come with the adjoint row DFT) or one CTA per row over all incidences.
+size_t fp_smem_state2p(const Dev& d) {
+  const int Q = d.Px / 16;
+  return ((size_t)16 * Q + (size_t)FW * (d.Px / 32) * YPAD + (size_t)FW * Q * 17) * sizeof(float2) +
+         3 * (size_t)FW * d.nx * sizeof(float) + (size_t)d.Px * sizeof(int);
+}
+// the tiled state pass: split state pass (nsg > 0), Px = 128, 256, 384, nx <= Px / 2
+bool fp_row2p_ok(const Dev& d) {
+  return d.nsg > 0 && (d.Px == 128 || d.Px == 256 || d.Px == 384) && 2 * d.nx <= d.Px &&
+         (size_t)d.ny * d.nsg <= PDF_LP_STRIDE && fp_smem_state2p(d) <= 96 * 1024;
+}
+template <class K>
+static int slots_of(K kernel, int nt, size_t smem) {
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, nt, smem);
+  cudaGetLastError();
+  return std::max(1, sms * std::max(1, occ));
+}
+
 pdf_status fp_rowifft_state(const Dev& d, cudaStream_t st) {
+  if (d.row2p) {
+    const int ntiles = d.ny * d.nsg;
+#define L(Q)                                                                                \
+  {                                                                                         \
+    static size_t sm_ = 0;                                                                  \
+    static int slots_ = 0;                                                                  \
+    if (sm_ != fp_smem_state2p(d)) {                                                        \
+      sm_ = fp_smem_state2p(d);                                                             \
+      slots_ = slots_of(kf_state_2p<Q>, Col2p<Q>::NT, sm_);                                 \
+    }                                                                                       \
+    kf_state_2p<Q><<<std::min(ntiles, slots_), Col2p<Q>::NT, sm_, st>>>(d, ntiles);          \
+  }
+    switch (d.Px / 16) {
+      case 8: L(8); break;
+      case 16: L(16); break;
+      default: L(24); break;
+    }
+#undef L
+    k_state_combine<<<(d.M + 127) / 128, 128, 0, st>>>(d);
+    pdf_count_launch(1);
+    return PDF_OK;
+  }
   if (d.nsg > 0) {
 #define L(P) kf_rowifft_sums<P><<<dim3(d.ny, d.nsg), FT, fp_smem_sums(d), st>>>(d)
     FAST_SWITCH(d.Px, L)

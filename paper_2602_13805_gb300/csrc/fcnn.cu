@@ -18,22 +18,38 @@
 
 constexpr int FCT = 32;   // output tile side and k chunk
 
+// The network output written straight into the coefficients: v = y[m][n] (bias added) goes to
+// alpha[m][n mod k2] (real part for n < k2, imaginary part otherwise) as alpha0 + v / s, where
+// C = (float*)alpha, ldc = k2, mask = (const float*)alpha0 and sc = s.
+__device__ __forceinline__ void fc_store_alpha(float* alpha, const float* a0, const float* sc, int k2, int m, int n,
+                                               float v) {
+  const int re = n < k2 ? 0 : 1, j = n - re * k2;
+  const size_t i = ((size_t)m * k2 + j) * 2 + re;
+  alpha[i] = a0[i] + v / sc[0];
+}
+
 // C(m, n) = sum_k A(m, k) B(k, n) for m < M, n < N, with A(m, k) = TA ? A[k lda + m] : A[m lda + k]
 // and B(k, n) = TB ? B[n ldb + k] : B[k ldb + n].  Epilogue EPI: 0 store; 1 add bias[n], ReLU;
-// 2 add bias[n]; 3 multiply by (mask[m ldc + n] > 0), the ReLU derivative of a stored activation.
-// With gridDim.z = S > 1 block z covers k in [z kc, (z+1) kc) and stores its partial sums to
-// C + z M N (row-major [M][N], no epilogue); k_fc_reduce adds the S partials in order.
+// 2 add bias[n]; 3 multiply by (mask[m ldc + n] > 0), the ReLU derivative of a stored activation;
+// 4 add bias[n] and write the coefficients (fc_store_alpha).  With gridDim.z = S > 1 block z covers
+// k in [z kc, (z+1) kc) and stores its partial sums to C + z M N (row-major [M][N], no epilogue);
+// k_fc_reduce adds the S partials in order.  With `colsum` (single k split only) the blocks of the
+// first column tile also write colsum[m] = sum_k A(m, k), summed in increasing k (the bias gradient
+// of a weight gradient dW = dZ^T X).
 template <bool TA, bool TB, int EPI>
 __global__ void __launch_bounds__(256) k_fc_gemm(const float* __restrict__ A, int lda, const float* __restrict__ B,
                                                  int ldb, float* __restrict__ C, int ldc, int M, int N, int K,
-                                                 int kc, const float* __restrict__ bias, const float* __restrict__ mask) {
+                                                 int kc, const float* __restrict__ bias, const float* __restrict__ mask,
+                                                 const float* __restrict__ sc, float* __restrict__ colsum) {
   __shared__ float As[FCT][FCT + 1];   // [m][k]
   __shared__ float Bs[FCT][FCT + 1];   // [k][n]
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int m0 = blockIdx.y * FCT, n0 = blockIdx.x * FCT;
   const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
   const bool partial = gridDim.z > 1;
+  const bool csum = colsum && !partial && blockIdx.x == 0 && tx == 0;
   float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  float cs0 = 0.f, cs1 = 0.f;
   for (int k0 = kb; k0 < ke; k0 += FCT) {
     for (int e = threadIdx.x; e < FCT * FCT; e += blockDim.x) {
       const int a = e / FCT, b = e - a * FCT;                            // b runs along the contiguous index
@@ -62,7 +78,16 @@ __global__ void __launch_bounds__(256) k_fc_gemm(const float* __restrict__ A, in
       acc[1][0] = fmaf(a1, b0, acc[1][0]);
       acc[1][1] = fmaf(a1, b1, acc[1][1]);
     }
+    if (csum)
+      for (int kk = 0; kk < FCT && k0 + kk < ke; ++kk) {
+        cs0 += As[ty][kk];
+        cs1 += As[ty + 16][kk];
+      }
     __syncthreads();
+  }
+  if (csum) {
+    if (m0 + ty < M) colsum[m0 + ty] = cs0;
+    if (m0 + ty + 16 < M) colsum[m0 + ty + 16] = cs1;
   }
 #pragma unroll
   for (int i = 0; i < 2; ++i)
@@ -76,25 +101,28 @@ __global__ void __launch_bounds__(256) k_fc_gemm(const float* __restrict__ A, in
         continue;
       }
       if (EPI == 1) v = fmaxf(v + bias[n], 0.f);
-      if (EPI == 2) v = v + bias[n];
+      if (EPI == 2 || EPI == 4) v = v + bias[n];
       if (EPI == 3) v = mask[(size_t)m * ldc + n] > 0.f ? v : 0.f;
-      C[(size_t)m * ldc + n] = v;
+      if (EPI == 4) fc_store_alpha(C, mask, sc, ldc, m, n, v);
+      else C[(size_t)m * ldc + n] = v;
     }
 }
 
 // C[m][n] = epilogue(sum over z (increasing) of part[z][m][n]) for the split-k form
 template <int EPI>
 __global__ void k_fc_reduce(const float* __restrict__ part, int S, float* __restrict__ C, int ldc, int M, int N,
-                            const float* __restrict__ bias, const float* __restrict__ mask) {
+                            const float* __restrict__ bias, const float* __restrict__ mask,
+                            const float* __restrict__ sc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M * N) return;
   const int m = i / N, n = i - m * N;
   float v = 0.f;
   for (int z = 0; z < S; ++z) v += part[(size_t)z * M * N + i];
   if (EPI == 1) v = fmaxf(v + bias[n], 0.f);
-  if (EPI == 2) v = v + bias[n];
+  if (EPI == 2 || EPI == 4) v = v + bias[n];
   if (EPI == 3) v = mask[(size_t)m * ldc + n] > 0.f ? v : 0.f;
-  C[(size_t)m * ldc + n] = v;
+  if (EPI == 4) fc_store_alpha(C, mask, sc, ldc, m, n, v);
+  else C[(size_t)m * ldc + n] = v;
 }
 
 // out[c] = sum over r (increasing) of A[r cols + c]: bias gradients
@@ -138,17 +166,6 @@ __global__ void k_fc_input(const float2* __restrict__ a0, int ni, int k2, float*
   }
 }
 
-// alpha = alpha0 + (y[:k2] + i y[k2:]) / s
-__global__ void k_fc_alpha(const float2* __restrict__ a0, const float* __restrict__ y, const float* __restrict__ s,
-                           int ni, int k2, float2* __restrict__ alpha) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ni * k2) return;
-  const int b = i / k2, j = i - b * k2, D = 2 * k2;
-  const float sc = s[0];
-  const float2 v = a0[i];
-  alpha[i] = make_float2(v.x + y[(size_t)b * D + j] / sc, v.y + y[(size_t)b * D + k2 + j] / sc);
-}
-
 // dL/dy = [Re g, Im g] / s
 __global__ void k_fc_dy(const float2* __restrict__ g, const float* __restrict__ s, int ni, int k2,
                         float* __restrict__ dY) {
@@ -167,18 +184,27 @@ constexpr int FC_KC = 2 * FCT;
 constexpr int FC_SMAX = 32;
 static int fc_splits(int K) { return std::min(FC_SMAX, (K + FC_KC - 1) / FC_KC); }
 
+// returns the number of kernels launched; `colsum` (TA products with lda = M): also the sums over
+// k of A(m, k)
 template <bool TA, bool TB, int EPI>
 static int gemm(const float* A, int lda, const float* B, int ldb, float* C, int ldc, int M, int N, int K,
-                const float* bias, const float* mask, float* work, cudaStream_t st) {
+                const float* bias, const float* mask, float* work, cudaStream_t st, const float* sc = nullptr,
+                float* colsum = nullptr) {
   const int S = fc_splits(K), kc = (K + S - 1) / S;
   const dim3 grid((N + FCT - 1) / FCT, (M + FCT - 1) / FCT, S);
   if (S == 1) {
-    k_fc_gemm<TA, TB, EPI><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, M, N, K, K, bias, mask);
+    k_fc_gemm<TA, TB, EPI><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, M, N, K, K, bias, mask, sc, colsum);
     return 1;
   }
-  k_fc_gemm<TA, TB, EPI><<<grid, 256, 0, st>>>(A, lda, B, ldb, work, N, M, N, K, kc, nullptr, nullptr);
-  k_fc_reduce<EPI><<<(M * N + 255) / 256, 256, 0, st>>>(work, S, C, ldc, M, N, bias, mask);
-  return 2;
+  k_fc_gemm<TA, TB, EPI><<<grid, 256, 0, st>>>(A, lda, B, ldb, work, N, M, N, K, kc, nullptr, nullptr, nullptr,
+                                                nullptr);
+  k_fc_reduce<EPI><<<(M * N + 255) / 256, 256, 0, st>>>(work, S, C, ldc, M, N, bias, mask, sc);
+  int n = 2;
+  if (colsum) {                                                          // A(m, k) = A[k lda + m] here
+    k_fc_colsum<<<(M + 255) / 256, 256, 0, st>>>(A, K, M, colsum);
+    ++n;
+  }
+  return n;
 }
 
 // parameter offsets in the flat vector
@@ -240,9 +266,10 @@ pdf_status fc_forward(pdf_problem* h, cudaStream_t st) {
   int n = 1;
   n += gemm<false, true, 1>(f.X, D, th + o.W1, D, f.h1, H, B, H, D, th + o.b1, nullptr, f.work, st);   // h1 = relu(X W1^T + b1)
   n += gemm<false, true, 1>(f.h1, H, th + o.W2, H, f.h2, H, B, H, H, th + o.b2, nullptr, f.work, st);  // h2 = relu(h1 W2^T + b2)
-  n += gemm<false, true, 2>(f.h2, H, th + o.W3, H, f.y, D, B, D, H, th + o.b3, nullptr, f.work, st);   // y = h2 W3^T + b3
-  k_fc_alpha<<<(B * k2 + 255) / 256, 256, 0, st>>>(f.alpha0, f.y, f.s, d.ni, k2, h->alpha);
-  pdf_count_launch(n);
+  // alpha = alpha0 + (y[:k2] + i y[k2:]) / s with y = h2 W3^T + b3, written by the product's epilogue
+  n += gemm<false, true, 4>(f.h2, H, th + o.W3, H, reinterpret_cast<float*>(h->alpha), k2, B, D, H, th + o.b3,
+                            reinterpret_cast<const float*>(f.alpha0), f.work, st, f.s);
+  pdf_count_launch(n - 1);
   PDF_LAUNCHED("network forward");
   return PDF_OK;
 }
@@ -256,15 +283,15 @@ pdf_status fc_backward(pdf_problem* h, cudaStream_t st) {
   float* g = f.gtheta;
   float* dY = f.y;                                                       // y is not needed any more
   k_fc_dy<<<(B * k2 + 255) / 256, 256, 0, st>>>(h->grad, f.s, d.ni, k2, dY);
-  int n = 4;
-  n += gemm<true, false, 0>(dY, D, f.h2, H, g + o.W3, H, D, H, B, nullptr, nullptr, f.work, st);      // dW3 = dY^T h2
-  k_fc_colsum<<<(D + 255) / 256, 256, 0, st>>>(dY, B, D, g + o.b3);                                  // db3
+  int n = 1;
+  // dW3 = dY^T h2, db3 = column sums of dY
+  n += gemm<true, false, 0>(dY, D, f.h2, H, g + o.W3, H, D, H, B, nullptr, nullptr, f.work, st, nullptr, g + o.b3);
   n += gemm<false, false, 3>(dY, D, th + o.W3, H, f.dz2, H, B, H, D, nullptr, f.h2, f.work, st);      // dz2 = (dY W3) 1[h2 > 0]
-  n += gemm<true, false, 0>(f.dz2, H, f.h1, H, g + o.W2, H, H, H, B, nullptr, nullptr, f.work, st);   // dW2 = dz2^T h1
-  k_fc_colsum<<<(H + 255) / 256, 256, 0, st>>>(f.dz2, B, H, g + o.b2);                               // db2
+  // dW2 = dz2^T h1, db2 = column sums of dz2
+  n += gemm<true, false, 0>(f.dz2, H, f.h1, H, g + o.W2, H, H, H, B, nullptr, nullptr, f.work, st, nullptr, g + o.b2);
   n += gemm<false, false, 3>(f.dz2, H, th + o.W2, H, f.dz1, H, B, H, H, nullptr, f.h1, f.work, st);   // dz1 = (dz2 W2) 1[h1 > 0]
-  n += gemm<true, false, 0>(f.dz1, H, f.X, D, g + o.W1, D, H, D, B, nullptr, nullptr, f.work, st);    // dW1 = dz1^T X
-  k_fc_colsum<<<(H + 255) / 256, 256, 0, st>>>(f.dz1, B, H, g + o.b1);                               // db1
+  // dW1 = dz1^T X, db1 = column sums of dz1
+  n += gemm<true, false, 0>(f.dz1, H, f.X, D, g + o.W1, D, H, D, B, nullptr, nullptr, f.work, st, nullptr, g + o.b1);
   pdf_count_launch(n);
   PDF_LAUNCHED("network backward");
   return PDF_OK;

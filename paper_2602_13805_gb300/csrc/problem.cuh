@@ -68,6 +68,7 @@ struct Dev {
   int gs_chunk;          // pixels per CTA of the SIMT G_S product
   int rdwarp;             // 1: the data residual runs as k_gsf_fwd_p (a warp per receiver, no reduction)
   int rd_synth;           // 1: the data residual is formed inside the tiled synthesis (kf_synth_2p)
+  int row2p;              // 1: split state pass by tiles (kf_state_2p)
 
   // CCO inside the loss (pdf_config.cco_in_loss): the regularisers act on chi_CCO (ccoloss.cu)
   int cco_loss;
@@ -203,6 +204,7 @@ pdf_status fp_configure();
 pdf_status fp_synth_rowfft(const Dev& d, const float2* alpha, float2* Jout, int do_fft, cudaStream_t st,
                            int dterm = 0);
 bool fp_synth2p_ok(const Dev& d);
+bool fp_row2p_ok(const Dev& d);
 int fp_synth2p_tpi(const Dev& d);
 pdf_status fp_rowfft_field(const Dev& d, const float2* in, cudaStream_t st);
 pdf_status fp_rowifft_field(const Dev& d, float2* out, cudaStream_t st);

@@ -323,6 +323,55 @@ __global__ void __launch_bounds__(FT, 3) kf_adj_ana_p(Dev d, const float2* in, i
   }
 }
 
+// Adjoint row IFFT + x-analysis with the analysis as a DFT (nx = PX / 2): the x basis is the
+// truncated unitary DFT (Eq. 9), Wx[jx][x] = exp(2 pi i f_jx x / nx) / sqrt(nx), so
+// T2[p][y][jx] = sum_x g[x] conj(Wx[jx][x]) is the forward nx-point DFT of the row g at the retained
+// frequencies f_jx, / sqrt(nx).  After the inverse PX-point row DFT the row's columns x < nx sit in
+// the warp FFT's natural input layout for nx = 32 (R / 2) points (lane l, slot m: x = l + 32 m), so a
+// forward (R/2)-slot warp FFT (nx-entry twiddle table tw2[e] = tw[2 e]) replaces the nx x kx product;
+// lane l, slot k1 then holds frequency k1 + (R/2) brev5(l), written out where it is retained.
+template <int PX>
+__global__ void __launch_bounds__(FT, 3) kf_adj_fft_p(Dev d, const float2* in, int mode) {
+  constexpr int R = PX / 32, H = R / 2, NX = PX / 2;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;                       // [PX]
+  float2* tw2 = sm + PX;                 // [NX]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  load_tw<PX>(tw, d.twx);
+  for (int i = threadIdx.x; i < NX; i += FT) tw2[i] = d.twx[2 * i];
+  __syncthreads();
+  const int kx = d.kx, hx = (kx + 1) / 2, fneg = NX - kx;     // f >= NX - kx + hx: jx = f - fneg
+  const float sc = 1.f / sqrtf((float)NX);
+  const int nrows = d.ni * d.ny;
+  for (int row = blockIdx.x * FW + warp; row < nrows; row += gridDim.x * FW) {
+    float2 h[H];
+    if (mode == 0) {
+      float2 g[R];
+#pragma unroll
+      for (int k = 0; k < R; ++k) g[k] = d.A[(size_t)row * PX + k * 32 + lane];
+      WarpFFT<PX>::inverse(g, tw, lane);
+#pragma unroll
+      for (int m = 0; m < H; ++m) {
+        const size_t idx = (size_t)row * NX + lane + 32 * m;
+        h[m] = d.fold ? g[m] + d.v[idx] : g[m] + d.v[idx] + d.gsh[idx];
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < H; ++m) h[m] = in[(size_t)row * NX + lane + 32 * m];
+    }
+    WarpFFT<NX>::forward(h, tw2, lane);
+    const int fb = H * brev5(lane);
+#pragma unroll
+    for (int k1 = 0; k1 < H; ++k1) {
+      const int f = k1 + fb;
+      const int jx = f < hx ? f : (f >= fneg + hx ? f - fneg : -1);
+      if (jx >= 0) d.T2[(size_t)row * kx + jx] = sc * h[k1];
+    }
+  }
+}
+size_t fp_smem_adjfft(const Dev& d) { return (size_t)(d.Px + d.Px / 2) * sizeof(float2); }
+static bool adjfft_ok(const Dev& d) { return 2 * d.nx == d.Px && d.Px >= 128 && d.kx <= d.nx; }
+
 // ---------------------------------------------------------------------------
 // Synthesis + padded row DFT, persistent: each CTA stages the twiddles and the x basis Wx [kx][nx]
 // in shared memory once; its warps then walk rows (p, y): T'[jx] = sum_jy Wy[jy][y] alpha_p[jy][jx]
@@ -385,8 +434,10 @@ __global__ void __launch_bounds__(FT, 3) kf_synth_p(Dev d, const float2* __restr
 // ---------------------------------------------------------------------------
 // Synthesis (Eq. 9) and padded row DFT by tiles of 8 rows of one incidence, for P = Px = 16 Q
 // (Q = 8, 16, 24) and nx <= P / 2.  Per tile: T'[r][jx] = sum_jy Wy[jy][y0 + r] alpha_p[jy][jx]
-// (alpha_p and the tile's Wy entries staged in shared memory by cp.async one tile ahead); the J
-// rows J[r][x] = sum_jx T'[r][jx] Wx[jx][x], one thread per x accumulating all 8 rows; then the
+// (alpha_p and the tile's Wy entries staged in shared memory by cp.async); the J rows
+// J[r][x] = sum_jx T'[r][jx] Wx[jx][x]: at full width (nx = P / 2) a warp per row takes the inverse
+// nx-point warp FFT of the retained modes (Wx is the truncated unitary DFT, so J is that transform
+// / sqrt(nx)), otherwise a thread per x accumulates all 8 rows; then the
 // row DFT in two passes through shared memory as in kf_colconv_2p (16-point DFTs over n2 from
 // the nx <= P/2 non-zero points, twiddle, Q-point DFTs over n1).  The spectra are staged in the
 // register FFT's digit-reversed order (position (f mod R) 32 + brev5(f / R) holds frequency f,
@@ -394,6 +445,7 @@ __global__ void __launch_bounds__(FT, 3) kf_synth_p(Dev d, const float2* __restr
 // keeps the layout the other kernels read.  With `dterm` each tile also forms the data residual
 // r_d[p][r] = sum_j (G_S Phi)[r][j] alpha_p[j] - E_sca[p][r] of its share of the receivers (a warp
 // per receiver, alpha_p already in shared memory) and its ||r_d||^2 partial (slot: tile index).
+// The next tile's alpha and Wy entries are copied by cp.async from the end of T' on.
 // ---------------------------------------------------------------------------
 #define S2P_ROWS 8
 template <int Q>
@@ -421,7 +473,10 @@ __global__ void __launch_bounds__(Col2p<Q>::NT, Col2p<Q>::MINB)
     twA[i] = d.twx[n1 * k2];
   }
   for (int f = tid; f < P; f += NT) posf[f] = (f % R) * 33 + brev5(f / R);
-  for (int m = tid; m < d.nx; m += NT) ux[m] = d.ux[m];
+  // full width (nx = P / 2): J rows by an inverse nx-point warp FFT, ux holds its twiddles
+  // exp(-2 pi i e / nx) = tw_P[2 e]; otherwise ux is the unit-circle table of the product
+  const bool jfft = 2 * d.nx == P;
+  for (int m = tid; m < d.nx; m += NT) ux[m] = jfft ? d.twx[2 * m] : d.ux[m];
   auto issue = [&](int t) {
     const int p = t / tpi, y0 = (t - p * tpi) * C;
     const float2* ap = alpha + (size_t)p * NA;
@@ -479,7 +534,28 @@ __global__ void __launch_bounds__(Col2p<Q>::NT, Col2p<Q>::MINB)
     }
     if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x);   // alpha and Wy are free until the next tile
     cp_async_commit();
-    if (tid < d.nx) {                      // J rows: thread x, all C rows
+    if (jfft) {                            // J rows: J[r][x] = (1 / sqrt(nx)) sum_f T'(f) e^{2 pi i f x / nx}
+      constexpr int H = P / 64;            // slots per lane of the nx = 32 H point warp FFT
+      const int warp = tid >> 5, lane = tid & 31, fneg = d.nx - d.kx;
+      const float sc = 1.f / sqrtf((float)d.nx);
+      for (int r = warp; r < C; r += NT / 32) {
+        float2 h[H];
+#pragma unroll
+        for (int k1 = 0; k1 < H; ++k1) {   // digit-reversed input: lane l, slot k1 has frequency k1 + H brev5(l)
+          const int f = k1 + H * brev5(lane);
+          const int jx = f < hx ? f : (f >= fneg + hx ? f - fneg : -1);
+          h[k1] = jx >= 0 ? ts[jx * C + r] : make_float2(0.f, 0.f);
+        }
+        WarpFFT<P / 2>::inverse(h, ux, lane);
+#pragma unroll
+        for (int m = 0; m < H; ++m) {
+          const int x = lane + 32 * m;
+          const float2 jv = sc * h[m];
+          if (y0 + r < d.ny) Jout[((size_t)p * d.ny + y0 + r) * d.nx + x] = jv;
+          xt[r * LS + x] = jv;
+        }
+      }
+    } else if (tid < d.nx) {               // J rows: thread x, all C rows
       const int x = tid;
       float2 acc[C];
 #pragma unroll
@@ -1190,6 +1266,23 @@ static int ana2p_slots(const Dev& d) {
 }
 
 pdf_status fp_adj_rowifft_ana(const Dev& d, const float2* in, int mode, cudaStream_t st) {
+  if (adjfft_ok(d)) {
+    const int nrows = d.ni * d.ny, nb = (nrows + FW - 1) / FW;
+#define L(P)                                                                                     \
+  {                                                                                              \
+    static int slots_ = 0;                                                                       \
+    if (!slots_) slots_ = persistent_slots(kf_adj_fft_p<P>, fp_smem_adjfft(d));                  \
+    kf_adj_fft_p<P><<<std::min(nb, slots_), FT, fp_smem_adjfft(d), st>>>(d, in, mode);            \
+  }
+    switch (d.Px) {
+      case 128: L(128); break;
+      case 256: L(256); break;
+      case 384: L(384); break;
+      default: L(512); break;
+    }
+#undef L
+    return PDF_OK;
+  }
   if (ana2p_ok(d)) {
     const int ntiles = d.ni * ((d.ny + S2P_ROWS - 1) / S2P_ROWS);
 #define L(Q)                                                                                          \

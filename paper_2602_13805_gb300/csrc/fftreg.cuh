@@ -96,6 +96,31 @@ template <bool INV> struct SmallDFT<16, INV> {
   static __device__ __forceinline__ void run(float2* v) { dft_4xq<4, INV>(v); }
 };
 
+// R = 2 * 3 points, m = 3 a + b:  X[k1 + 2 k2] = DFT_3 over b of ( W_6^{b k1} DFT_2 over a of x[3 a + b] )
+// (W_6^e = W_12^{2e})
+template <bool INV> struct SmallDFT<6, INV> {
+  static __device__ __forceinline__ void run(float2* v) {
+    float2 F[3][2];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      F[b][0] = v[b] + v[3 + b];
+      F[b][1] = v[b] - v[3 + b];
+      if (b > 0) {
+        float2 w = tw_small<12>(2 * b);
+        if (INV) w.y = -w.y;
+        F[b][1] = cmul(F[b][1], w);
+      }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 2; ++k1) {
+      float2 t[3] = {F[0][k1], F[1][k1], F[2][k1]};
+      Butterfly<float2, 3>::run(t, INV);
+#pragma unroll
+      for (int k2 = 0; k2 < 3; ++k2) v[k1 + 2 * k2] = t[k2];
+    }
+  }
+};
+
 // R = 8 * 3 points, m = 3 a + b:  X[k1 + 8 k2] = DFT_3 over b of ( W_24^{b k1} DFT_8 over a of x[3 a + b] )
 template <bool INV> struct SmallDFT<24, INV> {
   static __device__ __forceinline__ void run(float2* v) {

@@ -369,6 +369,60 @@ __global__ void __launch_bounds__(FT, 3) kf_adj_fft_p(Dev d, const float2* in, i
     }
   }
 }
+// y-analysis (second half of Phi^H, Eq. 9) as a warp FFT: out[p][jy][jx] = sum_y T2[p][y][jx]
+// conj(Wy[jy][y]) is the forward ny-point DFT of column jx of T2[p] at the retained frequencies f_jy,
+// / sqrt(ny).  CTA (p, 8 columns jx0 ..): the columns are copied by cp.async into shared memory,
+// warp w transforms column jx0 + w (lane l, slot m: y = l + 32 m; twiddles tw_ny[e] = tw_Py[2 e]) and
+// writes the retained outputs.  Advances the Adam step counter inside the solve loop, as the other
+// y-analysis kernels do.
+template <int NY>
+__global__ void __launch_bounds__(FT) kf_ana_y_fft(Dev d, const float2* __restrict__ T2, float2* __restrict__ out,
+                                                   int* step_inc) {
+  constexpr int H = NY / 32;
+  __shared__ float2 tws[NY];
+  __shared__ float2 cs[NY * 9];            // [y][8 columns], stride 9
+  const int p = blockIdx.x, jx0 = blockIdx.y * 8, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kx = d.kx, ky = d.ky, nc = min(8, kx - jx0);
+  if (step_inc && p == 0 && blockIdx.y == 0 && threadIdx.x == 0) *step_inc += 1;
+  for (int i = threadIdx.x; i < NY; i += FT) tws[i] = d.twy[2 * i];
+  const float2* T = T2 + (size_t)p * NY * kx + jx0;
+  for (int i = threadIdx.x; i < NY * 8; i += FT) {
+    const int y = i >> 3, c = i & 7;
+    if (c < nc) cp_async8(&cs[y * 9 + c], &T[(size_t)y * kx + c]);
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  if (warp >= nc) return;
+  float2 h[H];
+#pragma unroll
+  for (int m = 0; m < H; ++m) h[m] = cs[(lane + 32 * m) * 9 + warp];
+  WarpFFT<NY>::forward(h, tws, lane);
+  const int hy = (ky + 1) / 2, fneg = NY - ky, fb = H * brev5(lane);
+  const float sc = 1.f / sqrtf((float)NY);
+  float2* o = out + (size_t)p * ky * kx + jx0 + warp;
+#pragma unroll
+  for (int k1 = 0; k1 < H; ++k1) {
+    const int f = k1 + fb;
+    const int jy = f < hy ? f : (f >= fneg + hy ? f - fneg : -1);
+    if (jy >= 0) o[(size_t)jy * kx] = sc * h[k1];
+  }
+}
+
+// the FFT y-analysis: ny = Py / 2 in {64, 128, 192, 256}
+bool fp_ana_y_fft(const Dev& d, const float2* T2, float2* out, int* step_inc, cudaStream_t st) {
+  if (!(d.fast && 2 * d.ny == d.Py && d.ky <= d.ny)) return false;
+  const dim3 grid(d.ni, (d.kx + 7) / 8);
+  switch (d.ny) {
+    case 64: kf_ana_y_fft<64><<<grid, FT, 0, st>>>(d, T2, out, step_inc); break;
+    case 128: kf_ana_y_fft<128><<<grid, FT, 0, st>>>(d, T2, out, step_inc); break;
+    case 192: kf_ana_y_fft<192><<<grid, FT, 0, st>>>(d, T2, out, step_inc); break;
+    case 256: kf_ana_y_fft<256><<<grid, FT, 0, st>>>(d, T2, out, step_inc); break;
+    default: return false;
+  }
+  return true;
+}
+
 size_t fp_smem_adjfft(const Dev& d) { return (size_t)(d.Px + d.Px / 2) * sizeof(float2); }
 static bool adjfft_ok(const Dev& d) { return 2 * d.nx == d.Px && d.Px >= 128 && d.kx <= d.nx; }
 

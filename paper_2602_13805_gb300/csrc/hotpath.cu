@@ -837,7 +837,8 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
   }
   mark();
   float2* g = grad ? grad : h->grad;
-  if (ana_y_cp_ok(d))
+  if (fp_ana_y_fft(d, T2, g, loop_eval ? step_inc : nullptr, st)) {
+  } else if (ana_y_cp_ok(d))
     k_ana_y_cp<<<dim3(d.ni, (d.ky + 7) / 8), 256, sm_ana_y_cp(d), st>>>(d, T2, g, loop_eval ? step_inc : nullptr);
   else if (ana_y_sm_ok(d))
     k_ana_y_sm<<<dim3(d.ni, (d.ky + 7) / 8), 256, sm_ana_y(d), st>>>(d, T2, g, loop_eval ? step_inc : nullptr);

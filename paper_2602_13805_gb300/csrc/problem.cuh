@@ -101,6 +101,7 @@ struct FcState {
   float* dz2;            // [B][H]
   float2* alpha0;        // [ni][ky][kx] the network's input coefficients
   float* work;           // split-k partial sums
+  unsigned* tick;        // [FC_TICKS] per-output-tile arrival counters of the split-k products (zero between uses)
 };
 
 struct pdf_problem {
@@ -205,6 +206,7 @@ pdf_status fp_synth_rowfft(const Dev& d, const float2* alpha, float2* Jout, int 
                            int dterm = 0);
 bool fp_synth2p_ok(const Dev& d);
 bool fp_row2p_ok(const Dev& d);
+bool fp_ana_y_fft(const Dev& d, const float2* T2, float2* out, int* step_inc, cudaStream_t st);
 int fp_synth2p_tpi(const Dev& d);
 pdf_status fp_rowfft_field(const Dev& d, const float2* in, cudaStream_t st);
 pdf_status fp_rowifft_field(const Dev& d, float2* out, cudaStream_t st);

@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(Col2p<Q>::NT, Col2p<Q>::MINB) kf_colconv_2p(De
         const int n = n1 + Q * j;
         const float2 x = n < d.ny ? tile[c * LS + n] : make_float2(0.f, 0.f);
         e[j] = x;
-        o[j] = j == 0 ? x : cmul(x, c_tw16[j]);
+        o[j] = tw_mul<16, false>(x, j);
       }
       SmallDFT<8, false>::run(e);
       SmallDFT<8, false>::run(o);
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(Col2p<Q>::NT, Col2p<Q>::MINB) kf_colconv_2p(De
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int n = n1 + Q * j;
-        if (n < d.ny) Ap[(size_t)n * d.Px] = e[j] + (j == 0 ? o[0] : cmul(o[j], cconj(c_tw16[j])));
+        if (n < d.ny) Ap[(size_t)n * d.Px] = e[j] + tw_mul<16, true>(o[j], j);
       }
     }
   }
@@ -645,7 +645,7 @@ __global__ void __launch_bounds__(Col2p<Q>::NT, Col2p<Q>::MINB)
         const int n = n1 + Q * j;
         const float2 x = n < d.nx ? xt[r * LS + n] : make_float2(0.f, 0.f);
         e[j] = x;
-        o[j] = j == 0 ? x : cmul(x, c_tw16[j]);
+        o[j] = tw_mul<16, false>(x, j);
       }
       SmallDFT<8, false>::run(e);
       SmallDFT<8, false>::run(o);
@@ -767,7 +767,7 @@ __global__ void __launch_bounds__(Col2p<Q>::NT, Col2p<Q>::MINB)
         for (int j = 0; j < 8; ++j) {
           const int x = n1 + Q * j;
           if (x < d.nx) {
-            const float2 g = e[j] + (j == 0 ? o[0] : cmul(o[j], cconj(c_tw16[j])));
+            const float2 g = e[j] + tw_mul<16, true>(o[j], j);
             G[x * C + r] = live ? g + vp[j] : make_float2(0.f, 0.f);
           }
         }
@@ -901,7 +901,7 @@ __global__ void __launch_bounds__(Col2p<Q>::NT, Col2p<Q>::MINB) kf_state_2p(Dev 
         if (x < d.nx) {
           float3 c = make_float3(0.f, 0.f, 0.f);
           if (live) {
-            const float2 gd = e[j] + (j == 0 ? o[0] : cmul(o[j], cconj(c_tw16[j])));
+            const float2 gd = e[j] + tw_mul<16, true>(o[j], j);
             const float2 sv = cmul(d.beta, Jv[j]) + Ev[j] + gd;
             d.s[rowpix + x] = sv;
             const float2 nv = cmul(d.beta, cmulc(Jv[j], sv));

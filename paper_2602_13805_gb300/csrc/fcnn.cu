@@ -33,16 +33,30 @@ __device__ __forceinline__ void fc_store_alpha(float* alpha, const float* a0, co
 // 2 add bias[n]; 3 multiply by (mask[m ldc + n] > 0), the ReLU derivative of a stored activation;
 // 4 add bias[n] and write the coefficients (fc_store_alpha).  With gridDim.z = S > 1 block z covers
 // k in [z kc, (z+1) kc) and stores its partial sums to C + z M N (row-major [M][N], no epilogue);
-// k_fc_reduce adds the S partials in order.  With `colsum` (single k split only) the blocks of the
-// first column tile also write colsum[m] = sum_k A(m, k), summed in increasing k (the bias gradient
-// of a weight gradient dW = dZ^T X).
+// k_fc_reduce adds the S partials in order.  With `tick` (S > 1) the partials go to `work` instead
+// and the last block of each output tile to arrive adds them itself (see the end of the kernel), so
+// no reduction launch is needed.  With `colsum` (single k split only) the blocks of the first column
+// tile also write colsum[m] = sum_k A(m, k), summed in increasing k (the bias gradient of a weight
+// gradient dW = dZ^T X).
+template <int EPI>
+__device__ __forceinline__ void fc_epilogue(float* C, int ldc, int m, int n, float v, const float* bias,
+                                            const float* mask, const float* sc) {
+  if (EPI == 1) v = fmaxf(v + bias[n], 0.f);
+  if (EPI == 2 || EPI == 4) v = v + bias[n];
+  if (EPI == 3) v = mask[(size_t)m * ldc + n] > 0.f ? v : 0.f;
+  if (EPI == 4) fc_store_alpha(C, mask, sc, ldc, m, n, v);
+  else C[(size_t)m * ldc + n] = v;
+}
+
 template <bool TA, bool TB, int EPI>
 __global__ void __launch_bounds__(256) k_fc_gemm(const float* __restrict__ A, int lda, const float* __restrict__ B,
                                                  int ldb, float* __restrict__ C, int ldc, int M, int N, int K,
                                                  int kc, const float* __restrict__ bias, const float* __restrict__ mask,
-                                                 const float* __restrict__ sc, float* __restrict__ colsum) {
+                                                 const float* __restrict__ sc, float* __restrict__ colsum,
+                                                 float* __restrict__ work, unsigned* __restrict__ tick) {
   __shared__ float As[FCT][FCT + 1];   // [m][k]
   __shared__ float Bs[FCT][FCT + 1];   // [k][n]
+  __shared__ int last;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int m0 = blockIdx.y * FCT, n0 = blockIdx.x * FCT;
   const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
@@ -95,17 +109,47 @@ __global__ void __launch_bounds__(256) k_fc_gemm(const float* __restrict__ A, in
     for (int j = 0; j < 2; ++j) {
       const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
       if (m >= M || n >= N) continue;
-      float v = acc[i][j];
+      const float v = acc[i][j];
       if (partial) {
-        C[((size_t)blockIdx.z * M + m) * N + n] = v;
+        (tick ? work : C)[((size_t)blockIdx.z * M + m) * N + n] = v;
         continue;
       }
-      if (EPI == 1) v = fmaxf(v + bias[n], 0.f);
-      if (EPI == 2 || EPI == 4) v = v + bias[n];
-      if (EPI == 3) v = mask[(size_t)m * ldc + n] > 0.f ? v : 0.f;
-      if (EPI == 4) fc_store_alpha(C, mask, sc, ldc, m, n, v);
-      else C[(size_t)m * ldc + n] = v;
+      fc_epilogue<EPI>(C, ldc, m, n, v, bias, mask, sc);
     }
+  if (!partial || !tick) return;
+  // the last block of this output tile to arrive adds the S partials in increasing z (the order of
+  // k_fc_reduce), applies the epilogue and re-arms the counter for the next product
+  __threadfence();
+  __syncthreads();
+  const unsigned t = blockIdx.y * gridDim.x + blockIdx.x;
+  if (threadIdx.x == 0) last = atomicAdd(&tick[t], 1u) == gridDim.z - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // the four outputs of this thread summed together, z unrolled, so many loads are in flight;
+  // each output still adds its partials in increasing z
+  float v[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  int mi[2], nj[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    mi[i] = min(m0 + ty + 16 * i, M - 1);
+    nj[i] = min(n0 + tx + 16 * i, N - 1);
+  }
+  const int S = gridDim.z;
+#pragma unroll 6
+  for (int z = 0; z < S; ++z)
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) v[i][j] += __ldcg(&work[((size_t)z * M + mi[i]) * N + nj[j]]);
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+      if (m < M && n < N) fc_epilogue<EPI>(C, ldc, m, n, v[i][j], bias, mask, sc);
+    }
+  if (threadIdx.x == 0) tick[t] = 0u;
 }
 
 // C[m][n] = epilogue(sum over z (increasing) of part[z][m][n]) for the split-k form
@@ -118,11 +162,7 @@ __global__ void k_fc_reduce(const float* __restrict__ part, int S, float* __rest
   const int m = i / N, n = i - m * N;
   float v = 0.f;
   for (int z = 0; z < S; ++z) v += part[(size_t)z * M * N + i];
-  if (EPI == 1) v = fmaxf(v + bias[n], 0.f);
-  if (EPI == 2 || EPI == 4) v = v + bias[n];
-  if (EPI == 3) v = mask[(size_t)m * ldc + n] > 0.f ? v : 0.f;
-  if (EPI == 4) fc_store_alpha(C, mask, sc, ldc, m, n, v);
-  else C[(size_t)m * ldc + n] = v;
+  fc_epilogue<EPI>(C, ldc, m, n, v, bias, mask, sc);
 }
 
 // out[c] = sum over r (increasing) of A[r cols + c]: bias gradients
@@ -181,6 +221,7 @@ __global__ void k_fc_dy(const float2* __restrict__ g, const float* __restrict__ 
 // k chunk per split (two 32-wide steps): the batch is small, so a long k runs as many blocks of two
 // steps each instead of one block walking k with a round trip to L2 per step
 constexpr int FC_KC = 2 * FCT;
+constexpr int FC_TICKS = 4096;       // output tiles of a split-k product reduced by their last block
 constexpr int FC_SMAX = 32;
 static int fc_splits(int K) { return std::min(FC_SMAX, (K + FC_KC - 1) / FC_KC); }
 
@@ -189,15 +230,23 @@ static int fc_splits(int K) { return std::min(FC_SMAX, (K + FC_KC - 1) / FC_KC);
 template <bool TA, bool TB, int EPI>
 static int gemm(const float* A, int lda, const float* B, int ldb, float* C, int ldc, int M, int N, int K,
                 const float* bias, const float* mask, float* work, cudaStream_t st, const float* sc = nullptr,
-                float* colsum = nullptr) {
+                float* colsum = nullptr, unsigned* tick = nullptr) {
   const int S = fc_splits(K), kc = (K + S - 1) / S;
   const dim3 grid((N + FCT - 1) / FCT, (M + FCT - 1) / FCT, S);
   if (S == 1) {
-    k_fc_gemm<TA, TB, EPI><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, M, N, K, K, bias, mask, sc, colsum);
+    k_fc_gemm<TA, TB, EPI><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, M, N, K, K, bias, mask, sc, colsum,
+                                                  nullptr, nullptr);
+    return 1;
+  }
+  // reduction by the last block where the splits are few (with many, the separate reduction's
+  // M N threads add them faster than the blocks of one tile)
+  if (tick && !colsum && S <= 8 && grid.x * grid.y <= FC_TICKS) {
+    k_fc_gemm<TA, TB, EPI><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, M, N, K, kc, bias, mask, sc, nullptr,
+                                                  work, tick);
     return 1;
   }
   k_fc_gemm<TA, TB, EPI><<<grid, 256, 0, st>>>(A, lda, B, ldb, work, N, M, N, K, kc, nullptr, nullptr, nullptr,
-                                                nullptr);
+                                                nullptr, nullptr, nullptr);
   k_fc_reduce<EPI><<<(M * N + 255) / 256, 256, 0, st>>>(work, S, C, ldc, M, N, bias, mask, sc);
   int n = 2;
   if (colsum) {                                                          // A(m, k) = A[k lda + m] here
@@ -242,6 +291,8 @@ pdf_status fc_prepare(pdf_problem* h, int hidden, const void* params0, cudaStrea
     // split-k partials: the products with M = B rows and a long k (D or H)
     const size_t wn = (size_t)std::max(fc_splits(D) * std::max(H, D), fc_splits(H) * std::max(H, D)) * B;
     if ((s = ws_alloc(h, (void**)&f.work, sizeof(float) * wn)) != PDF_OK) return s;
+    if ((s = ws_alloc(h, (void**)&f.tick, sizeof(unsigned) * FC_TICKS)) != PDF_OK) return s;
+    PDF_CUDA(cudaMemsetAsync(f.tick, 0, sizeof(unsigned) * FC_TICKS, st));
     f.H = H;
     f.D = D;
     f.B = B;
@@ -264,7 +315,8 @@ pdf_status fc_forward(pdf_problem* h, cudaStream_t st) {
   const FcOff o = fc_off(D, H);
   const float* th = f.theta;
   int n = 1;
-  n += gemm<false, true, 1>(f.X, D, th + o.W1, D, f.h1, H, B, H, D, th + o.b1, nullptr, f.work, st);   // h1 = relu(X W1^T + b1)
+  n += gemm<false, true, 1>(f.X, D, th + o.W1, D, f.h1, H, B, H, D, th + o.b1, nullptr, f.work, st, nullptr, nullptr,
+                            f.tick);                                                                 // h1 = relu(X W1^T + b1)
   n += gemm<false, true, 1>(f.h1, H, th + o.W2, H, f.h2, H, B, H, H, th + o.b2, nullptr, f.work, st);  // h2 = relu(h1 W2^T + b2)
   // alpha = alpha0 + (y[:k2] + i y[k2:]) / s with y = h2 W3^T + b3, written by the product's epilogue
   n += gemm<false, true, 4>(f.h2, H, th + o.W3, H, reinterpret_cast<float*>(h->alpha), k2, B, D, H, th + o.b3,
@@ -286,7 +338,8 @@ pdf_status fc_backward(pdf_problem* h, cudaStream_t st) {
   int n = 1;
   // dW3 = dY^T h2, db3 = column sums of dY
   n += gemm<true, false, 0>(dY, D, f.h2, H, g + o.W3, H, D, H, B, nullptr, nullptr, f.work, st, nullptr, g + o.b3);
-  n += gemm<false, false, 3>(dY, D, th + o.W3, H, f.dz2, H, B, H, D, nullptr, f.h2, f.work, st);      // dz2 = (dY W3) 1[h2 > 0]
+  n += gemm<false, false, 3>(dY, D, th + o.W3, H, f.dz2, H, B, H, D, nullptr, f.h2, f.work, st, nullptr, nullptr,
+                             f.tick);                                                                // dz2 = (dY W3) 1[h2 > 0]
   // dW2 = dz2^T h1, db2 = column sums of dz2
   n += gemm<true, false, 0>(f.dz2, H, f.h1, H, g + o.W2, H, H, H, B, nullptr, nullptr, f.work, st, nullptr, g + o.b2);
   n += gemm<false, false, 3>(f.dz2, H, th + o.W2, H, f.dz1, H, B, H, H, nullptr, f.h1, f.work, st);   // dz1 = (dz2 W2) 1[h1 > 0]

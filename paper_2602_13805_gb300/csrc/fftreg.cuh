@@ -48,6 +48,21 @@ __device__ __forceinline__ float2 tw_small(int e) {
   return R == 8 ? c_tw8[e] : (R == 12 ? c_tw12[e] : (R == 16 ? c_tw16[e] : c_tw24[e]));
 }
 
+// t W_R^e (conjugated twiddle when INV) for an exponent that is a compile-time constant once the
+// caller's loops are unrolled: quarter turns (W^{R/4} = -i, W^{R/2} = -1, W^{3R/4} = i) are exact
+// swaps and sign changes, the other exponents a complex product with the table entry
+template <int R, bool INV>
+__device__ __forceinline__ float2 tw_mul(float2 t, int e) {
+  e %= R;
+  if (e == 0) return t;
+  if (4 * e == R) return INV ? make_float2(-t.y, t.x) : make_float2(t.y, -t.x);
+  if (2 * e == R) return make_float2(-t.x, -t.y);
+  if (4 * e == 3 * R) return INV ? make_float2(t.y, -t.x) : make_float2(-t.y, t.x);
+  float2 w = tw_small<R>(e);
+  if (INV) w.y = -w.y;
+  return cmul(t, w);
+}
+
 // R = 4 Q points, m = Q a + b:  X[k1 + 4 k2] = DFT_Q over b of ( W_R^{b k1} DFT_4 over a of x[Q a + b] )
 template <int Q, bool INV>
 __device__ __forceinline__ void dft_4xq(float2* v) {
@@ -58,15 +73,7 @@ __device__ __forceinline__ void dft_4xq(float2* v) {
     float2 t[4] = {v[b], v[Q + b], v[2 * Q + b], v[3 * Q + b]};
     Butterfly<float2, 4>::run(t, INV);
 #pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) {
-      if (b * k1 == 0) {
-        F[b][k1] = t[k1];
-      } else {
-        float2 w = tw_small<R>(b * k1);
-        if (INV) w.y = -w.y;
-        F[b][k1] = cmul(t[k1], w);
-      }
-    }
+    for (int k1 = 0; k1 < 4; ++k1) F[b][k1] = tw_mul<R, INV>(t[k1], b * k1);
   }
 #pragma unroll
   for (int k1 = 0; k1 < 4; ++k1) {
@@ -132,15 +139,7 @@ template <bool INV> struct SmallDFT<24, INV> {
       for (int a = 0; a < 8; ++a) t[a] = v[3 * a + b];
       dft_4xq<2, INV>(t);
 #pragma unroll
-      for (int k1 = 0; k1 < 8; ++k1) {
-        if (b * k1 == 0) {
-          F[b][k1] = t[k1];
-        } else {
-          float2 w = tw_small<24>(b * k1);
-          if (INV) w.y = -w.y;
-          F[b][k1] = cmul(t[k1], w);
-        }
-      }
+      for (int k1 = 0; k1 < 8; ++k1) F[b][k1] = tw_mul<24, INV>(t[k1], b * k1);
     }
 #pragma unroll
     for (int k1 = 0; k1 < 8; ++k1) {

@@ -304,8 +304,12 @@ __device__ __forceinline__ void ph_rowifft_sums(const Dev& d, int y, int g, floa
 
 // Split state pass, part 2 (thread per pixel): the group sums in group order -> R-hat (Eq. 6),
 // chi-hat (Eq. 7), D and the clamp flag.
-__device__ __forceinline__ void ph_state_combine(const Dev& d, int n) {
-  if (n >= d.M) return;
+struct StatePix {
+  float2 R, chi;
+  float D;
+  bool cl;
+};
+__device__ __forceinline__ StatePix state_combine_at(const Dev& d, int n) {
   FF a = FF{0.f, 0.f}, b = FF{0.f, 0.f}, c = FF{0.f, 0.f};
 #pragma unroll 8
   for (int g = 0; g < d.nsg; ++g) {
@@ -315,14 +319,19 @@ __device__ __forceinline__ void ph_state_combine(const Dev& d, int n) {
     b = ff_add(b, FF{A.z, A.w});
     c = ff_add(c, FF{B.x, B.y});
   }
-  const float cf = c.hi + c.lo;
-  const float2 Rv = make_float2((a.hi + a.lo) / cf, (b.hi + b.lo) / cf);
-  bool cl;
-  const float2 chi = chi_of_R_f(Rv, d.beta, d.q_min, &cl);
-  d.R[n] = Rv;
-  d.chi[n] = chi;
-  d.D[n] = cf;
-  d.clamp[n] = cl ? 1 : 0;
+  StatePix o;
+  o.D = c.hi + c.lo;
+  o.R = make_float2((a.hi + a.lo) / o.D, (b.hi + b.lo) / o.D);
+  o.chi = chi_of_R_f(o.R, d.beta, d.q_min, &o.cl);
+  return o;
+}
+__device__ __forceinline__ void ph_state_combine(const Dev& d, int n) {
+  if (n >= d.M) return;
+  const StatePix o = state_combine_at(d, n);
+  d.R[n] = o.R;
+  d.chi[n] = o.chi;
+  d.D[n] = o.D;
+  d.clamp[n] = o.cl ? 1 : 0;
 }
 
 // Adjoint inputs and the row DFT of u.  FUSED_R: the state residual r = R-hat s - beta J (Eq. 15)

@@ -11,6 +11,31 @@
 #define PDF_MAX_P 512           // largest padded FFT length (2 * 256)
 
 // ---------------------------------------------------------------------------
+// programmatic dependent launch: the solve loop's kernels are launched with programmatic stream
+// serialisation and start with pdl_wait(), which returns once the previous kernel in the stream has
+// completed and its memory is visible (a no-op under a plain launch).  No kernel triggers its
+// dependents early, so a dependent grid is scheduled only after every block of the previous one has
+// exited; what the attribute saves is the launch latency between consecutive kernels.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... P, typename... A>
+static inline void launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
+}
+
+// ---------------------------------------------------------------------------
 // complex helpers
 // ---------------------------------------------------------------------------
 template <typename T> struct cvec;

@@ -143,6 +143,7 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 
 template <int Q, bool CONJ>
 __global__ void __launch_bounds__(Col2p<Q>::NT, Col2p<Q>::MINB) kf_colconv_2p(Dev d, int ntiles) {
+  pdl_wait();
   constexpr int P = 16 * Q, NT = Col2p<Q>::NT, C = C2P_COLS, SL = 17;
   extern __shared__ float2 sm[];
   float2* twA = sm;                      // [16][Q]  W_P^{n1 k2} at k2 * Q + n1
@@ -332,6 +333,7 @@ __global__ void __launch_bounds__(FT, 3) kf_adj_ana_p(Dev d, const float2* in, i
 // lane l, slot k1 then holds frequency k1 + (R/2) brev5(l), written out where it is retained.
 template <int PX>
 __global__ void __launch_bounds__(FT, 3) kf_adj_fft_p(Dev d, const float2* in, int mode) {
+  pdl_wait();
   constexpr int R = PX / 32, H = R / 2, NX = PX / 2;
   extern __shared__ float2 sm[];
   float2* tw = sm;                       // [PX]
@@ -378,6 +380,7 @@ __global__ void __launch_bounds__(FT, 3) kf_adj_fft_p(Dev d, const float2* in, i
 template <int NY>
 __global__ void __launch_bounds__(FT) kf_ana_y_fft(Dev d, const float2* __restrict__ T2, float2* __restrict__ out,
                                                    int* step_inc) {
+  pdl_wait();
   constexpr int H = NY / 32;
   __shared__ float2 tws[NY];
   __shared__ float2 cs[NY * 9];            // [y][8 columns], stride 9
@@ -414,10 +417,10 @@ bool fp_ana_y_fft(const Dev& d, const float2* T2, float2* out, int* step_inc, cu
   if (!(d.fast && 2 * d.ny == d.Py && d.ky <= d.ny)) return false;
   const dim3 grid(d.ni, (d.kx + 7) / 8);
   switch (d.ny) {
-    case 64: kf_ana_y_fft<64><<<grid, FT, 0, st>>>(d, T2, out, step_inc); break;
-    case 128: kf_ana_y_fft<128><<<grid, FT, 0, st>>>(d, T2, out, step_inc); break;
-    case 192: kf_ana_y_fft<192><<<grid, FT, 0, st>>>(d, T2, out, step_inc); break;
-    case 256: kf_ana_y_fft<256><<<grid, FT, 0, st>>>(d, T2, out, step_inc); break;
+    case 64: launch_pdl(kf_ana_y_fft<64>, grid, FT, 0, st, d, T2, out, step_inc); break;
+    case 128: launch_pdl(kf_ana_y_fft<128>, grid, FT, 0, st, d, T2, out, step_inc); break;
+    case 192: launch_pdl(kf_ana_y_fft<192>, grid, FT, 0, st, d, T2, out, step_inc); break;
+    case 256: launch_pdl(kf_ana_y_fft<256>, grid, FT, 0, st, d, T2, out, step_inc); break;
     default: return false;
   }
   return true;
@@ -506,6 +509,7 @@ template <int Q>
 __global__ void __launch_bounds__(Col2p<Q>::NT, Col2p<Q>::MINB)
     kf_synth_2p(Dev d, const float2* __restrict__ alpha, float2* __restrict__ Jout, int do_fft, int ntiles,
                 int dterm) {
+  pdl_wait();
   constexpr int P = 16 * Q, NT = Col2p<Q>::NT, C = S2P_ROWS, SL = 17, R = P / 32, YS = R * 33;
   extern __shared__ float2 sm[];
   const int NA = d.ky * d.kx;
@@ -831,6 +835,7 @@ __global__ void __launch_bounds__(Col2p<Q>::NT, Col2p<Q>::MINB)
 // ---------------------------------------------------------------------------
 template <int Q>
 __global__ void __launch_bounds__(Col2p<Q>::NT, Col2p<Q>::MINB) kf_state_2p(Dev d, int ntiles) {
+  pdl_wait();
   constexpr int P = 16 * Q, NT = Col2p<Q>::NT, C = FW, SL = 17, R = P / 32, YS = R * YPAD;
   extern __shared__ float2 sm[];
   float2* twA = sm;                        // [16][Q]
@@ -953,6 +958,7 @@ __global__ void __launch_bounds__(FT) kf_rowifft_state(Dev d) {
 }
 template <int PX, bool FUSED_R>
 __global__ void __launch_bounds__(FT) kf_adj_rowfft(Dev d) {
+  pdl_wait();
   __shared__ float2 sm[PX];
   ph_adj_rowfft<PX, FUSED_R>(d, blockIdx.x, blockIdx.y, sm);
 }
@@ -962,6 +968,7 @@ __global__ void __launch_bounds__(FT) kf_rowifft_sums(Dev d) {
   ph_rowifft_sums<PX>(d, blockIdx.x, blockIdx.y, sm);
 }
 __global__ void __launch_bounds__(128) k_state_combine(Dev d) {
+  pdl_wait();
   ph_state_combine(d, blockIdx.x * blockDim.x + threadIdx.x);
 }
 template <int PX>
@@ -1067,8 +1074,8 @@ pdf_status fp_synth_rowfft(const Dev& d, const float2* alpha, float2* Jout, int 
   if (synth2p_ok(d)) {
     const int ntiles = d.ni * ((d.ny + S2P_ROWS - 1) / S2P_ROWS);
 #define L(Q)                                                                                     \
-  kf_synth_2p<Q><<<std::min(ntiles, synth2p_slots<Q>(d)), Col2p<Q>::NT, fp_smem_synth2p(d), st>>>( \
-      d, alpha, Jout, do_fft, ntiles, dterm)
+  launch_pdl(kf_synth_2p<Q>, std::min(ntiles, synth2p_slots<Q>(d)), Col2p<Q>::NT, fp_smem_synth2p(d), st, d, \
+             alpha, Jout, do_fft, ntiles, dterm)
     switch (d.Px / 16) {
       case 8: L(8); break;
       case 16: L(16); break;
@@ -1167,9 +1174,9 @@ pdf_status fp_colconv(const Dev& d, int conj, cudaStream_t st) {
   {                                                                                                       \
     const int g_ = std::min(ntiles, col2p_slots<Q>(d));                                                   \
     if (conj)                                                                                             \
-      kf_colconv_2p<Q, true><<<g_, Col2p<Q>::NT, fp_smem_col2p(d), st>>>(d, ntiles);                      \
+      launch_pdl(kf_colconv_2p<Q, true>, g_, Col2p<Q>::NT, fp_smem_col2p(d), st, d, ntiles);              \
     else                                                                                                  \
-      kf_colconv_2p<Q, false><<<g_, Col2p<Q>::NT, fp_smem_col2p(d), st>>>(d, ntiles);                     \
+      launch_pdl(kf_colconv_2p<Q, false>, g_, Col2p<Q>::NT, fp_smem_col2p(d), st, d, ntiles);             \
   }
     switch (d.Py / 16) {
       case 8: L(8); break;
@@ -1224,7 +1231,7 @@ pdf_status fp_rowifft_state(const Dev& d, cudaStream_t st) {
       sm_ = fp_smem_state2p(d);                                                             \
       slots_ = slots_of(kf_state_2p<Q>, Col2p<Q>::NT, sm_);                                 \
     }                                                                                       \
-    kf_state_2p<Q><<<std::min(ntiles, slots_), Col2p<Q>::NT, sm_, st>>>(d, ntiles);          \
+    launch_pdl(kf_state_2p<Q>, std::min(ntiles, slots_), Col2p<Q>::NT, sm_, st, d, ntiles);  \
   }
     switch (d.Px / 16) {
       case 8: L(8); break;
@@ -1232,7 +1239,7 @@ pdf_status fp_rowifft_state(const Dev& d, cudaStream_t st) {
       default: L(24); break;
     }
 #undef L
-    k_state_combine<<<(d.M + 127) / 128, 128, 0, st>>>(d);
+    launch_pdl(k_state_combine, (d.M + 127) / 128, 128, 0, st, d);
     pdf_count_launch(1);
     return PDF_OK;
   }
@@ -1251,7 +1258,7 @@ pdf_status fp_rowifft_state(const Dev& d, cudaStream_t st) {
 }
 pdf_status fp_adj_rowfft(const Dev& d, cudaStream_t st) {
   if (d.nsg > 0) {
-#define L(P) kf_adj_rowfft<P, true><<<frow_grid(d), FT, 0, st>>>(d)
+#define L(P) launch_pdl(kf_adj_rowfft<P, true>, frow_grid(d), FT, 0, st, d)
     FAST_SWITCH(d.Px, L)
 #undef L
     return PDF_OK;
@@ -1326,7 +1333,7 @@ pdf_status fp_adj_rowifft_ana(const Dev& d, const float2* in, int mode, cudaStre
   {                                                                                              \
     static int slots_ = 0;                                                                       \
     if (!slots_) slots_ = persistent_slots(kf_adj_fft_p<P>, fp_smem_adjfft(d));                  \
-    kf_adj_fft_p<P><<<std::min(nb, slots_), FT, fp_smem_adjfft(d), st>>>(d, in, mode);            \
+    launch_pdl(kf_adj_fft_p<P>, std::min(nb, slots_), FT, fp_smem_adjfft(d), st, d, in, mode);    \
   }
     switch (d.Px) {
       case 128: L(128); break;

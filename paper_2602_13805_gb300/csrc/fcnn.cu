@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(256) k_fc_gemm(const float* __restrict__ A, in
                                                  int kc, const float* __restrict__ bias, const float* __restrict__ mask,
                                                  const float* __restrict__ sc, float* __restrict__ colsum,
                                                  float* __restrict__ work, unsigned* __restrict__ tick) {
+  pdl_wait();
   __shared__ float As[FCT][FCT + 1];   // [m][k]
   __shared__ float Bs[FCT][FCT + 1];   // [k][n]
   __shared__ int last;
@@ -157,6 +158,7 @@ template <int EPI>
 __global__ void k_fc_reduce(const float* __restrict__ part, int S, float* __restrict__ C, int ldc, int M, int N,
                             const float* __restrict__ bias, const float* __restrict__ mask,
                             const float* __restrict__ sc) {
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M * N) return;
   const int m = i / N, n = i - m * N;
@@ -209,6 +211,7 @@ __global__ void k_fc_input(const float2* __restrict__ a0, int ni, int k2, float*
 // dL/dy = [Re g, Im g] / s
 __global__ void k_fc_dy(const float2* __restrict__ g, const float* __restrict__ s, int ni, int k2,
                         float* __restrict__ dY) {
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ni * k2) return;
   const int b = i / k2, j = i - b * k2, D = 2 * k2;
@@ -234,20 +237,20 @@ static int gemm(const float* A, int lda, const float* B, int ldb, float* C, int 
   const int S = fc_splits(K), kc = (K + S - 1) / S;
   const dim3 grid((N + FCT - 1) / FCT, (M + FCT - 1) / FCT, S);
   if (S == 1) {
-    k_fc_gemm<TA, TB, EPI><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, M, N, K, K, bias, mask, sc, colsum,
-                                                  nullptr, nullptr);
+    launch_pdl(k_fc_gemm<TA, TB, EPI>, grid, 256, 0, st, A, lda, B, ldb, C, ldc, M, N, K, K, bias, mask, sc, colsum,
+               (float*)nullptr, (unsigned*)nullptr);
     return 1;
   }
   // reduction by the last block where the splits are few (with many, the separate reduction's
   // M N threads add them faster than the blocks of one tile)
   if (tick && !colsum && S <= 8 && grid.x * grid.y <= FC_TICKS) {
-    k_fc_gemm<TA, TB, EPI><<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, M, N, K, kc, bias, mask, sc, nullptr,
-                                                  work, tick);
+    launch_pdl(k_fc_gemm<TA, TB, EPI>, grid, 256, 0, st, A, lda, B, ldb, C, ldc, M, N, K, kc, bias, mask, sc,
+               (float*)nullptr, work, tick);
     return 1;
   }
-  k_fc_gemm<TA, TB, EPI><<<grid, 256, 0, st>>>(A, lda, B, ldb, work, N, M, N, K, kc, nullptr, nullptr, nullptr,
-                                                nullptr, nullptr, nullptr);
-  k_fc_reduce<EPI><<<(M * N + 255) / 256, 256, 0, st>>>(work, S, C, ldc, M, N, bias, mask, sc);
+  launch_pdl(k_fc_gemm<TA, TB, EPI>, grid, 256, 0, st, A, lda, B, ldb, work, N, M, N, K, kc, (const float*)nullptr,
+             (const float*)nullptr, (const float*)nullptr, (float*)nullptr, (float*)nullptr, (unsigned*)nullptr);
+  launch_pdl(k_fc_reduce<EPI>, (M * N + 255) / 256, 256, 0, st, (const float*)work, S, C, ldc, M, N, bias, mask, sc);
   int n = 2;
   if (colsum) {                                                          // A(m, k) = A[k lda + m] here
     k_fc_colsum<<<(M + 255) / 256, 256, 0, st>>>(A, K, M, colsum);
@@ -334,7 +337,7 @@ pdf_status fc_backward(pdf_problem* h, cudaStream_t st) {
   const float* th = f.theta;
   float* g = f.gtheta;
   float* dY = f.y;                                                       // y is not needed any more
-  k_fc_dy<<<(B * k2 + 255) / 256, 256, 0, st>>>(h->grad, f.s, d.ni, k2, dY);
+  launch_pdl(k_fc_dy, (B * k2 + 255) / 256, 256, 0, st, (const float2*)h->grad, (const float*)f.s, d.ni, k2, dY);
   int n = 1;
   // dW3 = dY^T h2, db3 = column sums of dY
   n += gemm<true, false, 0>(dY, D, f.h2, H, g + o.W3, H, D, H, B, nullptr, nullptr, f.work, st, nullptr, g + o.b3);

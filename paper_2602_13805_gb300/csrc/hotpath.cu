@@ -266,7 +266,10 @@ __global__ void __launch_bounds__(256) k_gsh(Dev d, const float2* in, float2* ou
 // ---------------------------------------------------------------------------
 // regularisers (Eq. 17-19) and their cotangent pulled back to w = c_R / D
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_reg(Dev d) { ph_reg(d, blockIdx.x, d.chi, nullptr); }
+__global__ void __launch_bounds__(256) k_reg(Dev d) {
+  pdl_wait();
+  ph_reg(d, blockIdx.x, d.chi, nullptr);
+}
 
 // ---------------------------------------------------------------------------
 // adjoint: u (through G_D^H) and v (pointwise), then padded row DFT of u
@@ -558,6 +561,7 @@ static bool ana_y_cp_ok(const Dev& d) { return d.kx <= 32 && sm_ana_y_cp(d) <= 1
 // r_d[p0 .. p0 + 7][r], then thread (j, p) adds g[p][j] += (2 / ||E_sca||^2) sum_r r_d[p][r]
 // conj(gsf[r][j]) (two chains over even and odd r).
 __global__ void __launch_bounds__(256) k_gsf_adj_cp(Dev d, const float2* __restrict__ rd, float2* __restrict__ g) {
+  pdl_wait();
   extern __shared__ float2 sma[];
   const int NA = d.ky * d.kx, nr = d.nr;
   const int j0 = blockIdx.x * 32, p0 = blockIdx.y * 8;
@@ -800,7 +804,7 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
     if ((s = cc_reg(d, st)) != PDF_OK) return s;
     pdf_count_launch(CCO_LOSS_KERNELS - 1);
   } else {
-    k_reg<<<d.n_reg_blocks, 128, 0, st>>>(d);
+    launch_pdl(k_reg, d.n_reg_blocks, 128, 0, st, d);
   }
   mark();
   // adjoint
@@ -847,7 +851,8 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
   mark();
   if (d.fold) {
     if (gsf_adj_cp_ok(d))
-      k_gsf_adj_cp<<<dim3((d.ky * d.kx + 31) / 32, (d.ni + 7) / 8), 256, sm_gsf_adj_cp(d), st>>>(d, d.rd, g);
+      launch_pdl(k_gsf_adj_cp, dim3((d.ky * d.kx + 31) / 32, (d.ni + 7) / 8), 256, sm_gsf_adj_cp(d), st, d,
+                 (const float2*)d.rd, g);
     else
       k_gsf_adj<<<dim3((d.ky * d.kx + 31) / 32, (d.ni + 7) / 8), 256, 0, st>>>(d, d.rd, g);
     mark();

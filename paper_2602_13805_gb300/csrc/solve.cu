@@ -26,6 +26,7 @@
 // ---------------------------------------------------------------------------
 __global__ void k_adam(float* p, const float* g, float* m, float* v, int n, const int* tdev, const float2* tab,
                        int cap, float b1, float b2, float eps) {
+  pdl_wait();
   ph_adam(blockIdx.x * blockDim.x + threadIdx.x, p, g, m, v, n, *tdev, tab, cap, b1, b2, eps);
 }
 
@@ -318,9 +319,9 @@ static pdf_status init_bp_csi(pdf_problem* h, cudaStream_t st) {
 
 static pdf_status adam_step(pdf_problem* h, const pdf_solve_opts* o, cudaStream_t st) {
   const int n = 2 * h->d.ni * h->d.ky * h->d.kx;
-  k_adam<<<(n + 255) / 256, 256, 0, st>>>((float*)h->alpha, (const float*)h->grad, h->adam_m, h->adam_v, n,
-                                          h->adam_t, h->adam_tab, h->adam_cap, (float)o->adam_b1,
-                                          (float)o->adam_b2, (float)o->adam_eps);
+  launch_pdl(k_adam, (n + 255) / 256, 256, 0, st, (float*)h->alpha, (const float*)h->grad, h->adam_m, h->adam_v, n,
+             (const int*)h->adam_t, (const float2*)h->adam_tab, h->adam_cap, (float)o->adam_b1, (float)o->adam_b2,
+             (float)o->adam_eps);
   pdf_count_launch(1);
   PDF_LAUNCHED("Adam");
   return PDF_OK;
@@ -336,8 +337,9 @@ static pdf_status iteration(pdf_problem* h, const pdf_solve_opts* o, cudaStream_
     if ((s = hp_loss_grad(h, h->alpha, h->grad, terms, st, h->adam_t)) != PDF_OK) return s;
     if ((s = fc_backward(h, st)) != PDF_OK) return s;
     const int n = (int)h->fc.np;
-    k_adam<<<(n + 255) / 256, 256, 0, st>>>(h->fc.theta, h->fc.gtheta, h->fc.m, h->fc.v, n, h->adam_t, h->adam_tab,
-                                            h->adam_cap, (float)o->adam_b1, (float)o->adam_b2, (float)o->adam_eps);
+    launch_pdl(k_adam, (n + 255) / 256, 256, 0, st, h->fc.theta, (const float*)h->fc.gtheta, h->fc.m, h->fc.v, n,
+               (const int*)h->adam_t, (const float2*)h->adam_tab, h->adam_cap, (float)o->adam_b1, (float)o->adam_b2,
+               (float)o->adam_eps);
     pdf_count_launch(1);
     PDF_LAUNCHED("Adam on the network weights");
     return PDF_OK;

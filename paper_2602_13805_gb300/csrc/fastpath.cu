@@ -566,11 +566,25 @@ __global__ void __launch_bounds__(Col2p<Q>::NT, Col2p<Q>::MINB)
       for (int rr = r0 + warp; rr < r1; rr += NT / 32) {
         const float2* gr = d.gsf + (size_t)rr * NA;
         float2 a4[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-        int j = lane;
-        for (; j + 96 < NA; j += 128)
+        if (NA <= 1024) {                  // the lane's whole row slice in flight at once (one L2 round trip)
+          float2 gv[32];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) a4[q] = cmac(a4[q], __ldg(&gr[j + 32 * q]), as[j + 32 * q]);
-        for (; j < NA; j += 32) a4[0] = cmac(a4[0], __ldg(&gr[j]), as[j]);
+          for (int q = 0; q < 32; ++q) {
+            const int j = lane + 32 * q;
+            gv[q] = j < NA ? __ldg(&gr[j]) : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            const int j = lane + 32 * q;
+            if (j < NA) a4[q & 3] = cmac(a4[q & 3], gv[q], as[j]);
+          }
+        } else {
+          int j = lane;
+          for (; j + 96 < NA; j += 128)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) a4[q] = cmac(a4[q], __ldg(&gr[j + 32 * q]), as[j + 32 * q]);
+          for (; j < NA; j += 32) a4[0] = cmac(a4[0], __ldg(&gr[j]), as[j]);
+        }
         float2 a = (a4[0] + a4[1]) + (a4[2] + a4[3]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)

@@ -24,6 +24,12 @@ def _w(name, over):
 # generic shared-memory FFT on two, and the unfolded data term (G_S applied to J every evaluation) on two
 PARITY_CASES = [(n, o, {}) for n, o in SMALL_CASES] + [("c2", dict(), {})] + [
     ("g256", dict(nx=256, ny=256, ni=2, nr=8, kx=9, ky=9), {}),     # largest grid: 512-point lines (R = 16)
+    # pads to 128 x 128 but not full width: the synthesis tiles' thread-per-x J product, ragged row
+    # tiles (58 rows), a partial incidence group (5 of 8) in the tiled state pass, the tiled adjoint
+    # analysis and the direct y-analysis
+    ("g60x58", dict(nx=60, ny=58, ni=5, nr=7, kx=9, ky=7), {}),
+    # full width with an even number of retained modes: the warp-FFT J rows and analyses at K = 8
+    ("g64k8", dict(nx=64, ny=64, ni=6, nr=9, kx=8, ky=8), {}),
     ("g24x20-smemfft", dict(nx=24, ny=20, ni=5, nr=7, kx=7, ky=5), dict(fft_path=1)),
     ("c1-smemfft", dict(), dict(fft_path=1)),
     ("c1-unfolded", dict(), dict(fold_gs=0)),

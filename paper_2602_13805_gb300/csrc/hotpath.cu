@@ -271,6 +271,68 @@ __global__ void __launch_bounds__(256) k_reg(Dev d) {
   ph_reg(d, blockIdx.x, d.chi, nullptr);
 }
 
+// The regularisers (Eq. 17-19) by 2-D tiles of RT_Y x RT_X pixels in two phases: chi-hat of the
+// tile with a one-pixel halo staged in shared memory; each pixel's TV / bridge pieces evaluated
+// once (the tile plus its left column and upper row, one thread each); then at each pixel its own
+// pieces combined with its left and upper neighbours', carried to w.  One loss partial per tile
+// (slot blockIdx.y gridDim.x + blockIdx.x).
+#define RT_X 32
+#define RT_Y 8
+#define RT_PX ((RT_Y + 1) * (RT_X + 1))
+#define RT_THREADS ((RT_PX + 31) / 32 * 32)
+__global__ void __launch_bounds__(RT_THREADS) k_reg_tile(Dev d) {
+  __shared__ float2 cs[RT_Y + 2][RT_X + 2];
+  __shared__ RegPiece pc[RT_Y + 1][RT_X + 1];
+  __shared__ FF red_rt[3 * 32];
+  pdl_wait();
+  const int x0 = blockIdx.x * RT_X, y0 = blockIdx.y * RT_Y;
+  const int ty = threadIdx.x / RT_X, y = y0 + ty, x = x0 + threadIdx.x % RT_X, n = y * d.nx + x;
+  const bool own = threadIdx.x < RT_X * RT_Y && y < d.ny && x < d.nx;
+  // this pixel's operands for carrying the cotangent to w, fetched before the staging waits
+  bool clamped = true;
+  float2 Rn = make_float2(0.f, 0.f);
+  float Dn = 1.f;
+  if (own) {
+    clamped = d.clamp[n] != 0;
+    Rn = d.R[n];
+    Dn = d.D[n];
+  }
+  for (int i = threadIdx.x; i < (RT_Y + 2) * (RT_X + 2); i += blockDim.x) {
+    const int ly = i / (RT_X + 2), lx = i - ly * (RT_X + 2), y = y0 - 1 + ly, x = x0 - 1 + lx;
+    cs[ly][lx] = (y >= 0 && y < d.ny && x >= 0 && x < d.nx) ? d.chi[y * d.nx + x] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  if (threadIdx.x < RT_PX) {  // region pixel (y0 - 1 + ly, x0 - 1 + lx)
+    const int ly = threadIdx.x / (RT_X + 1), lx = threadIdx.x - ly * (RT_X + 1);
+    const int y = y0 - 1 + ly, x = x0 - 1 + lx;
+    if (y >= 0 && y < d.ny && x >= 0 && x < d.nx) {
+      const float2* c = &cs[ly][lx];
+      pc[ly][lx] = reg_piece(d, tvb_at(d, [=](int oy, int ox) { return c[oy * (RT_X + 2) + ox]; }, y, x, 0, 0));
+    }
+  }
+  __syncthreads();
+  float lb = 0.f, ltv = 0.f, lbr = 0.f;
+  if (own) {
+    const int tx = x - x0;
+    const float2 cchi = reg_combine(d, cs[ty + 1][tx + 1], pc[ty + 1][tx + 1], x > 0 ? &pc[ty + 1][tx] : nullptr,
+                                    y > 0 ? &pc[ty][tx + 1] : nullptr, lb, ltv, lbr);
+    d.w[n] = reg_w_at(d, clamped, Rn, Dn, cchi);
+  }
+  FF t3[3] = {ff_make(lb), ff_make(ltv), ff_make(lbr)};
+  ff_block_sum_multi<3>(t3, red_rt);
+  if (threadIdx.x == 0) {
+    const int b = blockIdx.y * gridDim.x + blockIdx.x;
+    d.lpart[LP_BOUND * PDF_LP_STRIDE + b] = t3[0];
+    d.lpart[LP_TV * PDF_LP_STRIDE + b] = t3[1];
+    d.lpart[LP_BRIDGE * PDF_LP_STRIDE + b] = t3[2];
+  }
+}
+static dim3 reg_tile_grid(const Dev& d) { return dim3((d.nx + RT_X - 1) / RT_X, (d.ny + RT_Y - 1) / RT_Y); }
+static bool reg_tile_ok(const Dev& d) {
+  const dim3 g = reg_tile_grid(d);
+  return (size_t)g.x * g.y <= PDF_LP_STRIDE;
+}
+
 // ---------------------------------------------------------------------------
 // adjoint: u (through G_D^H) and v (pointwise), then padded row DFT of u
 // ---------------------------------------------------------------------------
@@ -557,46 +619,60 @@ static size_t sm_ana_y_cp(const Dev& d) { return ((size_t)d.ny * d.kx + 8 * (siz
 static bool ana_y_cp_ok(const Dev& d) { return d.kx <= 32 && sm_ana_y_cp(d) <= 100 * 1024; }
 
 // Adjoint data term on the coefficients with its operands staged in one round (cp.async): CTA
-// (32 coefficients j0 .., 8 incidences p0 ..) copies gsf[r][j0 .. j0 + 31] for every receiver and
-// r_d[p0 .. p0 + 7][r], then thread (j, p) adds g[p][j] += (2 / ||E_sca||^2) sum_r r_d[p][r]
-// conj(gsf[r][j]) (two chains over even and odd r).
-__global__ void __launch_bounds__(256) k_gsf_adj_cp(Dev d, const float2* __restrict__ rd, float2* __restrict__ g) {
+// (32 coefficients j0 .., 16 incidences p0 ..) copies gsf[r][j0 .. j0 + 31] for every receiver and
+// r_d[p0 .. p0 + 15][r] (rows padded to an even length), then thread (j, q), q < 8, adds
+// g[p][j] += (2 / ||E_sca||^2) sum_r r_d[p][r] conj(gsf[r][j]) for p = p0 + q and p0 + q + 8 (two
+// chains each, over even and odd r, one 16-byte broadcast load per receiver pair and incidence).
+#define GSA_P 16
+__global__ void __launch_bounds__(GSA_P * 16) k_gsf_adj_cp(Dev d, const float2* __restrict__ rd, float2* __restrict__ g) {
   pdl_wait();
-  extern __shared__ float2 sma[];
-  const int NA = d.ky * d.kx, nr = d.nr;
-  const int j0 = blockIdx.x * 32, p0 = blockIdx.y * 8;
-  const int nj = min(32, NA - j0), np = min(8, d.ni - p0);
-  float2* gs = sma;                        // [nr][32]
-  float2* rs = gs + nr * 32;               // [8][nr]
-  for (int i = threadIdx.x; i < nr * 32; i += blockDim.x) {
+  extern __shared__ float4 sma4[];
+  const int NA = d.ky * d.kx, nr = d.nr, nre = (nr + 1) & ~1;
+  const int j0 = blockIdx.x * 32, p0 = blockIdx.y * GSA_P;
+  const int nj = min(32, NA - j0), np = min(GSA_P, d.ni - p0);
+  float2* rs = reinterpret_cast<float2*>(sma4);  // [GSA_P][nre]
+  float2* gs = rs + GSA_P * nre;                 // [nre][32]
+  for (int i = threadIdx.x; i < nre * 32; i += blockDim.x) {
     const int r = i >> 5, jj = i & 31;
-    if (jj < nj) cp_async8_g(&gs[i], &d.gsf[(size_t)r * NA + j0 + jj]);
+    if (jj < nj && r < nr) cp_async8_g(&gs[i], &d.gsf[(size_t)r * NA + j0 + jj]);
     else gs[i] = make_float2(0.f, 0.f);
   }
-  for (int i = threadIdx.x; i < 8 * nr; i += blockDim.x) {
-    const int pp = i / nr, r = i - pp * nr;
-    if (pp < np) cp_async8_g(&rs[i], &rd[(size_t)(p0 + pp) * nr + r]);
+  for (int i = threadIdx.x; i < GSA_P * nre; i += blockDim.x) {
+    const int pp = i / nre, r = i - pp * nre;
+    if (pp < np && r < nr) cp_async8_g(&rs[i], &rd[(size_t)(p0 + pp) * nr + r]);
     else rs[i] = make_float2(0.f, 0.f);
   }
   cp_async_commit_g();
   cp_async_wait_all_g();
   __syncthreads();
-  const int jj = threadIdx.x & 31, pp = threadIdx.x >> 5;
-  float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-  const float2* rp = rs + pp * nr;
-  int r = 0;
+  const int jj = threadIdx.x & 31, q = threadIdx.x >> 5;
+  float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+  const float4* ra = reinterpret_cast<const float4*>(rs + q * nre);
+  const float4* rb = reinterpret_cast<const float4*>(rs + (q + GSA_P / 2) * nre);
 #pragma unroll 4
-  for (; r + 1 < nr; r += 2) {
-    a0 = cmacc(a0, rp[r], gs[r * 32 + jj]);
-    a1 = cmacc(a1, rp[r + 1], gs[(r + 1) * 32 + jj]);
+  for (int r2 = 0; r2 < nre / 2; ++r2) {
+    const float4 u = ra[r2], v = rb[r2];
+    const float2 g0 = gs[(2 * r2) * 32 + jj], g1 = gs[(2 * r2 + 1) * 32 + jj];
+    a0 = cmacc(a0, make_float2(u.x, u.y), g0);
+    a1 = cmacc(a1, make_float2(u.z, u.w), g1);
+    b0 = cmacc(b0, make_float2(v.x, v.y), g0);
+    b1 = cmacc(b1, make_float2(v.z, v.w), g1);
   }
-  if (r < nr) a0 = cmacc(a0, rp[r], gs[r * 32 + jj]);
-  if (jj < nj && pp < np) {
-    const size_t i = (size_t)(p0 + pp) * NA + j0 + jj;
-    g[i] = g[i] + d.invn[1] * (a0 + a1);
+  if (jj < nj) {
+    if (q < np) {
+      const size_t i = (size_t)(p0 + q) * NA + j0 + jj;
+      g[i] = g[i] + d.invn[1] * (a0 + a1);
+    }
+    if (q + GSA_P / 2 < np) {
+      const size_t i = (size_t)(p0 + q + GSA_P / 2) * NA + j0 + jj;
+      g[i] = g[i] + d.invn[1] * (b0 + b1);
+    }
   }
 }
-static size_t sm_gsf_adj_cp(const Dev& d) { return ((size_t)d.nr * 32 + 8 * (size_t)d.nr) * sizeof(float2); }
+static size_t sm_gsf_adj_cp(const Dev& d) {
+  const size_t nre = (size_t)((d.nr + 1) & ~1);
+  return (nre * 32 + GSA_P * nre) * sizeof(float2);
+}
 static bool gsf_adj_cp_ok(const Dev& d) { return sm_gsf_adj_cp(d) <= 100 * 1024; }
 
 
@@ -804,7 +880,10 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
     if ((s = cc_reg(d, st)) != PDF_OK) return s;
     pdf_count_launch(CCO_LOSS_KERNELS - 1);
   } else {
-    launch_pdl(k_reg, d.n_reg_blocks, 128, 0, st, d);
+    if (reg_tile_ok(d))
+      launch_pdl(k_reg_tile, reg_tile_grid(d), RT_THREADS, 0, st, d);
+    else
+      launch_pdl(k_reg, d.n_reg_blocks, 128, 0, st, d);
   }
   mark();
   // adjoint
@@ -851,7 +930,7 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
   mark();
   if (d.fold) {
     if (gsf_adj_cp_ok(d))
-      launch_pdl(k_gsf_adj_cp, dim3((d.ky * d.kx + 31) / 32, (d.ni + 7) / 8), 256, sm_gsf_adj_cp(d), st, d,
+      launch_pdl(k_gsf_adj_cp, dim3((d.ky * d.kx + 31) / 32, (d.ni + GSA_P - 1) / GSA_P), GSA_P * 16, sm_gsf_adj_cp(d), st, d,
                  (const float2*)d.rd, g);
     else
       k_gsf_adj<<<dim3((d.ky * d.kx + 31) / 32, (d.ni + 7) / 8), 256, 0, st>>>(d, d.rd, g);
@@ -860,7 +939,9 @@ pdf_status hp_loss_grad(pdf_problem* h, const float2* alpha, float2* grad, doubl
   if (!loop_eval) {
     const int n_data = d.rd_synth ? d.ni * fp_synth2p_tpi(d) : d.rdwarp ? d.ni * ((d.nr + 7) / 8) : n_data_blocks;
     k_finalize<<<1, 1024, 0, st>>>(d, terms ? terms : h->terms, d.fast ? fp_n_state(d) : d.ny, n_data,
-                                  d.n_reg_blocks, step_inc);
+                                  reg_tile_ok(d) && !d.cco_loss ? (int)(reg_tile_grid(d).x * reg_tile_grid(d).y)
+                                                                 : d.n_reg_blocks,
+                                  step_inc);
     mark();
   }
   pdf_count_launch((d.fold ? (tc ? 10 : 12) : (tc ? 7 : 12)) - (loop_eval ? 1 : 0) - (d.rdwarp ? 1 : 0) -

@@ -630,12 +630,15 @@ __device__ __forceinline__ void ph_gsh(const Dev& d, int bx, float2* sm, const f
 
 // The regularisers' cotangent c_chi on chi-hat carried to w = conj(d chi / d R) c_chi / D:
 // chi = R / (beta (1 - R)) gives d chi / d R = 1 / (beta (1 - R)^2), zero where the clamp is active.
-__device__ __forceinline__ float2 reg_w(const Dev& d, int n, float2 cchi) {
-  if (d.clamp[n]) return make_float2(0.f, 0.f);
-  const float2 R = d.R[n];
+__device__ __forceinline__ float2 reg_w_at(const Dev& d, bool clamped, float2 R, float Dn, float2 cchi) {
+  if (clamped) return make_float2(0.f, 0.f);
   const float2 q = make_float2(1.f - R.x, -R.y);
   const float2 dchi = cdivf(make_float2(1.f, 0.f), cmul(d.beta, cmul(q, q)));
-  return (1.f / d.D[n]) * cmul(cconj(dchi), cchi);
+  return (1.f / Dn) * cmul(cconj(dchi), cchi);
+}
+__device__ __forceinline__ float2 reg_w(const Dev& d, int n, float2 cchi) {
+  if (d.clamp[n]) return make_float2(0.f, 0.f);
+  return reg_w_at(d, false, d.R[n], d.D[n], cchi);
 }
 
 struct TVB {  // per-pixel pieces of the TV and bridge terms at one pixel
@@ -645,24 +648,78 @@ struct TVB {  // per-pixel pieces of the TV and bridge terms at one pixel
   float sg, e;      // sigmoid and exp factors
 };
 
-__device__ __forceinline__ float mag_at(const float2* chi, int nx, int y, int x, float eps) {
-  const float2 c = chi[y * nx + x];
-  return sqrtf(cabs2(c) + eps);
-}
-
-__device__ __forceinline__ TVB tvb_at(const Dev& d, const float2* chi, int y, int x) {
+// The TV and bridge pieces at pixel (y + oy, x + ox); `at(oy, ox)` reads chi there (global memory or
+// a staged tile), so every caller shares one arithmetic.
+template <class At>
+__device__ __forceinline__ TVB tvb_at(const Dev& d, At at, int y, int x, int oy, int ox) {
   TVB o;
-  const float2 c = chi[y * d.nx + x];
-  const bool hx = x + 1 < d.nx, hy = y + 1 < d.ny;
-  o.dx = hx ? chi[y * d.nx + x + 1] - c : make_float2(0.f, 0.f);
-  o.dy = hy ? chi[(y + 1) * d.nx + x] - c : make_float2(0.f, 0.f);
+  const float2 c = at(oy, ox);
+  const bool hx = x + ox + 1 < d.nx, hy = y + oy + 1 < d.ny;
+  const float2 cx = hx ? at(oy, ox + 1) : c, cy = hy ? at(oy + 1, ox) : c;
+  o.dx = hx ? cx - c : make_float2(0.f, 0.f);
+  o.dy = hy ? cy - c : make_float2(0.f, 0.f);
   o.t = sqrtf(cabs2(o.dx) + cabs2(o.dy) + d.eps_tv);
   const float m = sqrtf(cabs2(c) + d.eps_abs);
-  o.gx = hx ? mag_at(chi, d.nx, y, x + 1, d.eps_abs) - m : 0.f;
-  o.gy = hy ? mag_at(chi, d.nx, y + 1, x, d.eps_abs) - m : 0.f;
+  o.gx = hx ? sqrtf(cabs2(cx) + d.eps_abs) - m : 0.f;
+  o.gy = hy ? sqrtf(cabs2(cy) + d.eps_abs) - m : 0.f;
   o.sg = 1.f / (1.f + expf(-(m - d.tau_b) / d.tau_b));
   o.e = expf(-(o.gx * o.gx + o.gy * o.gy));
   return o;
+}
+
+// What one pixel's TV and bridge terms give: their loss values, the cotangent pieces they put on
+// the pixel itself (own) and on its right / lower neighbours' cotangents as seen from there (the
+// neighbour's "left" / "upper" term).
+struct RegPiece {
+  float2 tv_own, tv_l, tv_u;  // -(dx + dy)/t;  dx/t;  dy/t
+  float dm_own, dm_l, dm_u;   // bridge cotangent on |chi|: own;  -2 gx sg e;  -2 gy sg e
+  float t, b;                 // TV and bridge loss values
+};
+__device__ __forceinline__ RegPiece reg_piece(const Dev& d, const TVB& o) {
+  RegPiece r;
+  r.tv_own = (-1.f / o.t) * (o.dx + o.dy);
+  r.tv_l = (1.f / o.t) * o.dx;
+  r.tv_u = (1.f / o.t) * o.dy;
+  r.dm_own = o.sg * (1.f - o.sg) / d.tau_b * o.e + 2.f * (o.gx + o.gy) * o.sg * o.e;
+  r.dm_l = -2.f * o.gx * o.sg * o.e;
+  r.dm_u = -2.f * o.gy * o.sg * o.e;
+  r.t = o.t;
+  r.b = o.sg * o.e;
+  return r;
+}
+
+// Regularisers of Eq. (17)-(19) at pixel value c from the pieces of its own, left (x > 0) and upper
+// (y > 0) TV / bridge terms: sets lb, ltv, lbr and returns the cotangent on chi there.
+__device__ __forceinline__ float2 reg_combine(const Dev& d, float2 c, const RegPiece& o, const RegPiece* l,
+                                             const RegPiece* u, float& lb, float& ltv, float& lbr) {
+  const float neg = fmaxf(-c.x, 0.f);
+  lb = neg * neg;
+  ltv = o.t;
+  lbr = o.b;
+  float2 ctv = o.tv_own;
+  float dm = o.dm_own;
+  if (l) {
+    ctv = ctv + l->tv_l;
+    dm += l->dm_l;
+  }
+  if (u) {
+    ctv = ctv + u->tv_u;
+    dm += u->dm_u;
+  }
+  const float m = sqrtf(cabs2(c) + d.eps_abs);
+  float2 cchi = d.lam_tv * ctv + (d.lam_bridge * dm / m) * c;
+  cchi.x += d.lam_bound * (-2.f * neg);
+  return cchi;
+}
+
+// Regularisers at pixel (y, x) with every piece evaluated here (own, left, upper).
+template <class At>
+__device__ __forceinline__ float2 reg_pixel(const Dev& d, At at, int y, int x, float& lb, float& ltv, float& lbr) {
+  const RegPiece o = reg_piece(d, tvb_at(d, at, y, x, 0, 0));
+  RegPiece l, u;
+  if (x > 0) l = reg_piece(d, tvb_at(d, at, y, x, 0, -1));
+  if (y > 0) u = reg_piece(d, tvb_at(d, at, y, x, -1, 0));
+  return reg_combine(d, at(0, 0), o, x > 0 ? &l : nullptr, y > 0 ? &u : nullptr, lb, ltv, lbr);
 }
 
 
@@ -675,29 +732,9 @@ __device__ __forceinline__ void ph_reg(const Dev& d, int bx, const float2* img, 
   float lb = 0.f, ltv = 0.f, lbr = 0.f;
   if (n < d.M) {
     const int y = n / d.nx, x = n - y * d.nx;
-    const float2 c = img[n];
-    const float neg = fmaxf(-c.x, 0.f);
-    lb = neg * neg;
-    const TVB o = tvb_at(d, img, y, x);
-    ltv = o.t;
-    lbr = o.sg * o.e;
-    // TV cotangent: -(dx + dy)/t at the own term, + dx/t of the left term, + dy/t of the upper term
-    float2 ctv = (-1.f / o.t) * (o.dx + o.dy);
-    // bridge cotangent on |chi|: own sigmoid term, own differences (-1), left / upper differences (+1)
-    float dm = o.sg * (1.f - o.sg) / d.tau_b * o.e + 2.f * (o.gx + o.gy) * o.sg * o.e;
-    if (x > 0) {
-      const TVB l = tvb_at(d, img, y, x - 1);
-      ctv = ctv + (1.f / l.t) * l.dx;
-      dm += -2.f * l.gx * l.sg * l.e;
-    }
-    if (y > 0) {
-      const TVB u = tvb_at(d, img, y - 1, x);
-      ctv = ctv + (1.f / u.t) * u.dy;
-      dm += -2.f * u.gy * u.sg * u.e;
-    }
-    const float m = sqrtf(cabs2(c) + d.eps_abs);
-    float2 cchi = d.lam_tv * ctv + (d.lam_bridge * dm / m) * c;
-    cchi.x += d.lam_bound * (-2.f * neg);
+    const float2* p = img + n;
+    const int nx = d.nx;
+    const float2 cchi = reg_pixel(d, [=](int oy, int ox) { return p[oy * nx + ox]; }, y, x, lb, ltv, lbr);
     if (cot) {
       cot[n] = cchi;
     } else {

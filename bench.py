@@ -177,7 +177,7 @@ KERNEL_OF_STAGE = {"k_colconv": "kf_colconv_2p<P/16>", "k_synth_rowfft": "kf_syn
 TRAFFIC_PER_LAUNCH = {("c5", "k_colconv"): 38964992 + 19456}      # kf_colconv_2p<24>, the ncu summary in profiles/
 
 
-def cluster_flops(w, fold=1):
+def cluster_flops(w, fold=1, hidden=0):
     """Algorithmic FP32 flops of one iteration of the fused loop (linear algebra only).
 
     Per incidence: synthesis T' = Wy^T alpha (ny ky kx complex MACs) and J = T' Wx (ny nx kx), the
@@ -186,8 +186,11 @@ def cluster_flops(w, fold=1):
     complex products, each), and the data term forward and adjoint: with the folded operator
     (fold = 1, the only form the fused loop runs) (G_S Phi) alpha and its adjoint, nr ky kx complex
     MACs each; unfolded (fold = 0) G_S J and G_S^H r_d, nr M each.  A complex MAC is 8 flops, a
-    complex product 6.  The pointwise CIE / regulariser work is not counted, so this is a lower
-    bound on the work done.
+    complex product 6.  With the coefficient-correcting network (hidden width H > 0, D = 2 ky kx
+    outputs) also its forward pass (H D + H H + D H real MACs), the chain rule to the hidden layers
+    (D H + H H) and the weight gradients (H D + H H + D H) per incidence, 2 flops a MAC.  The
+    pointwise CIE / regulariser work and the Adam updates are not counted, so this is a lower bound
+    on the work done.
     """
     px, py = next_smooth(2 * w.nx), next_smooth(2 * w.ny)
     M = w.nx * w.ny
@@ -195,7 +198,9 @@ def cluster_flops(w, fold=1):
     fft = lambda n: 5 * n * np.log2(n)
     gd = (2 * w.ny * fft(px) + 2 * px * fft(py)) + 6 * px * py
     gs = 8 * w.nr * (w.ky * w.kx if fold else M)
-    return float(w.ni * (2 * syn + 2 * gd + 2 * gs))
+    H, D = hidden, 2 * w.ky * w.kx
+    net = 2 * (3 * (H * D + H * H + D * H) - H * D) if H > 0 else 0
+    return float(w.ni * (2 * syn + 2 * gd + 2 * gs + net))
 
 
 def hbm_model(w, loop_ms, peaks, fold=1):
@@ -357,7 +362,7 @@ def run_ours(args, rank, world, local):
     achieved = kb[dom_name] / (dom_ms * 1e-3) / 1e9
     fma_tflops = pdf.pdf_fp32_fma_peak(10)             # measured FP32 FMA peak (burst)
     if rep.loop_mode == 3 and loop_ms is not None:
-        fl = cluster_flops(w, args.fold) * w.iters
+        fl = cluster_flops(w, args.fold, args.fcnn) * w.iters
         ach32 = fl / (loop_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "kernel": "k_cluster_solve", "achieved": ach32, "peak": fma_tflops,
                     "unit": "TFLOP/s", "frac": ach32 / fma_tflops, "traffic": None,
@@ -365,7 +370,7 @@ def run_ours(args, rank, world, local):
                     "peak_derived": fp32_peak_tflops(peaks),
                     "note": "one launch runs the whole Adam loop; algorithmic FP32 flops (FFT convolutions, "
                             "Fourier synthesis/analysis, the folded data operator G_S Phi and its "
-                            "adjoint) / the launch's CUDA-event time "
+                            "adjoint, the network's products when it is on) / the launch's CUDA-event time "
                             "(solve minus the same solve with 0 iterations); peak = FP32 FMA throughput "
                             "measured by pdf_fp32_fma_peak on this GPU (peak_derived: 152 SMs x 128 FP32 "
                             "lanes x 2 x max SM clock); the loop is latency- and barrier-bound at this size; "

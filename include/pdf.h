@@ -229,9 +229,11 @@ const char* pdf_kernel_name(int32_t k);
 const char* pdf_stage_name(pdf_problem* h, int32_t k);
 
 /* Phase timestamps of the cluster loop (use_graph = 3), for libraries built with the compile
- * definition PDF_PHASE_STAMPS only: out[4][16] receives the global-timer readings (ns) that
+ * definition PDF_PHASE_STAMPS only: out[4][20] receives the global-timer readings (ns) that
  * thread 0 of the first CTA took after each barrier of iterations 5..8 of the last cluster
- * solve (15 marks per iteration, the 16th unused).  Synchronises the device.  PDF_EUNSUPPORTED
+ * solve (marks 0-14 the loss and gradient steps; with the coefficient-correcting network also
+ * 16 after its forward pass, 15 after the chain rule's grid barrier and 17 after the Adam step
+ * on its weights; unused marks hold stale values).  Synchronises the device.  PDF_EUNSUPPORTED
  * in ordinary builds, whose kernels carry no marks. */
 pdf_status pdf_phase_stamps(uint64_t* out);
 

@@ -22,6 +22,14 @@
 //      every CTA of the cluster                                                        | cluster barrier
 //   7. dL/d alpha_p = sum of the partials (same order in every CTA), Adam step on each CTA's copy
 //      of alpha_p (identical in all CTAs of the cluster)
+// With the coefficient-correcting network (Sec. 3, network architecture) the Adam variable is the
+// network's weight vector theta instead: alpha_p = alpha_(0),p + Delta alpha(theta; x_p) is formed at
+// the top of each iteration by the cluster (each CTA a slice of the first layer's and the output
+// layer's rows, broadcast to every CTA of the cluster through DSMEM), step 7 keeps dL/d alpha_p, and
+// the chain rule runs per incidence (dL/dy_p, dz2_p from per-CTA partials over the output rows, dz1_p)
+// into a global array; after a GRID barrier every CTA of the grid forms a slice of dL/d theta as sums
+// over the incidences (increasing p) and takes the Adam step on it, and a second GRID barrier
+// publishes theta before the next forward pass.
 // The data term goes through the folded operator G_S Phi, its receivers split over the cluster:
 // CTA k holds rows r = k + C t, forms r_d,p there in phase 1 and adds (2/||E_sca||^2)(G_S Phi)^H r_d,p
 // over those rows to its phase-6 partial.
@@ -58,7 +66,29 @@ struct ClusterArgs {
   unsigned* bar;
   int* err;               // 1: a grid barrier timed out; 2: launched with the wrong cluster shape
   long long wait_cap;     // clock cycles a grid-barrier wait may last
+  // network form (H > 0): theta = W1 [H][D], b1 [H], W2 [H][H], b2 [H], W3 [D][H], b3 [D], D = 2 ky kx
+  int H;
+  float* theta;           // [np] in / out
+  float* tm;              // [np] Adam moments of theta
+  float* tv;
+  const float* X;         // [ni][D] scaled network input
+  const float* xs;        // [1] input scale s
+  const float2* alpha0;   // [ni][ky][kx] alpha_(0)
+  float* nvec;            // [ni][D + 4H] per incidence: dL/dy, h2, dz2, h1, dz1
+  int wc;                 // 1: W2, b2 and each CTA's output rows of W3, b3 copied to shared memory
 };
+
+// Shared floats of the network form's weight copy (W2, b2, a CTA's output rows of W3 and b3).
+static inline size_t cl_net_cache_floats(int H, int D, int C) {
+  const size_t nsl = (size_t)((D + C - 1) / C);
+  return H > 0 ? (size_t)H * H + H + nsl * H + nsl : 0;
+}
+
+// Shared floats of the network form: x_p [D], h1, h2, dz2, dz1 [H each], the cluster's dz2 partials
+// [C][H], a reduction scratch [CL_NT], alpha_(0),p [D].
+static inline size_t cl_net_floats(int H, int D, int C) {
+  return H > 0 ? 2 * (size_t)D + 4 * (size_t)H + (size_t)C * H + CL_NT : 0;
+}
 
 __device__ __forceinline__ unsigned cl_ld_acquire(const unsigned* p) {
   unsigned v;
@@ -101,11 +131,13 @@ __device__ __forceinline__ void cl_grid_barrier(unsigned* bar, unsigned target, 
 }
 
 // Phase timestamps (instrumented builds, -DPDF_PHASE_STAMPS): thread 0 of CTA 0 records the
-// global timer right after each barrier of iterations CL_STAMP_IT0 .. CL_STAMP_IT0 + 3.  Other
-// builds compile the marks to nothing.
+// global timer right after each barrier of iterations CL_STAMP_IT0 .. CL_STAMP_IT0 + 3 (marks 0-14
+// the loss and gradient steps; with the network also 16 after its forward pass, 15 after the chain
+// rule's grid barrier and 17 after the Adam step on theta).  Other builds compile the marks to
+// nothing.
 #define CL_STAMP_IT0 5
 #ifdef PDF_PHASE_STAMPS
-__device__ unsigned long long g_cl_stamps[4][16];
+__device__ unsigned long long g_cl_stamps[4][20];
 #define CL_STAMP(i)                                                                             \
   do {                                                                                          \
     if (blockIdx.x == 0 && threadIdx.x == 0 && it >= CL_STAMP_IT0 && it < CL_STAMP_IT0 + 4) {   \
@@ -256,6 +288,99 @@ __device__ __noinline__ float4 cl_pixel_sums(const float4* __restrict__ o, int n
   return make_float4(nr_ - cr, ni_ - ci, dd - cd, 0.f);
 }
 
+// Network weights are read through L2 (GLB: theta changes between iterations) or from this CTA's
+// shared-memory copy of them.
+template <bool GLB>
+__device__ __forceinline__ float cl_net_ld(const float* p) {
+  if (GLB) return __ldcg(p);
+  return *p;
+}
+__device__ __forceinline__ void cl_cp_async4(float* smem, const float* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+// Network form: out[r0 + i] = sum_c W[i cols + c] v[c] + bias[i] for i < nrow (W, bias: from row r0
+// on), a warp per row (lanes over c, c = lane + 32 u in increasing u, a butterfly warp sum);
+// epi(r0 + i, value) on lane 0.  Each warp takes NR of its rows at once and issues all their loads
+// (CPL per lane and row, in chunks of 32 CPL columns) before the multiply-adds, so the round trips
+// overlap.
+template <bool GLB, int CPL, int NR, class Epi>
+__device__ __forceinline__ void cl_net_rows(const float* __restrict__ W, const float* __restrict__ bias, int cols,
+                                            const float* v, int r0, int nrow, Epi epi) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll 1
+  for (int ib = warp; ib < nrow; ib += CL_NW * NR) {
+    float acc[NR], bv[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      acc[j] = 0.f;
+      bv[j] = ib + CL_NW * j < nrow ? cl_net_ld<GLB>(&bias[ib + CL_NW * j]) : 0.f;
+    }
+#pragma unroll 1
+    for (int c0 = 0; c0 < cols; c0 += 32 * CPL) {
+      float w[NR][CPL];
+#pragma unroll
+      for (int j = 0; j < NR; ++j)
+#pragma unroll
+        for (int u = 0; u < CPL; ++u) {
+          const int i = ib + CL_NW * j, c = c0 + lane + 32 * u;
+          w[j][u] = i < nrow && c < cols ? cl_net_ld<GLB>(&W[(size_t)i * cols + c]) : 0.f;
+        }
+#pragma unroll
+      for (int j = 0; j < NR; ++j)
+#pragma unroll
+        for (int u = 0; u < CPL; ++u) {
+          const int c = c0 + lane + 32 * u;
+          if (c < cols) acc[j] = fmaf(w[j][u], v[c], acc[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      float t = acc[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      const int i = ib + CL_NW * j;
+      if (lane == 0 && i < nrow) epi(r0 + i, t + bv[j]);
+    }
+  }
+}
+// Network form: out[c] = sum over i < nrow of W[i cols + c] v[i] for c < cols <= CL_NT (W, v: from
+// row r0 on): thread (grp, c) sums i = grp, grp + G, ... in increasing i (G = CL_NT / cols), 16
+// loads in flight at a time, the G partials are added in group order and epi(c, value) runs on the
+// threads c < cols.  Ends with a CTA barrier.
+template <bool GLB, class Epi>
+__device__ __forceinline__ void cl_net_cols(const float* __restrict__ W, int cols, const float* v, int nrow,
+                                            float* red, Epi epi) {
+  const int G = CL_NT / cols, t = threadIdx.x, c = t % cols, grp = t / cols;
+  if (grp < G) {
+    float acc = 0.f;
+#pragma unroll 1
+    for (int ib = grp; ib < nrow; ib += 16 * G) {
+      float w[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int i = ib + u * G;
+        w[u] = i < nrow ? cl_net_ld<GLB>(&W[(size_t)i * cols + c]) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int i = ib + u * G;
+        if (i < nrow) acc = fmaf(w[u], v[i], acc);
+      }
+    }
+    red[grp * cols + c] = acc;
+  }
+  __syncthreads();
+  if (t < cols) {
+    float sum = red[c];
+#pragma unroll 1
+    for (int q = 1; q < G; ++q) sum += red[q * cols + c];
+    epi(c, sum);
+  }
+  __syncthreads();
+}
+
 template <int P>
 __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a) {
   constexpr int R = P / 32;
@@ -320,6 +445,24 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
   float* am = (float*)(gdv + NA);            // [2 NA]
   float* av = am + 2 * NA;                   // [2 NA]
   float2* gsf = (float2*)(av + 2 * NA);      // [NRK][NA] folded receiver operator, own receivers
+  // network form (the same offset in every CTA: after the largest receiver share)
+  const int H = a.H, D = 2 * NA;
+  float* xsn = (float*)(gsf + (size_t)((nr + C - 1) / C) * NA);   // [D] x_p
+  float* h1s = xsn + D;                      // [H]
+  float* h2s = h1s + H;                      // [H]
+  float* dz2s = h2s + H;                     // [H]
+  float* dz1s = dz2s + H;                    // [H]
+  float* npart = dz1s + H;                   // [C][H] dz2 partials of the cluster's CTAs
+  float* nred = npart + C * H;               // [CL_NT]
+  float* a0n = nred + CL_NT;                 // [D] alpha_(0),p: real parts, then imaginary parts
+  // with a.wc: this CTA's copy of W2, b2 and of its output rows' W3, b3 (read in the forward pass and
+  // again in the chain rule of the same iteration)
+  const int nsl = (D + C - 1) / C, n0 = min(D, k * nsl), nrw = min(D, n0 + nsl) - n0;
+  float* cW2 = a0n + D;                      // [H][H]
+  float* cb2 = cW2 + H * H;                  // [H]
+  float* cW3 = cb2 + H;                      // [nsl][H] rows n0 ..
+  float* cb3 = cW3 + nsl * H;                // [nsl]
+  float* dys = av;                           // [D] dL/dy_p (av is Adam state of alpha only)
 
   // ---- one-time loads ----
 #pragma unroll 1
@@ -350,14 +493,67 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     const int t = i / NA, j = i - t * NA;
     gsf[i] = d.gsf[(size_t)(k + C * t) * NA + j];
   }
+  float net_s = 1.f;
+  if (H > 0) {
+#pragma unroll 1
+    for (int i = threadIdx.x; i < D; i += CL_NT) {
+      xsn[i] = a.X[(size_t)p * D + i];
+      const int re = i < NA ? 0 : 1, j = i - re * NA;
+      a0n[i] = reinterpret_cast<const float*>(a.alpha0)[((size_t)p * NA + j) * 2 + re];
+    }
+    net_s = a.xs[0];
+  }
   const float ke = d.invn[0], ks = d.invn[1];
   const float2 beta = d.beta, bc = cconj(d.beta);
   const unsigned nblocks = gridDim.x;
+  unsigned nbar = 0;                         // grid barriers passed (targets nbar * nblocks)
+  // theta's offsets in the flat vector
+  const size_t oW1 = 0, ob1 = (size_t)H * D, oW2 = ob1 + H, ob2 = oW2 + (size_t)H * H, oW3 = ob2 + H,
+               ob3 = oW3 + (size_t)D * H, npar = ob3 + D;
   cl.sync();
 
   for (int it = 0; it < a.iters; ++it) {
     CL_STAMP(0);
     float4* nd = a.nd + (size_t)(it & 1) * ni * M;
+    if (H > 0) {
+      // ===== 0. alpha_p = alpha_(0),p + Delta alpha(theta; x_p) =====
+      const float* th = a.theta;
+      if (a.wc) {                            // W2, b2 and the output rows' W3, b3 in one round of copies
+#pragma unroll 1
+        for (int i = threadIdx.x; i < H * H; i += CL_NT) cl_cp_async4(cW2 + i, th + oW2 + i);
+#pragma unroll 1
+        for (int i = threadIdx.x; i < nrw * H; i += CL_NT) cl_cp_async4(cW3 + i, th + oW3 + (size_t)n0 * H + i);
+        if ((int)threadIdx.x < H) cl_cp_async4(cb2 + threadIdx.x, th + ob2 + threadIdx.x);
+#pragma unroll 1
+        for (int i = threadIdx.x; i < nrw; i += CL_NT) cl_cp_async4(cb3 + i, th + ob3 + n0 + i);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+      }
+      const int hs = (H + C - 1) / C, h0 = min(H, k * hs), nh = min(H, h0 + hs) - h0;
+      cl_net_rows<true, 16, 1>(th + oW1 + (size_t)h0 * D, th + ob1 + h0, D, xsn, h0, nh, [&](int h, float v) {
+        v = fmaxf(v, 0.f);
+#pragma unroll 1
+        for (int q = 0; q < C; ++q) cl.map_shared_rank(h1s, q)[h] = v;
+      });
+      if (a.wc) asm volatile("cp.async.wait_group 0;" ::: "memory");
+      cl.sync();
+      auto out_alpha = [&](int n, float v) {
+        const int re = n < NA ? 0 : 1, j = n - re * NA;
+        const float o = a0n[n] + v / net_s;
+#pragma unroll 1
+        for (int q = 0; q < C; ++q) reinterpret_cast<float*>(cl.map_shared_rank(al, q))[2 * j + re] = o;
+      };
+      if (a.wc) {
+        cl_net_rows<false, 2, 4>(cW2, cb2, H, h1s, 0, H, [&](int h, float v) { h2s[h] = fmaxf(v, 0.f); });
+        __syncthreads();
+        cl_net_rows<false, 2, 8>(cW3, cb3, H, h2s, n0, nrw, out_alpha);
+      } else {
+        cl_net_rows<true, 2, 4>(th + oW2, th + ob2, H, h1s, 0, H, [&](int h, float v) { h2s[h] = fmaxf(v, 0.f); });
+        __syncthreads();
+        cl_net_rows<true, 2, 8>(th + oW3 + (size_t)n0 * H, th + ob3 + n0, H, h2s, n0, nrw, out_alpha);
+      }
+      cl.sync();
+      CL_STAMP(16);
+    }
     // ===== 1. synthesis (Eq. 9): T' of all rows, J on own rows, the padded row DFT of J on own columns =====
     // T'[y][jx] = sum_jy Wy[jy][y] al[jy][jx] (low threads) while the top warps form r_d
     cl_cgemm<2, 2, 1, false, false>(ny, kx, ky, wyf, 1, ny, al, kx, 1,
@@ -454,8 +650,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
       const float2 n = cmul(beta, cmulc(J, s));
       __stcg(&nd[(size_t)p * M + y0 * nx + i], make_float4(n.x, n.y, cabs2(s), 0.f));
     }
-    const unsigned nbar = a.sl > 0 ? 2u : 1u;                           // grid barriers per iteration
-    cl_grid_barrier(a.bar, ((unsigned)it * nbar + 1u) * nblocks, a.err, a.wait_cap, [&] {
+    cl_grid_barrier(a.bar, ++nbar * nblocks, a.err, a.wait_cap, [&] {
 #pragma unroll 1
       for (int i = threadIdx.x - 32; i < NA; i += CL_NT - 32) {            // (G_S Phi)^H r_d, own receivers (Eq. 16)
         float2 g = make_float2(0.f, 0.f);
@@ -500,7 +695,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
           __stcg(a.dsg + j, clamped ? -Df : Df);
         }
       }
-      cl_grid_barrier(a.bar, ((unsigned)it * 2u + 2u) * nblocks, a.err, a.wait_cap, [] {});
+      cl_grid_barrier(a.bar, ++nbar * nblocks, a.err, a.wait_cap, [] {});
       const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 1
       for (int i0 = threadIdx.x; i0 < HPk; i0 += 4 * CL_NT) {            // own rows + halo, four loads in flight
@@ -696,12 +891,17 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     });
     cl.sync();
     CL_STAMP(13);
-    // ===== 7. gradient and Adam step on this CTA's copy of alpha_p =====
+    // ===== 7. gradient and Adam step on this CTA's copy of alpha_p (network form: dL/dy_p) =====
 #pragma unroll 1
     for (int i = threadIdx.x; i < NA; i += CL_NT) {
       float2 g = make_float2(0.f, 0.f);
 #pragma unroll 1
       for (int q = 0; q < C; ++q) g = g + gpart[q * NA + i];
+      if (H > 0) {
+        dys[i] = g.x / net_s;
+        dys[NA + i] = g.y / net_s;
+        continue;
+      }
       float2 ap = al[i];
       ph_adam(0, &ap.x, &g.x, &am[2 * i], &av[2 * i], 1, it + 1, a.tab, a.cap, a.b1, a.b2, a.eps);
       ph_adam(0, &ap.y, &g.y, &am[2 * i + 1], &av[2 * i + 1], 1, it + 1, a.tab, a.cap, a.b1, a.b2, a.eps);
@@ -709,8 +909,90 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
     }
     __syncthreads();
     CL_STAMP(14);
+    if (H > 0) {
+      // ===== 8. chain rule to theta, per incidence =====
+      const float* th = a.theta;
+      // dz2 = (W3^T dL/dy) 1[h2 > 0]: this CTA's output rows, partials to every CTA, summed in rank order
+      auto put_part = [&](int h, float v) {
+#pragma unroll 1
+        for (int q = 0; q < C; ++q) cl.map_shared_rank(npart, q)[k * H + h] = v;
+      };
+      if (a.wc) cl_net_cols<false>(cW3, H, dys + n0, nrw, nred, put_part);
+      else cl_net_cols<true>(th + oW3 + (size_t)n0 * H, H, dys + n0, nrw, nred, put_part);
+      cl.sync();
+      if ((int)threadIdx.x < H) {
+        const int h = threadIdx.x;
+        float v = npart[h];
+#pragma unroll 1
+        for (int q = 1; q < C; ++q) v += npart[q * H + h];
+        dz2s[h] = h2s[h] > 0.f ? v : 0.f;
+      }
+      __syncthreads();
+      // dz1 = (W2^T dz2) 1[h1 > 0]
+      auto put_dz1 = [&](int h, float v) { dz1s[h] = h1s[h] > 0.f ? v : 0.f; };
+      if (a.wc) cl_net_cols<false>(cW2, H, dz2s, H, nred, put_dz1);
+      else cl_net_cols<true>(th + oW2, H, dz2s, H, nred, put_dz1);
+      const int NV = D + 4 * H;
+      if (k == 0) {
+        float* nv = a.nvec + (size_t)p * NV;
+#pragma unroll 1
+        for (int i = threadIdx.x; i < NV; i += CL_NT) {
+          const float v = i < D ? dys[i] : i < D + H ? h2s[i - D] : i < D + 2 * H ? dz2s[i - D - H]
+                          : i < D + 3 * H ? h1s[i - D - 2 * H] : dz1s[i - D - 3 * H];
+          __stcg(nv + i, v);
+        }
+      }
+      cl_grid_barrier(a.bar, ++nbar * nblocks, a.err, a.wait_cap, [] {});
+      CL_STAMP(15);
+      // ===== 9. dL/d theta on this CTA's slice of theta (sums over incidences, increasing p) and Adam =====
+      const size_t ps = (npar + nblocks - 1) / nblocks, i0 = (size_t)blockIdx.x * ps, i1 = min(npar, i0 + ps);
+      const float2 asc = ph_adam_sc(a.tab, a.cap, it + 1);
+#pragma unroll 1
+      for (size_t i = i0 + threadIdx.x; i < i1; i += CL_NT) {
+        // dW = dZ^T U over the incidences (U = X, h1 or h2), the bias gradients the sums of dZ
+        int zo, uo = -1, zi, ui = 0;
+        bool ux = false;
+        if (i < ob1) {
+          zo = D + 3 * H; zi = (int)((i - oW1) / D); ui = (int)((i - oW1) % D); ux = true;
+        } else if (i < oW2) {
+          zo = D + 3 * H; zi = (int)(i - ob1);
+        } else if (i < ob2) {
+          zo = D + H; zi = (int)((i - oW2) / H); uo = D + 2 * H; ui = (int)((i - oW2) % H);
+        } else if (i < oW3) {
+          zo = D + H; zi = (int)(i - ob2);
+        } else if (i < ob3) {
+          zo = 0; zi = (int)((i - oW3) / H); uo = D; ui = (int)((i - oW3) % H);
+        } else {
+          zo = 0; zi = (int)(i - ob3);
+        }
+        float tp = __ldcg(a.theta + i), mi = a.tm[i], vi = a.tv[i];
+        // (a bias term is z times 1: fmaf(z, 1, g) rounds z + g once, as the plain sum does)
+        float g = 0.f;
+#pragma unroll 1
+        for (int q0 = 0; q0 < ni; q0 += 16) {
+          float z[16], u[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int q = q0 + j;
+            const float* nv = a.nvec + (size_t)q * NV;
+            z[j] = q < ni ? __ldcg(nv + zo + zi) : 0.f;
+            u[j] = q >= ni ? 0.f : ux ? __ldg(a.X + (size_t)q * D + ui) : uo >= 0 ? __ldcg(nv + uo + ui) : 1.f;
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (q0 + j < ni) g = fmaf(z[j], u[j], g);
+        }
+        ph_adam_at(tp, g, mi, vi, asc, a.b1, a.b2, a.eps);
+        __stcg(a.theta + i, tp);
+        a.tm[i] = mi;
+        a.tv[i] = vi;
+      }
+      __syncthreads();
+      CL_STAMP(17);
+      if (it + 1 < a.iters) cl_grid_barrier(a.bar, ++nbar * nblocks, a.err, a.wait_cap, [] {});
+    }
   }
-  if (k == 0)
+  if (k == 0 && H == 0)
 #pragma unroll 1
     for (int i = threadIdx.x; i < NA; i += CL_NT) a.alpha[(size_t)p * NA + i] = al[i];
   cl.sync();
@@ -719,7 +1001,7 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
 // ---------------------------------------------------------------------------
 // host
 // ---------------------------------------------------------------------------
-static size_t cluster_smem(const Dev& d, int C, int RB, int CB, int P) {
+static size_t cluster_smem(const Dev& d, int C, int RB, int CB, int P, int H) {
   const size_t NA = (size_t)d.ky * d.kx, GP = (size_t)RB * d.nx, HP = (size_t)(RB + 2) * d.nx,
                TP = (size_t)(RB + 1) * d.nx;
   const size_t nscr = 2 * GP + HP + 2 * TP;
@@ -729,7 +1011,7 @@ static size_t cluster_smem(const Dev& d, int C, int RB, int CB, int P) {
                     NA + NU + 2 * (size_t)d.nr +
                     (size_t)d.ny * d.kx + (size_t)d.ky * d.ny + (size_t)d.kx * CB +
                     (size_t)CB * P + (size_t)d.kx * d.nx + NA + (size_t)((d.nr + C - 1) / C) * NA;
-  return f2 * sizeof(float2) + 4 * NA * sizeof(float);
+  return f2 * sizeof(float2) + 4 * NA * sizeof(float) + cl_net_floats(H, 2 * (int)NA, C) * sizeof(float);
 }
 
 // dynamic shared memory limit of the cluster kernel (227 KB per block; no static use)
@@ -793,6 +1075,8 @@ struct ClPlanRow {
 static int cl_plan(const pdf_problem* h, ClPlanRow* rows, int nmax) {
   const Dev& d = h->d;
   if (!d.fast || h->tc || !d.fold || !d.what || d.cco_loss || d.Px != d.Py || d.Px > 128 || d.kx > 64) return 0;
+  const int H = h->fc_active ? h->fc.H : 0;
+  if (H > CL_NT) return 0;
   int dev = 0, sms = 0, coop = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -805,7 +1089,7 @@ static int cl_plan(const pdf_problem* h, ClPlanRow* rows, int nmax) {
   for (int c : sizes) {
     if (n >= nmax) break;
     if (!cluster_ok(d, sms, c)) continue;
-    const size_t smem = cluster_smem(d, c, cl_rb(d, c), cl_cb(d, c), d.Px);
+    const size_t smem = cluster_smem(d, c, cl_rb(d, c), cl_cb(d, c), d.Px, H);
     ClPlanRow r = {c, (int)smem, -1, 0};
     if (smem <= CL_SMEM_MAX) {
       r.clusters = d.Px == 64 ? max_active_clusters<64>(d.ni, c, smem) : max_active_clusters<128>(d.ni, c, smem);
@@ -872,7 +1156,8 @@ pdf_status cl_run(pdf_problem* h, const pdf_solve_opts* o, int iters, cudaStream
   a.sl = rep_bytes > 128 * 1024 ? (d.M + nb - 1) / nb : 0;
   for (a.sg = 1; 8 * a.sg < d.ni; a.sg *= 2) {
   }
-  if ((uint64_t)iters * 2 * nb >= 0xffffffffull) return PDF_OK;  // barrier counter range
+  a.H = h->fc_active ? h->fc.H : 0;
+  if ((uint64_t)iters * (a.H > 0 ? 4 : 2) * nb >= 0xffffffffull) return PDF_OK;  // barrier counter range
   if (!h->cl_nd) {
     pdf_status s;
     const size_t bytes = sizeof(float4) * (2 * (size_t)d.ni + 1) * d.M + sizeof(float) * (size_t)d.M;
@@ -890,6 +1175,23 @@ pdf_status cl_run(pdf_problem* h, const pdf_solve_opts* o, int iters, cudaStream
   a.bar = h->bar;
   a.err = h->perr;
   a.wait_cap = o->barrier_wait_cycles > 0 ? (long long)o->barrier_wait_cycles : (1ll << 31);
+  a.theta = a.tm = a.tv = a.nvec = nullptr;
+  a.X = a.xs = nullptr;
+  a.alpha0 = nullptr;
+  if (a.H > 0) {
+    FcState& f = h->fc;
+    if (!f.nvec) {
+      pdf_status s;
+      if ((s = ws_alloc(h, (void**)&f.nvec, sizeof(float) * (size_t)d.ni * (f.D + 4 * f.H))) != PDF_OK) return s;
+    }
+    a.theta = f.theta;
+    a.tm = f.m;
+    a.tv = f.v;
+    a.X = f.X;
+    a.xs = f.s;
+    a.alpha0 = f.alpha0;
+    a.nvec = f.nvec;
+  }
   // Test hook for the solve's recovery path: with PDF_TEST_CLUSTER_SHAPE=mismatch in the environment
   // the kernel is told to expect a cluster size no launch has, so every CTA takes the entry check's
   // early return (error flag 2) exactly as when a tool launches it without its cluster shape.
@@ -897,7 +1199,19 @@ pdf_status cl_run(pdf_problem* h, const pdf_solve_opts* o, int iters, cudaStream
     if (strcmp(t, "mismatch") == 0) a.C = 0;
   PDF_CUDA(cudaMemsetAsync(h->bar, 0, sizeof(unsigned), st));
   cudaLaunchAttribute at[2];
-  const size_t smem = (size_t)rows[pick].smem;
+  size_t smem = (size_t)rows[pick].smem;
+  // the network weights' shared copy, where it fits beside the plan with all clusters still resident
+  a.wc = 0;
+  if (a.H > 0) {
+    const size_t wc = smem + cl_net_cache_floats(a.H, 2 * d.ky * d.kx, rows[pick].C) * sizeof(float);
+    const int fit = wc > CL_SMEM_MAX ? -1
+                    : d.Px == 64 ? max_active_clusters<64>(d.ni, rows[pick].C, wc)
+                                 : max_active_clusters<128>(d.ni, rows[pick].C, wc);
+    if (fit >= d.ni) {
+      a.wc = 1;
+      smem = wc;
+    }
+  }
   cudaError_t e;
   if (d.Px == 64) {
     cudaLaunchConfig_t cfg = cluster_config<64>(d.ni, rows[pick].C, smem, st, at);

@@ -296,6 +296,7 @@ pdf_status fc_prepare(pdf_problem* h, int hidden, const void* params0, cudaStrea
     if ((s = ws_alloc(h, (void**)&f.work, sizeof(float) * wn)) != PDF_OK) return s;
     if ((s = ws_alloc(h, (void**)&f.tick, sizeof(unsigned) * FC_TICKS)) != PDF_OK) return s;
     PDF_CUDA(cudaMemsetAsync(f.tick, 0, sizeof(unsigned) * FC_TICKS, st));
+    f.nvec = nullptr;                                                    // sized by the cluster loop on use
     f.H = H;
     f.D = D;
     f.B = B;

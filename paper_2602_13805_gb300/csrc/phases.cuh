@@ -800,18 +800,24 @@ __device__ __forceinline__ void ph_finalize(const Dev& d, double* terms, int n_s
 
 
 // Adam (torch.optim.Adam arithmetic, FP32) on element i of the real view, step t >= 1 given
+// one element: parameter p, gradient g, moments m, v; sc = tab[t - 1] of the step
+__device__ __forceinline__ void ph_adam_at(float& p, float g, float& m, float& v, float2 sc, float b1, float b2,
+                                           float eps) {
+  m = m + (1.f - b1) * (g - m);
+  v = v * b2;
+  v = v + ((1.f - b2) * g) * g;
+  const float denom = sqrtf(v) / sc.y + eps;
+  p = p + (-sc.x) * (m / denom);
+}
+// the step's table entry: lr / (1 - b1^t), sqrt(1 - b2^t), evaluated in FP64 on the host
+__device__ __forceinline__ float2 ph_adam_sc(const float2* tab, int cap, int t) { return tab[min(max(t, 1), cap) - 1]; }
 __device__ __forceinline__ void ph_adam(int i, float* p, const float* g, float* m, float* v, int n, int t,
                                         const float2* tab, int cap, float b1, float b2, float eps) {
   if (i >= n) return;
-  t = min(max(t, 1), cap);
-  const float2 sc = tab[t - 1];        // lr / (1 - b1^t), sqrt(1 - b2^t), evaluated in FP64 on the host
-  const float gi = g[i];
-  float mi = m[i];
-  mi = mi + (1.f - b1) * (gi - mi);
-  float vi = v[i] * b2;
-  vi = vi + ((1.f - b2) * gi) * gi;
+  const float2 sc = ph_adam_sc(tab, cap, t);
+  float pi = p[i], mi = m[i], vi = v[i];
+  ph_adam_at(pi, g[i], mi, vi, sc, b1, b2, eps);
   m[i] = mi;
   v[i] = vi;
-  const float denom = sqrtf(vi) / sc.y + eps;
-  p[i] = p[i] + (-sc.x) * (mi / denom);
+  p[i] = pi;
 }

@@ -102,6 +102,7 @@ struct FcState {
   float2* alpha0;        // [ni][ky][kx] the network's input coefficients
   float* work;           // split-k partial sums
   unsigned* tick;        // [FC_TICKS] per-output-tile arrival counters of the split-k products (zero between uses)
+  float* nvec;           // [B][D + 4H] per-incidence chain-rule vectors of the cluster loop (allocated on first use)
 };
 
 struct pdf_problem {

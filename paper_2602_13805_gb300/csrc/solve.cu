@@ -433,7 +433,7 @@ static pdf_status run_loop(pdf_problem* h, const pdf_solve_opts* o, int fused, i
     return PDF_OK;
   }
   bool persisted = false;
-  if (fused && o->use_graph == 3 && !h->fc_active) {
+  if (fused && o->use_graph == 3) {
     if ((s = cl_run(h, o, o->iters, st, &persisted)) != PDF_OK) return s;
     if (persisted) {
       it = o->iters;

@@ -131,3 +131,6 @@ def test_cluster_flops_c2_both_forms():
     per_inc = 2 * 606720 + 2 * 1818624
     assert bench.cluster_flops(w, fold=1) == 16 * (per_inc + 2 * 57600) == 79454208
     assert bench.cluster_flops(w, fold=0) == 16 * (per_inc + 2 * 1048576) == 111165440
+    # the network (H = 64, D = 450) per incidence: forward 28 800 + 4 096 + 28 800 MACs, chain rule
+    # 28 800 + 4 096, weight gradients 28 800 + 4 096 + 28 800: 156 288 MACs, 312 576 flops
+    assert bench.cluster_flops(w, fold=1, hidden=64) == 79454208 + 16 * 312576 == 84455424

@@ -73,18 +73,77 @@ def test_loss_history_tracks_oracle():
     prob.close()
 
 
-def test_graph_and_eager_loops_agree_and_cluster_falls_back():
+def test_graph_and_eager_loops_agree():
     w, c, a0, th0 = _case()
     prob = c.problem()
     kw = dict(iters=30, init=1, alpha0=_dev(a0), apply_cco=False, fcnn_hidden=H, fcnn_params0=_dev(th0))
     e = prob.solve(use_graph=0, **kw)
     g = prob.solve(use_graph=1, **kw)
-    k = prob.solve(use_graph=3, **kw)
     assert torch.equal(e["alpha"], g["alpha"])                       # same kernels, same order
-    assert torch.equal(g["alpha"], k["alpha"])
-    assert g["loop_mode"] == 1 and k["loop_mode"] == 1              # the cluster loop optimises alpha only
+    assert g["loop_mode"] == 1
     plain = prob.solve(use_graph=1, iters=30, init=1, alpha0=_dev(a0), apply_cco=False)
     assert not torch.equal(plain["alpha"], g["alpha"])               # the graph was rebuilt for the plain form
+    prob.close()
+
+
+@pytest.mark.parametrize("name,kw", [("c1", {}), ("c2", {}), ("cP", {}), ("c2-ni14", dict(ni=14))])
+def test_cluster_loop_network_form_matches_graph(name, kw):
+    # The network form inside the one-launch cluster loop (forward and chain rule per incidence in
+    # each cluster, dL/d theta and Adam on theta in slices over the grid between two grid barriers)
+    # against the CUDA graph of the stand-alone kernels: the same formulas with other summation
+    # orders (the network's dot products, the loss gradient), so FP32-level drift only.
+    from paper_2602_13805_gb300 import pdf
+    w = scenes.workload(name.split("-")[0], **kw)
+    c = Case(w)
+    a0 = c.alpha(scale=0.2, seed=4)
+    th0 = scenes.fcnn_params(w.ky, w.kx, H, seed=7)
+    prob = c.problem()
+    chi_t = _dev(c.chi.astype(np.complex64))
+    kw2 = dict(iters=40, init=1, alpha0=_dev(a0), chi_true=chi_t, fcnn_hidden=H, fcnn_params0=_dev(th0))
+    g = prob.solve(use_graph=1, **kw2)
+    k = prob.solve(use_graph=3, **kw2)
+    k2 = prob.solve(use_graph=3, **kw2)
+    plan = pdf.pdf_cluster_plan(prob.h)
+    print(name, "cluster plan with the network (C, smem, co-resident clusters, usable):", plan)
+    assert g["loop_mode"] == 1
+    assert k["loop_mode"] == (3 if any(r[3] for r in plan) else 1)
+    if name in ("c1", "cP", "c2-ni14"):
+        assert k["loop_mode"] == 3
+    assert torch.equal(k["alpha"], k2["alpha"])                       # deterministic
+    err = (g["alpha"] - k["alpha"]).abs().max().item() / g["alpha"].abs().max().item()
+    print(name, "network form: cluster vs graph alpha rel", err, "relerr_cco", g["relerr_cco"], k["relerr_cco"])
+    assert err < 1e-3
+    assert abs(g["relerr_cco"] - k["relerr_cco"]) < 1e-3
+    np.testing.assert_allclose(g["terms"], k["terms"], rtol=1e-3)
+    prob.close()
+
+
+@pytest.mark.parametrize("name", ["c1", "cP"])
+def test_cluster_loop_network_one_step_matches_oracle(name):
+    w, c, a0, th0 = _case(name)
+    prob = c.problem()
+    out = prob.solve(iters=1, init=1, alpha0=_dev(a0), apply_cco=False, use_graph=3,
+                     fcnn_hidden=H, fcnn_params0=_dev(th0))
+    assert out["loop_mode"] == 3
+    ref = fcnn.reparam_solve(c.ops, c.esca, 1, th0, H, lr=1e-2, alpha0=a0.astype(np.complex128), apply_cco=False)
+    d_gpu = out["alpha"].cpu().numpy() - a0
+    d_ref = ref["alpha"] - a0
+    assert np.abs(d_ref).max() > 0
+    assert_close(f"{name} cluster loop, one-step Delta alpha", d_gpu, d_ref, 1e-3)
+    prob.close()
+
+
+def test_cluster_loop_network_shape_mismatch_falls_back_to_the_graph(monkeypatch):
+    w, c, a0, th0 = _case()
+    prob = c.problem()
+    kw = dict(iters=20, init=1, alpha0=_dev(a0), apply_cco=False, fcnn_hidden=H, fcnn_params0=_dev(th0))
+    g = prob.solve(use_graph=1, **kw)
+    monkeypatch.setenv("PDF_TEST_CLUSTER_SHAPE", "mismatch")
+    k = prob.solve(use_graph=3, **kw)
+    monkeypatch.delenv("PDF_TEST_CLUSTER_SHAPE")
+    assert k["loop_mode"] == 1
+    assert torch.equal(k["alpha"], g["alpha"])                       # theta and its moments were untouched
+    assert prob.solve(use_graph=3, **kw)["loop_mode"] == 3
     prob.close()
 
 

@@ -84,10 +84,10 @@ static inline size_t cl_net_cache_floats(int H, int D, int C) {
   return H > 0 ? (size_t)H * H + H + nsl * H + nsl : 0;
 }
 
-// Shared floats of the network form: x_p [D], h1, h2, dz2, dz1 [H each], the cluster's dz2 partials
-// [C][H], a reduction scratch [CL_NT], alpha_(0),p [D].
+// Shared floats of the network form: x_p [D], h1, h2, dz2, dz1 [H each], the cluster's dz2 and dz1
+// partials [C][H] each, a reduction scratch [CL_NT], alpha_(0),p [D].
 static inline size_t cl_net_floats(int H, int D, int C) {
-  return H > 0 ? 2 * (size_t)D + 4 * (size_t)H + (size_t)C * H + CL_NT : 0;
+  return H > 0 ? 2 * (size_t)D + 4 * (size_t)H + 2 * (size_t)C * H + CL_NT : 0;
 }
 
 __device__ __forceinline__ unsigned cl_ld_acquire(const unsigned* p) {
@@ -453,7 +453,8 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
   float* dz2s = h2s + H;                     // [H]
   float* dz1s = dz2s + H;                    // [H]
   float* npart = dz1s + H;                   // [C][H] dz2 partials of the cluster's CTAs
-  float* nred = npart + C * H;               // [CL_NT]
+  float* npart2 = npart + C * H;             // [C][H] dz1 partials (without the weight copy)
+  float* nred = npart2 + C * H;              // [CL_NT]
   float* a0n = nred + CL_NT;                 // [D] alpha_(0),p: real parts, then imaginary parts
   // with a.wc: this CTA's copy of W2, b2 and of its output rows' W3, b3 (read in the forward pass and
   // again in the chain rule of the same iteration)
@@ -547,8 +548,13 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
         __syncthreads();
         cl_net_rows<false, 2, 8>(cW3, cb3, H, h2s, n0, nrw, out_alpha);
       } else {
-        cl_net_rows<true, 2, 4>(th + oW2, th + ob2, H, h1s, 0, H, [&](int h, float v) { h2s[h] = fmaxf(v, 0.f); });
-        __syncthreads();
+        // without the copy, h2 is split over the cluster as h1 is (each CTA reads its rows of W2 once)
+        cl_net_rows<true, 2, 4>(th + oW2 + (size_t)h0 * H, th + ob2 + h0, H, h1s, h0, nh, [&](int h, float v) {
+          v = fmaxf(v, 0.f);
+#pragma unroll 1
+          for (int q = 0; q < C; ++q) cl.map_shared_rank(h2s, q)[h] = v;
+        });
+        cl.sync();
         cl_net_rows<true, 2, 8>(th + oW3 + (size_t)n0 * H, th + ob3 + n0, H, h2s, n0, nrw, out_alpha);
       }
       cl.sync();
@@ -928,10 +934,26 @@ __global__ void __launch_bounds__(CL_NT, 1) k_cluster_solve(Dev d, ClusterArgs a
         dz2s[h] = h2s[h] > 0.f ? v : 0.f;
       }
       __syncthreads();
-      // dz1 = (W2^T dz2) 1[h1 > 0]
-      auto put_dz1 = [&](int h, float v) { dz1s[h] = h1s[h] > 0.f ? v : 0.f; };
-      if (a.wc) cl_net_cols<false>(cW2, H, dz2s, H, nred, put_dz1);
-      else cl_net_cols<true>(th + oW2, H, dz2s, H, nred, put_dz1);
+      // dz1 = (W2^T dz2) 1[h1 > 0]; without the copy from partials over this CTA's rows of W2 (the
+      // slice of h1 and h2), exchanged and summed in rank order
+      if (a.wc) {
+        cl_net_cols<false>(cW2, H, dz2s, H, nred, [&](int h, float v) { dz1s[h] = h1s[h] > 0.f ? v : 0.f; });
+      } else {
+        const int hs = (H + C - 1) / C, h0 = min(H, k * hs), nh = min(H, h0 + hs) - h0;
+        cl_net_cols<true>(th + oW2 + (size_t)h0 * H, H, dz2s + h0, nh, nred, [&](int h, float v) {
+#pragma unroll 1
+          for (int q = 0; q < C; ++q) cl.map_shared_rank(npart2, q)[k * H + h] = v;
+        });
+        cl.sync();
+        if ((int)threadIdx.x < H) {
+          const int h = threadIdx.x;
+          float v = npart2[h];
+#pragma unroll 1
+          for (int q = 1; q < C; ++q) v += npart2[q * H + h];
+          dz1s[h] = h1s[h] > 0.f ? v : 0.f;
+        }
+        __syncthreads();
+      }
       const int NV = D + 4 * H;
       if (k == 0) {
         float* nv = a.nvec + (size_t)p * NV;

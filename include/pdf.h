@@ -158,8 +158,12 @@ typedef struct pdf_solve_opts {
    * components), two hidden layers of width H with ReLU, a linear output y_p of D reals, and
    * Delta alpha_p = (y_p[0 .. ky kx) + i y_p[ky kx .. D)) / s; one network for all incidences.
    * fcnn_params0: device float32, caller-owned, read at the start of the solve: W1 [H][D], b1 [H],
-   * W2 [H][H], b2 [H], W3 [D][H], b3 [D], row-major, concatenated.  1 <= H <= 4096.  The loop runs
-   * as the CUDA graph (use_graph 1..3) or one launch per kernel (0); alpha_out receives alpha-hat. */
+   * W2 [H][H], b2 [H], W3 [D][H], b3 [D], row-major, concatenated.  1 <= H <= 4096.  With
+   * use_graph 3 and H <= 512 the loop runs inside the cluster launch where the grid qualifies for
+   * it (forward pass and chain rule per incidence in each cluster, the weight gradient and Adam in
+   * slices over the grid between two grid barriers per iteration); otherwise as the CUDA graph
+   * (use_graph 1..3) or one launch per kernel (0).  alpha_out receives alpha-hat at the final
+   * weights. */
   int32_t fcnn_hidden;       /* 0 = off (Adam on alpha) */
   const void* fcnn_params0;
   /* Cap, in SM clock cycles, on each grid-barrier wait of the one-launch loop forms (use_graph 2

@@ -25,11 +25,12 @@
 // With the coefficient-correcting network (Sec. 3, network architecture) the Adam variable is the
 // network's weight vector theta instead: alpha_p = alpha_(0),p + Delta alpha(theta; x_p) is formed at
 // the top of each iteration by the cluster (each CTA a slice of the first layer's and the output
-// layer's rows, broadcast to every CTA of the cluster through DSMEM), step 7 keeps dL/d alpha_p, and
-// the chain rule runs per incidence (dL/dy_p, dz2_p from per-CTA partials over the output rows, dz1_p)
-// into a global array; after a GRID barrier every CTA of the grid forms a slice of dL/d theta as sums
-// over the incidences (increasing p) and takes the Adam step on it, and a second GRID barrier
-// publishes theta before the next forward pass.
+// layer's rows, broadcast to every CTA of the cluster through DSMEM; the second layer likewise
+// unless the CTA holds a shared-memory copy of W2), step 7 keeps dL/d alpha_p, and the chain rule
+// runs per incidence (dL/dy_p, dz2_p from per-CTA partials over the output rows, dz1_p, from
+// partials over the CTAs' rows of W2 without the copy) into a global array; after a GRID barrier
+// every CTA of the grid forms a slice of dL/d theta as sums over the incidences (increasing p) and
+// takes the Adam step on it, and a second GRID barrier publishes theta before the next forward pass.
 // The data term goes through the folded operator G_S Phi, its receivers split over the cluster:
 // CTA k holds rows r = k + C t, forms r_d,p there in phase 1 and adds (2/||E_sca||^2)(G_S Phi)^H r_d,p
 // over those rows to its phase-6 partial.
